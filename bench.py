@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Throughput of sigma = H C over the bosonic Fock basis (arXiv:2005.13679,
+Eq. Haction) on GB300.
+
+Default workload: generic Hermitian h/W, N = 100 bosons in M = 6 orbitals
+(96,560,646 configurations, complex128 C of 1.5 GB, larger than L2), FP64-class
+apply.  A step is one H C product with inputs resident in HBM.  Prints one JSON
+line (rank 0).  Multi-GPU runs (torchrun) are independent replicas, one per
+rank (weak scaling; the apply needs no exchange between replicas).
+
+--impl reference times the plain CPU oracle (the only reference this project
+has) on the host cores, on a bounded sample of rows of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H·C applies/s and config-terms/s, FP64 vs FP32-mixed/batched, % of HBM roofline"
+PREC = {"f64": 0, "f64_native": 1, "f32_mixed": 2}
+DTYPE = {"f64": "f64 (fp32-pair arithmetic)", "f64_native": "f64", "f32_mixed": "c64 storage, fp32 products, fp32-pair accumulation"}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (bounded sample of rows)
+# --------------------------------------------------------------------------
+def oracle_rate(w, h, W, C, seconds: float):
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    terms_per_cfg = None
+    rng = np.random.default_rng(123)
+    n = 8
+    while True:
+        rows = rng.integers(0, w.nc, n)
+        t0 = time.perf_counter()
+        oracle.apply_rows(w.N, w.M, h, W, C, rows)
+        dt = time.perf_counter() - t0
+        if dt > 0.2 * seconds or n >= 1 << 22:
+            break
+        n = int(n * min(16.0, max(2.0, 0.3 * seconds / max(dt, 1e-4))))
+    return n, dt
+
+
+def run_reference(args, w):
+    import numpy as np
+
+    from paper_2005_13679_gb300 import inputs  # noqa: F401  (input generator only)
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    h, W = w.hamiltonian()
+    C = w.state() if w.nrhs == 1 else w.state()[:, 0].copy()
+    terms_total = terms_formula(w, h, W)
+    per_cfg = terms_total / w.nc
+    budget = max(5.0, min(60.0, 120.0 / max(1, args.steps + args.warmup)))
+    rows_per_step, _ = oracle_rate(w, h, W, C, budget)
+    import oracle
+    rng = np.random.default_rng(7)
+    for _ in range(args.warmup):
+        oracle.apply_rows(w.N, w.M, h, W, C, rng.integers(0, w.nc, max(1, rows_per_step // 8)))
+    times = []
+    for _ in range(args.steps):
+        rows = rng.integers(0, w.nc, rows_per_step)
+        t0 = time.perf_counter()
+        oracle.apply_rows(w.N, w.M, h, W, C, rows)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = per_cfg * rows_per_step * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "config-terms/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "N": w.N, "M": w.M, "nc": w.nc},
+        "cpu_baseline": {"value": value, "unit": "config-terms/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{rows_per_step} random rows of sigma per step (row form of the oracle), "
+                                   f"{per_cfg:.1f} config-terms per configuration"},
+        "e2e": {"value": value, "unit": "config-terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def terms_formula(w, h, W):
+    """Configuration terms of one apply (same definition as fock_hamiltonian_terms)."""
+    import numpy as np
+    N, M = w.N, w.M
+    nc = lambda n: math.comb(n + M - 1, M - 1) if n >= 0 else 0
+    P = M * (M + 1) // 2
+    idx = {}
+    for k in range(M):
+        for q in range(k, M):
+            idx[(k, q)] = len(idx)
+    R = np.zeros((P, P), dtype=np.complex128)
+    if W is not None:
+        for k in range(M):
+            for q in range(M):
+                for s in range(M):
+                    for l in range(M):
+                        R[idx[(min(k, q), max(k, q))], idx[(min(s, l), max(s, l))]] += W[k, q, s, l]
+    offh = int(np.count_nonzero(h - np.diag(np.diag(h))))
+    return nc(N) + nc(N - 1) * offh + (nc(N - 2) * int(np.count_nonzero(R)) if N >= 2 else 0)
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def time_steps(torch, fn, steps, warmup, barrier):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    barrier()
+    return e0.elapsed_time(e1) / steps
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="generic_n100_m6")
+    ap.add_argument("--precision", default="f64", choices=list(PREC))
+    ap.add_argument("--extras", type=int, default=1, help="also time the other precisions and forms")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    from paper_2005_13679_gb300 import inputs
+    w = inputs.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import numpy as np
+    import torch
+
+    from paper_2005_13679_gb300 import fock
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        barrier = lambda: dist.barrier()
+    else:
+        torch.cuda.set_device(0)
+        barrier = lambda: None
+    fock.load()
+    peaks, peak_src = load_peaks()
+
+    h, W = w.hamiltonian()
+    sp = fock.Space(w.N, w.M)
+    H = fock.Hamiltonian(sp, h, W)
+    prec = PREC[args.precision]
+    Cn = w.state()
+    Cd = torch.from_numpy(Cn).cuda()
+    if prec == 2:
+        Cd = Cd.to(torch.complex64)
+    sig = torch.empty_like(Cd)
+    wsz = fock.fock_apply_workspace_size(sp.handle, H.handle, w.nrhs, prec)
+    wsb = torch.empty(max(wsz, 16), dtype=torch.uint8, device="cuda")
+
+    def step():
+        fock.fock_apply_H(sp.handle, H.handle, Cd, sig, w.nrhs, prec, fock.FOCK_ARM_AUTO, wsb)
+
+    clk = ClockSampler(local)
+    clk.start()
+    ms = time_steps(torch, step, args.steps, args.warmup, barrier)
+    clocks = clk.stop()
+    ms_all = ms
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_all = t.item()
+    terms = H.terms * w.nrhs
+    value = terms * ws / (ms_all * 1e-3)
+    applies = ws * w.nrhs / (ms_all * 1e-3)
+
+    # end to end through the host-buffer entry point (pinned buffers)
+    elem = 8 if prec == 2 else 16
+    Ch = (torch.from_numpy(Cn).to(torch.complex64) if prec == 2 else torch.from_numpy(Cn)).pin_memory()
+    Sh = torch.empty_like(Ch).pin_memory()
+
+    def e2e_step():
+        fock.fock_apply_H_host(sp.handle, H.handle, Ch, Sh, w.nrhs, prec, fock.FOCK_ARM_AUTO)
+
+    e2e_ms = time_steps(torch, e2e_step, max(3, args.steps // 4), 1, barrier)
+    del Ch, Sh
+
+    nbytes = w.nc * w.nrhs * elem
+    hbm_gbs = 2 * nbytes / (ms * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": "config-terms/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE[args.precision], "data": "synthetic",
+        "config": {"workload": w.name, "N": w.N, "M": w.M, "nc": w.nc, "nrhs": w.nrhs,
+                   "precision": args.precision, "arm": "hash", "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"replicas x{ws}"},
+        "applies_per_s": applies,
+        "config_terms_per_apply": terms,
+        "gpu_launches": (3 if prec == 0 else 1) * args.steps,
+        "hbm": {"compulsory_bytes": 2 * nbytes, "achieved_gbs": hbm_gbs, "peak_gbs": peaks["hbm_gbs"],
+                "frac": hbm_gbs / peaks["hbm_gbs"], "peak_source": peak_src},
+        "e2e": {"value": terms / (e2e_ms * 1e-3), "unit": "config-terms/s",
+                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms},
+        "clocks": clocks,
+    }
+    if rank == 0 and args.extras:
+        extras = {}
+        for name, p in PREC.items():
+            if p == prec:
+                continue
+            X = torch.from_numpy(Cn).cuda()
+            if p == 2:
+                X = X.to(torch.complex64)
+            Y = torch.empty_like(X)
+            steps = 2 if p == 1 else max(3, args.steps // 2)
+            t = time_steps(torch, lambda: fock.fock_apply_H(sp.handle, H.handle, X, Y, w.nrhs, p,
+                                                              fock.FOCK_ARM_AUTO, wsb), steps, 1, lambda: None)
+            extras[name] = {"ms_per_step": t, "config_terms_per_s": terms / (t * 1e-3)}
+            del X, Y
+        out["other_precisions"] = extras
+        n, dt = oracle_rate(w, h, W, Cn if w.nrhs == 1 else Cn[:, 0].copy(), args.cpu_seconds)
+        per_cfg = H.terms / w.nc
+        out["cpu_baseline"] = {"value": per_cfg * n / dt, "unit": "config-terms/s", "cores": 1,
+                               "kind": "oracle", "sample": f"{n} random rows of sigma (row form), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

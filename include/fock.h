@@ -1,0 +1,229 @@
+/*
+ * fock.h -- C ABI of the GB300 library for the bosonic Fock-space hot path of
+ * Andriati & Gammal, "Hashing algorithms, optimized mappings and massive
+ * parallelization of multiconfigurational methods for bosons"
+ * (arXiv:2005.13679).
+ *
+ * The library computes, on one GPU, the action sigma = H C of the many-body
+ * Hamiltonian (Eq. Haction)
+ *
+ *     H = sum_{kl} h_kl a^dag_k a_l + 1/2 sum_{kqsl} W_kqsl a^dag_k a^dag_q a_s a_l
+ *
+ * on coefficient vectors over the Fock basis of N bosons in M orbitals
+ * (Eq. nc, N_c(N, M) = C(N+M-1, M-1) configurations), together with the
+ * configuration hash (Eq. TotalCost, Algorithms 1 and 2), the single- and
+ * double-jump index maps of Sec. 3, and a Lanczos ground-state driver (Sec. 5).
+ *
+ * Conventions used by every entry point:
+ *   - orbitals are numbered 0..M-1, an occupation vector is int32 n[0..M-1]
+ *     with sum N;
+ *   - configuration indices are int64 and follow Algorithm 1: index 0 has all
+ *     particles in orbital 0, index N_c - 1 has them all in orbital M - 1;
+ *   - complex numbers are interleaved (re, im); h is row-major [M][M]
+ *     (h[k*M+l] multiplies a^dag_k a_l), W is row-major [M][M][M][M]
+ *     (W[((k*M+q)*M+s)*M+l] multiplies 1/2 a^dag_k a^dag_q a_s a_l);
+ *   - "_dev" pointers are CUDA device pointers owned by the caller; "_host"
+ *     pointers are host pointers owned by the caller;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream);
+ *     calls are asynchronous on it unless stated otherwise;
+ *   - every call returns an int status: FOCK_OK (0) or a negative FOCK_ERR_*
+ *     code; fock_strerror() names it.  No call aborts the process, and on error
+ *     no output is guaranteed unless the call says so.
+ *
+ * Ownership: fock_space and fock_ham objects are created and destroyed by the
+ * library and bound to the CUDA device that was current at creation; they may
+ * be shared by threads for read-only calls (rank, unrank, apply) but not
+ * destroyed while a call on them is running.
+ */
+#ifndef FOCK_H
+#define FOCK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------- */
+/* Status codes                                                              */
+/* ------------------------------------------------------------------------- */
+#define FOCK_OK                  0
+#define FOCK_ERR_ARG            -1   /* null pointer, size or enum out of range  */
+#define FOCK_ERR_OVERFLOW       -2   /* N_c(N, M) >= 2^63                         */
+#define FOCK_ERR_INVALID_CONFIG -3   /* an occupation vector is not in H(N, M)   */
+#define FOCK_ERR_RANGE          -4   /* an index is outside [0, N_c)             */
+#define FOCK_ERR_NOMEM          -5   /* a device allocation failed / won't fit   */
+#define FOCK_ERR_NOT_HERMITIAN  -6   /* h or the two-body operator not Hermitian */
+#define FOCK_ERR_ALIAS          -7   /* input and output buffers overlap         */
+#define FOCK_ERR_CUDA           -8   /* a CUDA runtime call failed               */
+#define FOCK_ERR_NOCONV         -9   /* Lanczos stopped before the tolerance     */
+#define FOCK_ERR_UNSUPPORTED   -10   /* combination not provided by this build   */
+#define FOCK_ERR_TIMEOUT       -11   /* a bounded device wait gave up            */
+#define FOCK_ERR_NOT_BUILT     -12   /* jump maps requested but not built        */
+#define FOCK_ERR_DEVICE        -13   /* object used on another device            */
+
+/* Human-readable name of a status code (static storage, never NULL). */
+const char *fock_strerror(int status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int fock_version(void);
+
+/* ------------------------------------------------------------------------- */
+/* Configuration space H(N, M)  (Eq. nc; Sec. 2)                             */
+/* ------------------------------------------------------------------------- */
+typedef struct fock_space fock_space;
+
+/* Create the space of N >= 1 bosons in 1 <= M <= 12 orbitals on the current
+ * device: computes N_c(N, M) (Eq. nc) exactly and uploads the binomial tables
+ * used by the hash (Eq. TotalCost).  Fails with FOCK_ERR_OVERFLOW when
+ * N_c >= 2^63, FOCK_ERR_ARG for N < 1, M < 1 or M > 12, FOCK_ERR_CUDA or
+ * FOCK_ERR_NOMEM on device errors.  *out is set only on success. */
+int fock_space_create(int32_t N, int32_t M, fock_space **out);
+
+/* Release the space, its tables and any jump maps.  NULL is accepted. */
+int fock_space_destroy(fock_space *sp);
+
+/* N_c(N, M), the number of configurations. */
+int fock_space_size(const fock_space *sp, int64_t *nc);
+
+/* Rank a batch of occupation vectors (Algorithm 1).  occ_dev is
+ * [count][M] int32, idx_dev receives count int64 indices.  Rows that are not
+ * valid configurations (a negative entry or a sum other than N) receive -1
+ * and the call returns FOCK_ERR_INVALID_CONFIG after the whole batch ran.
+ * Synchronous: waits on `stream` to read the validity flag. */
+int fock_rank(const fock_space *sp, const int32_t *occ_dev, int64_t count,
+              int64_t *idx_dev, void *stream);
+
+/* Unrank a batch of indices (Algorithm 2).  idx_dev has count int64 entries,
+ * occ_dev receives [count][M] int32.  An index outside [0, N_c) gives a row
+ * of -1 and FOCK_ERR_RANGE after the whole batch ran.  Synchronous. */
+int fock_unrank(const fock_space *sp, const int64_t *idx_dev, int64_t count,
+                int32_t *occ_dev, void *stream);
+
+/* ------------------------------------------------------------------------- */
+/* Jump maps  (Sec. 3, "Mapping routines"; Fig. 4)                          */
+/* ------------------------------------------------------------------------- */
+#define FOCK_MAP_SINGLE 1   /* one particle k -> l                           */
+#define FOCK_MAP_DOUBLE 2   /* two particles {k, q} -> {s, l}                */
+
+/* Build the jump maps selected by `which` (a mask of FOCK_MAP_*) on the
+ * device, owned by the space.  Layouts, chosen so that consecutive
+ * configurations are consecutive in memory:
+ *   single: int32 J1[(k*M + l) * N_c + gamma] = index of n(gamma) - e_k + e_l,
+ *           or -1 when n_k = 0 (k == l gives gamma itself when n_k >= 1);
+ *   double: int32 J2[(r*P + a) * N_c + gamma], P = M(M+1)/2, where r and a
+ *           number the pairs k <= q in lexicographic order
+ *           (pair(k, q) = k*M - k(k-1)/2 + (q - k)); the entry is the index of
+ *           n(gamma) - e_k - e_q + e_s + e_l for r = (k, q) and a = (s, l), or
+ *           -1 when r cannot be removed (n_k, n_q >= 1, and n_k >= 2 if k == q).
+ * Memory: 4*M*M*N_c bytes (single) and 4*P*P*N_c bytes (double); both need
+ * N_c < 2^31.  With dry_run != 0 nothing is built and *bytes receives the
+ * total; otherwise *bytes (may be NULL) receives the bytes now held.
+ * FOCK_ERR_NOMEM when the maps do not fit in free device memory. */
+int fock_build_jump_maps(fock_space *sp, int which, int dry_run, size_t *bytes, void *stream);
+
+/* Read-only device pointer to a built map (see layouts above), its number of
+ * slots (M*M or P*P) and the slot stride in elements (N_c).
+ * FOCK_ERR_NOT_BUILT if that map is not built. */
+int fock_jump_map_get(const fock_space *sp, int which, const int32_t **map_dev,
+                      int64_t *slots, int64_t *slot_stride);
+
+/* Free the jump maps (the space stays valid). */
+int fock_jump_maps_free(fock_space *sp);
+
+/* ------------------------------------------------------------------------- */
+/* Hamiltonian  (Eqs. noninteracting, interacting; Sec. 1)                   */
+/* ------------------------------------------------------------------------- */
+typedef struct fock_ham fock_ham;
+
+/* Stage h ([M][M] complex, interleaved) and W ([M]^4 complex, or NULL for a
+ * one-body operator) for the space.  The two-body operator depends only on the
+ * multisets {k, q} and {s, l}, so W is reduced to one coefficient per pair of
+ * multisets (summing the orderings); for N >= 2 the one-body term is folded
+ * into that reduced two-body form through sum_x a^dag_k a^dag_x a_x a_l =
+ * (N - 1) a^dag_k a_l on H(N, M).  When tol >= 0 the call checks that h and
+ * the reduced two-body operator are Hermitian to within tol times the largest
+ * coefficient and returns FOCK_ERR_NOT_HERMITIAN otherwise; tol < 0 skips the
+ * check (the apply is defined for any coefficients).  Host buffers are
+ * copied; the caller keeps ownership. */
+int fock_hamiltonian_create(const fock_space *sp, const double *h_host,
+                            const double *W_host, double tol, fock_ham **out);
+
+/* Release a Hamiltonian and its device workspace.  NULL is accepted. */
+int fock_hamiltonian_destroy(fock_ham *ham);
+
+/* Operation count of one apply, in "configuration terms": the number of
+ * (configuration, operator-string) pairs with a nonzero coefficient,
+ *   N_c + N_c(N-1, M) * #{k != l : h_kl != 0}
+ *       + N_c(N-2, M) * #{(r, a) : reduced two-body coefficient != 0},
+ * independent of the implementation (the throughput metric's numerator). */
+int fock_hamiltonian_terms(const fock_ham *ham, int64_t *config_terms);
+
+/* Nonzero 1 if every coefficient is real (imaginary parts all zero). */
+int fock_hamiltonian_is_real(const fock_ham *ham, int *is_real);
+
+/* ------------------------------------------------------------------------- */
+/* sigma = H C  (Eq. Haction)                                                */
+/* ------------------------------------------------------------------------- */
+/* precision */
+#define FOCK_PREC_F64        0  /* complex128 in/out; result within 1e-13 of
+                                   exact (normwise); FP32-pair arithmetic     */
+#define FOCK_PREC_F64_NATIVE 1  /* complex128 in/out; native FP64 arithmetic */
+#define FOCK_PREC_F32_MIXED  2  /* complex64 in/out; FP32 products, FP32-pair
+                                   accumulation per configuration             */
+/* arm */
+#define FOCK_ARM_AUTO 0         /* library's choice                            */
+#define FOCK_ARM_HASH 1         /* target indices from the hash on the fly    */
+#define FOCK_ARM_MAPS 2         /* target indices from the built jump maps    */
+
+/* Device workspace (bytes) an apply with these options needs; 0 if none. */
+int fock_apply_workspace_size(const fock_space *sp, const fock_ham *ham, int32_t nrhs,
+                              int precision, size_t *bytes);
+
+/* sigma = H C for nrhs vectors stored [N_c][nrhs] (configuration-major, the
+ * nrhs values of one configuration adjacent), complex128 for FOCK_PREC_F64*
+ * and complex64 for FOCK_PREC_F32_MIXED.  1 <= nrhs <= 16.  C_dev and
+ * sigma_dev must not overlap (FOCK_ERR_ALIAS).  Each sigma_gamma is computed
+ * by one thread from the configurations reached by removing one or two
+ * particles from gamma and adding them back (pull form), so no atomics are
+ * used and results are deterministic.  workspace_dev may be NULL, in which
+ * case a buffer owned by `ham` is allocated on first use (grown when needed);
+ * otherwise it must hold fock_apply_workspace_size() bytes.  Asynchronous on
+ * `stream`.  FOCK_ERR_NOT_BUILT for FOCK_ARM_MAPS without the maps. */
+int fock_apply_H(const fock_space *sp, const fock_ham *ham, const void *C_dev,
+                 void *sigma_dev, int32_t nrhs, int precision, int arm,
+                 void *workspace_dev, size_t workspace_bytes, void *stream);
+
+/* Same as fock_apply_H with host buffers: copies C_host to the device, applies
+ * and copies sigma back into sigma_host, then waits on `stream`.  Device
+ * buffers are owned by `ham` and reused across calls.  For pinned (page-locked)
+ * host memory the copies run at full link speed. */
+int fock_apply_H_host(const fock_space *sp, const fock_ham *ham, const void *C_host,
+                      void *sigma_host, int32_t nrhs, int precision, int arm, void *stream);
+
+/* ------------------------------------------------------------------------- */
+/* Lanczos ground state  (Sec. 5)                                            */
+/* ------------------------------------------------------------------------- */
+/* Lowest eigenvalue of H by Lanczos with full re-orthogonalisation inside
+ * restart cycles of restart_len vectors (explicit restart from the current
+ * Ritz vector).  Krylov vectors and all orthogonalisation are FP64 (real when
+ * the Hamiltonian is real, complex otherwise); the H C products use
+ * `precision`; the returned E0 is the FP64 Rayleigh quotient of the final
+ * unit vector with a FOCK_PREC_F64 apply, and *residual (may be NULL) is
+ * ||H v - E0 v|| for it.  Stops when the residual estimate is below
+ * tol * max(|E0|, 1) or after max_iter products.  start_dev (may be NULL) is
+ * an N_c complex128 start vector; otherwise one is drawn from `seed` with the
+ * SplitMix64 generator.  vec_dev (may be NULL) receives the unit ground vector
+ * as N_c complex128.  Synchronous.  Returns FOCK_ERR_NOCONV with the best E0
+ * when max_iter is reached first. */
+int fock_lanczos_ground(const fock_space *sp, const fock_ham *ham, int32_t max_iter,
+                        int32_t restart_len, double tol, uint64_t seed, int precision,
+                        const void *start_dev, double *E0, double *residual,
+                        void *vec_dev, int32_t *iters, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FOCK_H */

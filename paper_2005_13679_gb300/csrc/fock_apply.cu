@@ -1,0 +1,487 @@
+// fock_apply.cu -- Hamiltonian staging and the sigma = H C entry points.
+//
+// Staging (Eqs. noninteracting and interacting): the operator string
+// a^dag_k a^dag_q a_s a_l depends only on the multisets r = {k, q} and
+// a = {s, l}, so W is reduced to R[r][a] = 1/2 sum over the orderings of W.
+// For N >= 2 the one-body part is folded in through
+//     sum_x a^dag_k a^dag_x a_x a_l = (N - 1) a^dag_k a_l    on H(N, M),
+// i.e. R[{k,x}][{x,l}] += h_kl / (N - 1) for every ordering with a shared x,
+// so one two-body pass computes the whole of sigma (the folded terms land on
+// targets the two-body pass visits anyway).  Without W, or for N = 1, the
+// one-body list (removal k, addition l, coefficient h_kl) is used instead.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <complex>
+#include <vector>
+
+#include "fock_apply_kernel.cuh"
+
+int fock_launch_apply_f64(const void *, bool, int, bool, bool, int, cudaStream_t);
+int fock_launch_apply_df(const void *, bool, int, bool, bool, int, cudaStream_t);
+int fock_launch_apply_mixed(const void *, bool, int, bool, bool, int, cudaStream_t);
+
+typedef std::complex<double> cplx;
+
+static int64_t count_nm(int64_t n, int64_t m) {
+  if (m <= 0 || n < 0) return 0;
+  unsigned __int128 r = 1;
+  for (int64_t i = 1; i <= m - 1; ++i) r = r * (unsigned __int128)(n + i) / (unsigned __int128)i;
+  return r > (unsigned __int128)INT64_MAX ? INT64_MAX : (int64_t)r;
+}
+
+static void split_float(double x, float &hi, float &lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+static void free_ham(fock_ham *h) {
+  if (!h) return;
+  free(h->h_rem);
+  free(h->h_add);
+  free(h->h_coef);
+  cudaFree(h->d_rem);
+  cudaFree(h->d_add);
+  cudaFree(h->d_coef64);
+  cudaFree(h->d_coefdf);
+  cudaFree(h->d_coef32);
+  cudaFree(h->d_sqrt64);
+  cudaFree(h->d_sqrtdf);
+  cudaFree(h->d_sqrt32);
+  cudaFree(h->ws);
+  cudaFree(h->hb_in);
+  cudaFree(h->hb_out);
+  free(h);
+}
+
+extern "C" int fock_hamiltonian_destroy(fock_ham *ham) {
+  free_ham(ham);
+  return FOCK_OK;
+}
+
+template <class T>
+static int upload(T **dst, const T *src, size_t n) {
+  if (n == 0) n = 1;
+  FOCK_CUDA_TRY(cudaMalloc(dst, n * sizeof(T)));
+  FOCK_CUDA_TRY(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+  return FOCK_OK;
+}
+
+extern "C" int fock_hamiltonian_create(const fock_space *sp, const double *h_host,
+                                       const double *W_host, double tol, fock_ham **out) {
+  if (!sp || !h_host || !out) return FOCK_ERR_ARG;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return FOCK_ERR_CUDA;
+  if (cur != sp->device) return FOCK_ERR_DEVICE;
+  const int N = sp->N, M = sp->M, P = fock_pair_count(M);
+  for (size_t i = 0; i < (size_t)2 * M * M; ++i)
+    if (!isfinite(h_host[i])) return FOCK_ERR_ARG;
+  if (W_host)
+    for (size_t i = 0; i < (size_t)2 * M * M * M * M; ++i)
+      if (!isfinite(W_host[i])) return FOCK_ERR_ARG;
+
+  auto hk = [&](int k, int l) { return cplx(h_host[2 * (k * M + l)], h_host[2 * (k * M + l) + 1]); };
+  const bool two_body = W_host != nullptr && N >= 2;
+
+  // Reduced two-body coefficients (without and with the folded one-body part).
+  std::vector<cplx> RW((size_t)P * P, 0.0), R((size_t)P * P, 0.0);
+  if (W_host) {
+    for (int k = 0; k < M; ++k)
+      for (int q = 0; q < M; ++q)
+        for (int s = 0; s < M; ++s)
+          for (int l = 0; l < M; ++l) {
+            size_t w = (((size_t)k * M + q) * M + s) * M + l;
+            cplx v(W_host[2 * w], W_host[2 * w + 1]);
+            int r = fock_pair_index(M, k < q ? k : q, k < q ? q : k);
+            int a = fock_pair_index(M, s < l ? s : l, s < l ? l : s);
+            RW[(size_t)r * P + a] += 0.5 * v;
+          }
+  }
+
+  // Hermiticity: h = h^dag and R[r][a] = conj(R[a][r]).
+  double hmax = 0.0, wmax = 0.0;
+  for (int k = 0; k < M; ++k)
+    for (int l = 0; l < M; ++l) hmax = fmax(hmax, std::abs(hk(k, l)));
+  for (auto &v : RW) wmax = fmax(wmax, std::abs(v));
+  if (tol >= 0.0) {
+    const double ref = fmax(fmax(hmax, wmax), 1e-300);
+    for (int k = 0; k < M; ++k)
+      for (int l = 0; l < M; ++l)
+        if (std::abs(hk(k, l) - std::conj(hk(l, k))) > tol * ref) return FOCK_ERR_NOT_HERMITIAN;
+    if (two_body)
+      for (int r = 0; r < P; ++r)
+        for (int a = 0; a < P; ++a)
+          if (std::abs(RW[(size_t)r * P + a] - std::conj(RW[(size_t)a * P + r])) > tol * ref)
+            return FOCK_ERR_NOT_HERMITIAN;
+  }
+
+  fock_ham *H = (fock_ham *)calloc(1, sizeof(fock_ham));
+  if (!H) return FOCK_ERR_NOMEM;
+  H->sp = sp;
+  H->device = sp->device;
+
+  std::vector<FockRemoval> rem;
+  std::vector<FockAddition> add;
+  std::vector<cplx> coef;
+  if (two_body) {
+    R = RW;
+    for (int k = 0; k < M; ++k)
+      for (int x = 0; x < M; ++x)
+        for (int l = 0; l < M; ++l) {
+          cplx v = hk(k, l);
+          if (v == 0.0) continue;
+          // ordered tuple (k, x, x, l): a^dag_k a^dag_x a_x a_l
+          int r = fock_pair_index(M, k < x ? k : x, k < x ? x : k);
+          int a = fock_pair_index(M, x < l ? x : l, x < l ? l : x);
+          R[(size_t)r * P + a] += v / (double)(N - 1);
+        }
+    int r = 0;
+    for (int k = 0; k < M; ++k)
+      for (int q = k; q < M; ++q, ++r) {
+        FockRemoval e;
+        e.k = (int8_t)k; e.q = (int8_t)q; e.size = 2; e.pad = 0;
+        e.a_beg = (int32_t)add.size();
+        e.slot_base = r * P;
+        int a = 0;
+        for (int s = 0; s < M; ++s)
+          for (int l = s; l < M; ++l, ++a) {
+            cplx v = R[(size_t)r * P + a];
+            if (v == 0.0) continue;
+            FockAddition d;
+            d.s = (int8_t)s; d.l = (int8_t)l; d.a_index = (int16_t)a;
+            add.push_back(d);
+            coef.push_back(v);
+          }
+        e.a_end = (int32_t)add.size();
+        if (e.a_end > e.a_beg) rem.push_back(e);
+      }
+  } else {
+    for (int k = 0; k < M; ++k) {
+      FockRemoval e;
+      e.k = (int8_t)k; e.q = -1; e.size = 1; e.pad = 0;
+      e.a_beg = (int32_t)add.size();
+      e.slot_base = k * M;
+      for (int l = 0; l < M; ++l) {
+        cplx v = hk(k, l);
+        if (v == 0.0) continue;
+        FockAddition d;
+        d.s = -1; d.l = (int8_t)l; d.a_index = (int16_t)l;
+        add.push_back(d);
+        coef.push_back(v);
+      }
+      e.a_end = (int32_t)add.size();
+      if (e.a_end > e.a_beg) rem.push_back(e);
+    }
+  }
+
+  // Operation count (implementation independent).
+  int64_t off_h = 0;
+  for (int k = 0; k < M; ++k)
+    for (int l = 0; l < M; ++l)
+      if (k != l && hk(k, l) != 0.0) off_h += 1;
+  int64_t nz_w = 0;
+  for (auto &v : RW)
+    if (v != 0.0) nz_w += 1;
+  H->config_terms = sp->nc + count_nm(N - 1, M) * off_h + (N >= 2 ? count_nm(N - 2, M) * nz_w : 0);
+
+  H->nrem = (int)rem.size();
+  H->nadd = (int)add.size();
+  H->real = true;
+  double cmax = 0.0;
+  for (auto &v : coef) {
+    if (v.imag() != 0.0) H->real = false;
+    cmax = fmax(cmax, std::abs(v));
+  }
+  H->dense = two_body && H->nadd == P * P;
+  H->max_abs_coef = cmax;
+  H->coef_scale = cmax > 0.0 ? ldexp(1.0, ilogb(cmax) + 1) : 1.0;
+
+  // Host copies and device uploads.
+  const size_t nadd = add.size();
+  std::vector<double2> c64(nadd);
+  std::vector<float4> cdf(nadd);
+  std::vector<float2> c32(nadd);
+  for (size_t i = 0; i < nadd; ++i) {
+    c64[i] = make_double2(coef[i].real(), coef[i].imag());
+    float rh, rl, ih, il;
+    split_float(coef[i].real() / H->coef_scale, rh, rl);
+    split_float(coef[i].imag() / H->coef_scale, ih, il);
+    cdf[i] = make_float4(rh, ih, rl, il);
+    c32[i] = make_float2((float)coef[i].real(), (float)coef[i].imag());
+  }
+  const int nsq = N + 4;
+  std::vector<double> s64(nsq);
+  std::vector<float2> sdf(nsq);
+  std::vector<float> s32(nsq);
+  for (int i = 0; i < nsq; ++i) {
+    s64[i] = sqrt((double)i);
+    float hi, lo;
+    split_float(s64[i], hi, lo);
+    sdf[i] = make_float2(hi, lo);
+    s32[i] = (float)s64[i];
+  }
+  H->h_rem = (FockRemoval *)malloc(sizeof(FockRemoval) * (rem.size() + 1));
+  H->h_add = (FockAddition *)malloc(sizeof(FockAddition) * (nadd + 1));
+  H->h_coef = (double *)malloc(sizeof(double) * 2 * (nadd + 1));
+  if (!H->h_rem || !H->h_add || !H->h_coef) {
+    free_ham(H);
+    return FOCK_ERR_NOMEM;
+  }
+  if (!rem.empty()) memcpy(H->h_rem, rem.data(), sizeof(FockRemoval) * rem.size());
+  if (nadd) memcpy(H->h_add, add.data(), sizeof(FockAddition) * nadd);
+  for (size_t i = 0; i < nadd; ++i) {
+    H->h_coef[2 * i] = coef[i].real();
+    H->h_coef[2 * i + 1] = coef[i].imag();
+  }
+  int st = FOCK_OK;
+  if (!st) st = upload(&H->d_rem, rem.data(), rem.size());
+  if (!st) st = upload(&H->d_add, add.data(), nadd);
+  if (!st) st = upload(&H->d_coef64, c64.data(), nadd);
+  if (!st) st = upload(&H->d_coefdf, cdf.data(), nadd);
+  if (!st) st = upload(&H->d_coef32, c32.data(), nadd);
+  if (!st) st = upload(&H->d_sqrt64, s64.data(), (size_t)nsq);
+  if (!st) st = upload(&H->d_sqrtdf, sdf.data(), (size_t)nsq);
+  if (!st) st = upload(&H->d_sqrt32, s32.data(), (size_t)nsq);
+  if (st) {
+    free_ham(H);
+    return st;
+  }
+  *out = H;
+  return FOCK_OK;
+}
+
+extern "C" int fock_hamiltonian_terms(const fock_ham *ham, int64_t *config_terms) {
+  if (!ham || !config_terms) return FOCK_ERR_ARG;
+  *config_terms = ham->config_terms;
+  return FOCK_OK;
+}
+
+extern "C" int fock_hamiltonian_is_real(const fock_ham *ham, int *is_real) {
+  if (!ham || !is_real) return FOCK_ERR_ARG;
+  *is_real = ham->real ? 1 : 0;
+  return FOCK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// FP32-pair input preparation: exponent of max |C| (one atomicMax of the FP64
+// exponent field), then every entry scaled by 2^-(e) and split into hi + lo.
+// Scaling by a power of two is exact and keeps the pairs inside FP32 range
+// whatever the magnitude of C.
+// ---------------------------------------------------------------------------
+__global__ void fock_max_exponent_kernel(const double *__restrict__ x, int64_t n, int *out) {
+  int best = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(__ldg(x + i));
+    const int e = (int)((bits >> 52) & 0x7ff);
+    best = e > best ? e : best;
+  }
+  for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0 && best > 0) atomicMax(out, best);
+}
+
+// out_exp = e_max - 1023 so that |C| * 2^-out_exp < 2.
+__global__ void fock_split_kernel(const double2 *__restrict__ x, int64_t n, const int *ebits,
+                                  float4 *__restrict__ y, int *out_exp) {
+  const int eb = max(__ldg(ebits), 1);
+  const int sh = 1023 - eb;
+  if (blockIdx.x == 0 && threadIdx.x == 0) out_exp[0] = -sh;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = __ldg(x + i);
+    const double re = ldexp(v.x, sh), im = ldexp(v.y, sh);
+    const float rh = __double2float_rn(re), ih = __double2float_rn(im);
+    const float rl = __double2float_rn(re - (double)rh), il = __double2float_rn(im - (double)ih);
+    y[i] = make_float4(rh, ih, rl, il);
+  }
+}
+
+static const size_t kWsHeader = 256;
+
+size_t fock_apply_ws_bytes(const fock_space *sp, const fock_ham *ham, int nrhs, int precision) {
+  (void)ham;
+  if (precision != FOCK_PREC_F64) return 0;
+  return kWsHeader + (size_t)sp->nc * (size_t)nrhs * sizeof(float4);
+}
+
+extern "C" int fock_apply_workspace_size(const fock_space *sp, const fock_ham *ham, int32_t nrhs,
+                                         int precision, size_t *bytes) {
+  if (!sp || !ham || !bytes || nrhs < 1 || nrhs > FOCK_MAX_NRHS) return FOCK_ERR_ARG;
+  if (precision < FOCK_PREC_F64 || precision > FOCK_PREC_F32_MIXED) return FOCK_ERR_ARG;
+  *bytes = fock_apply_ws_bytes(sp, ham, nrhs, precision);
+  return FOCK_OK;
+}
+
+template <class Idx>
+static void fill_args(ApplyArgs<Idx> &a, const fock_space *sp, const fock_ham *ham, const void *C,
+                      void *sigma, int nrhs, int precision, const int32_t *map, const int *in_exp) {
+  a.N = sp->N;
+  a.M = sp->M;
+  a.nc = (Idx)sp->nc;
+  a.xdim = sp->tab.xdim;
+  a.rows = sp->tab.rows;
+  if (sizeof(Idx) == 4) {
+    a.mod = (const Idx *)sp->tab.mod32;
+    a.sat = (const Idx *)sp->tab.sat32;
+  } else {
+    a.mod = (const Idx *)sp->tab.mod64;
+    a.sat = (const Idx *)sp->tab.sat64;
+  }
+  a.rem = ham->d_rem;
+  a.nrem = ham->nrem;
+  a.add = ham->d_add;
+  a.nsq = sp->N + 4;
+  a.C = C;
+  a.sigma = sigma;
+  a.nrhs = nrhs;
+  a.map = map;
+  a.in_exp = in_exp;
+  a.real = ham->real;
+  switch (precision) {
+    case FOCK_PREC_F64:
+      a.coef = ham->d_coefdf;
+      a.sq = ham->d_sqrtdf;
+      a.out_scale = ham->coef_scale;
+      break;
+    case FOCK_PREC_F64_NATIVE:
+      a.coef = ham->d_coef64;
+      a.sq = ham->d_sqrt64;
+      a.out_scale = 1.0;
+      break;
+    default:
+      a.coef = ham->d_coef32;
+      a.sq = ham->d_sqrt32;
+      a.out_scale = 1.0;
+      break;
+  }
+}
+
+int fock_apply_internal(const fock_space *sp, const fock_ham *ham, const void *C, void *sigma,
+                        int nrhs, int precision, int arm, void *ws, size_t ws_bytes,
+                        cudaStream_t stream) {
+  const size_t elem = precision == FOCK_PREC_F32_MIXED ? 8 : 16;
+  const size_t bytes = (size_t)sp->nc * (size_t)nrhs * elem;
+  const char *c0 = (const char *)C, *s0 = (const char *)sigma;
+  if (c0 < s0 + bytes && s0 < c0 + bytes) return FOCK_ERR_ALIAS;
+  const bool two_body = ham->nrem > 0 && ham->h_rem[0].size == 2;
+  const int32_t *map = nullptr;
+  if (arm == FOCK_ARM_MAPS) {
+    map = two_body ? sp->d_j2 : sp->d_j1;
+    if (!map) return FOCK_ERR_NOT_BUILT;
+  }
+  if (ham->nrem == 0) {
+    FOCK_CUDA_TRY(cudaMemsetAsync(sigma, 0, bytes, stream));
+    return FOCK_OK;
+  }
+  const int maxm = sp->M <= 4 ? 4 : (sp->M <= 8 ? 8 : 12);
+  const bool nrhs16 = nrhs > 1;
+  const int *in_exp = nullptr;
+  const void *Cin = C;
+  if (precision == FOCK_PREC_F64) {
+    const size_t need = fock_apply_ws_bytes(sp, ham, nrhs, precision);
+    if (!ws || ws_bytes < need) return FOCK_ERR_ARG;
+    int *words = (int *)ws;  // [0] exponent bits, [1] output exponent
+    float4 *split = (float4 *)((char *)ws + kWsHeader);
+    const int64_t n = sp->nc * (int64_t)nrhs;
+    FOCK_CUDA_TRY(cudaMemsetAsync(words, 0, 8, stream));
+    const int sms = fock_get_sm_count(sp->device);
+    int64_t blocks = (2 * n + 255) / 256;
+    if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+    fock_max_exponent_kernel<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, stream>>>(
+        (const double *)C, 2 * n, words);
+    blocks = (n + 255) / 256;
+    if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+    fock_split_kernel<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, stream>>>(
+        (const double2 *)C, n, words, split, words + 1);
+    FOCK_CUDA_TRY(cudaGetLastError());
+    in_exp = words + 1;
+    Cin = split;
+  }
+  const bool maps = map != nullptr;
+  if (sp->idx32) {
+    ApplyArgs<uint32_t> a;
+    fill_args(a, sp, ham, Cin, sigma, nrhs, precision, map, in_exp);
+    switch (precision) {
+      case FOCK_PREC_F64: return fock_launch_apply_df(&a, true, maxm, nrhs16, maps, sp->device, stream);
+      case FOCK_PREC_F64_NATIVE: return fock_launch_apply_f64(&a, true, maxm, nrhs16, maps, sp->device, stream);
+      default: return fock_launch_apply_mixed(&a, true, maxm, nrhs16, maps, sp->device, stream);
+    }
+  }
+  ApplyArgs<uint64_t> a;
+  fill_args(a, sp, ham, Cin, sigma, nrhs, precision, map, in_exp);
+  switch (precision) {
+    case FOCK_PREC_F64: return fock_launch_apply_df(&a, false, maxm, nrhs16, maps, sp->device, stream);
+    case FOCK_PREC_F64_NATIVE: return fock_launch_apply_f64(&a, false, maxm, nrhs16, maps, sp->device, stream);
+    default: return fock_launch_apply_mixed(&a, false, maxm, nrhs16, maps, sp->device, stream);
+  }
+}
+
+static int grow_ws(fock_ham *ham, size_t need) {
+  if (ham->ws_bytes >= need) return FOCK_OK;
+  cudaFree(ham->ws);
+  ham->ws = nullptr;
+  ham->ws_bytes = 0;
+  FOCK_CUDA_TRY(cudaMalloc(&ham->ws, need));
+  ham->ws_bytes = need;
+  return FOCK_OK;
+}
+
+static int check_apply_args(const fock_space *sp, const fock_ham *ham, int nrhs, int precision, int arm) {
+  if (!sp || !ham || ham->sp != sp) return FOCK_ERR_ARG;
+  if (nrhs < 1 || nrhs > FOCK_MAX_NRHS) return FOCK_ERR_ARG;
+  if (precision < FOCK_PREC_F64 || precision > FOCK_PREC_F32_MIXED) return FOCK_ERR_ARG;
+  if (arm < FOCK_ARM_AUTO || arm > FOCK_ARM_MAPS) return FOCK_ERR_ARG;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return FOCK_ERR_CUDA;
+  if (cur != sp->device) return FOCK_ERR_DEVICE;
+  return FOCK_OK;
+}
+
+extern "C" int fock_apply_H(const fock_space *sp, const fock_ham *ham, const void *C_dev,
+                            void *sigma_dev, int32_t nrhs, int precision, int arm,
+                            void *workspace_dev, size_t workspace_bytes, void *stream) {
+  int st = check_apply_args(sp, ham, nrhs, precision, arm);
+  if (st) return st;
+  if (!C_dev || !sigma_dev) return FOCK_ERR_ARG;
+  const size_t need = fock_apply_ws_bytes(sp, ham, nrhs, precision);
+  if (need > 0 && !workspace_dev) {
+    st = grow_ws((fock_ham *)ham, need);
+    if (st) return st;
+    workspace_dev = ham->ws;
+    workspace_bytes = ham->ws_bytes;
+  }
+  return fock_apply_internal(sp, ham, C_dev, sigma_dev, nrhs, precision, arm, workspace_dev,
+                             workspace_bytes, (cudaStream_t)stream);
+}
+
+extern "C" int fock_apply_H_host(const fock_space *sp, const fock_ham *ham, const void *C_host,
+                                 void *sigma_host, int32_t nrhs, int precision, int arm, void *stream) {
+  int st = check_apply_args(sp, ham, nrhs, precision, arm);
+  if (st) return st;
+  if (!C_host || !sigma_host) return FOCK_ERR_ARG;
+  fock_ham *H = (fock_ham *)ham;
+  const size_t elem = precision == FOCK_PREC_F32_MIXED ? 8 : 16;
+  const size_t bytes = (size_t)sp->nc * (size_t)nrhs * elem;
+  if (H->hb_bytes < bytes) {
+    cudaFree(H->hb_in);
+    cudaFree(H->hb_out);
+    H->hb_in = H->hb_out = nullptr;
+    H->hb_bytes = 0;
+    FOCK_CUDA_TRY(cudaMalloc(&H->hb_in, bytes));
+    FOCK_CUDA_TRY(cudaMalloc(&H->hb_out, bytes));
+    H->hb_bytes = bytes;
+  }
+  const size_t need = fock_apply_ws_bytes(sp, ham, nrhs, precision);
+  if (need > 0) {
+    st = grow_ws(H, need);
+    if (st) return st;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  FOCK_CUDA_TRY(cudaMemcpyAsync(H->hb_in, C_host, bytes, cudaMemcpyHostToDevice, s));
+  st = fock_apply_internal(sp, ham, H->hb_in, H->hb_out, nrhs, precision, arm, H->ws, H->ws_bytes, s);
+  if (st) return st;
+  FOCK_CUDA_TRY(cudaMemcpyAsync(sigma_host, H->hb_out, bytes, cudaMemcpyDeviceToHost, s));
+  FOCK_CUDA_TRY(cudaStreamSynchronize(s));
+  return FOCK_OK;
+}

@@ -1,0 +1,144 @@
+// fock_arith.cuh -- arithmetic policies of the H C kernels.
+//
+// GB300 executes FP64 FMAs at about 1/74 of the FP32 rate (measured 1.0 versus
+// 74 TFLOP/s), so the FP64-accurate apply runs on the FP32 pipes with values
+// held as unevaluated sums of two floats, hi + lo (Dekker's product with FMA,
+// Knuth's TwoSum; 48-bit significands), and only the final conversion uses
+// FP64 instructions.  Error-free transformations use the _rn intrinsics so the
+// compiler cannot contract a rounded product into a following addition.
+//
+//   PolF64   : complex128 storage, native FP64 FMA arithmetic (reference arm)
+//   PolDF    : complex128 storage (pre-split into float hi/lo), FP32-pair arithmetic
+//   PolMixed : complex64 storage, FP32 products and partial sums, FP32-pair
+//              accumulation per configuration
+#pragma once
+
+#include <cuda_runtime.h>
+
+// ---- FP32-pair primitives --------------------------------------------------
+// (h, l) += a * b with a = (ah, al), b = (bh, bl).  The product's high part
+// p = fl(ah*bh) and its rounding error come from one FMA; the cross terms
+// ah*bl + al*bh are added in FP32 (their error is below 2^-46 relative); the
+// sum h + p is split exactly by TwoSum and the error joins the low word.
+__device__ __forceinline__ void df_prod_acc(float &h, float &l, float ah, float al, float bh, float bl) {
+  float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  float s = __fadd_rn(h, p);
+  float bb = __fsub_rn(s, h);
+  float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  h = s;
+  l = __fadd_rn(l, __fadd_rn(err, e));
+}
+
+// (h, l) += (bh, bl)
+__device__ __forceinline__ void df_add_acc(float &h, float &l, float bh, float bl) {
+  float s = __fadd_rn(h, bh);
+  float bb = __fsub_rn(s, h);
+  float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+  h = s;
+  l = __fadd_rn(l, __fadd_rn(err, bl));
+}
+
+// Normalised product of two pairs.
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  float s = __fadd_rn(p, e);
+  return make_float2(s, __fsub_rn(e, __fsub_rn(s, p)));
+}
+
+// ---- native FP64 -----------------------------------------------------------
+struct PolF64 {
+  using vec_t = double2;   // one complex element of C / sigma
+  using amp_t = double;    // real amplitude (square-root products)
+  using coef_t = double2;  // complex coefficient
+  using acc_t = double2;
+  using inner_t = double2;
+  static constexpr bool kInner = false;
+
+  static __device__ __forceinline__ amp_t amul(amp_t a, amp_t b) { return a * b; }
+  static __device__ __forceinline__ void zero(acc_t &a) { a = make_double2(0.0, 0.0); }
+  static __device__ __forceinline__ coef_t scale(coef_t c, amp_t x) { return make_double2(c.x * x, c.y * x); }
+  static __device__ __forceinline__ void mac(acc_t &a, coef_t k, vec_t v, bool real) {
+    a.x = fma(k.x, v.x, a.x);
+    a.y = fma(k.x, v.y, a.y);
+    if (!real) {
+      a.x = fma(-k.y, v.y, a.x);
+      a.y = fma(k.y, v.x, a.y);
+    }
+  }
+  static __device__ __forceinline__ void flush(acc_t &a, const inner_t &i) { a.x += i.x; a.y += i.y; }
+  static __device__ __forceinline__ vec_t finish(const acc_t &a, double scale) {
+    return make_double2(a.x * scale, a.y * scale);
+  }
+};
+
+// ---- FP32 pairs ------------------------------------------------------------
+struct PolDF {
+  using vec_t = float4;    // (re_hi, im_hi, re_lo, im_lo), pre-split copy of C
+  using amp_t = float2;    // (hi, lo)
+  using coef_t = float4;   // (re_hi, im_hi, re_lo, im_lo)
+  using acc_t = float4;    // (re_hi, re_lo, im_hi, im_lo), low words not renormalised
+  using inner_t = float4;
+  static constexpr bool kInner = false;
+
+  static __device__ __forceinline__ amp_t amul(amp_t a, amp_t b) { return df_mul(a, b); }
+  static __device__ __forceinline__ void zero(acc_t &a) { a = make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ coef_t scale(coef_t c, amp_t x) {
+    float2 re = df_mul(make_float2(c.x, c.z), x);
+    float2 im = df_mul(make_float2(c.y, c.w), x);
+    return make_float4(re.x, im.x, re.y, im.y);
+  }
+  static __device__ __forceinline__ void mac(acc_t &a, coef_t k, vec_t v, bool real) {
+    df_prod_acc(a.x, a.y, k.x, k.z, v.x, v.z);        // + Re k Re v
+    df_prod_acc(a.z, a.w, k.x, k.z, v.y, v.w);        // + Re k Im v
+    if (!real) {
+      df_prod_acc(a.x, a.y, -k.y, -k.w, v.y, v.w);    // - Im k Im v
+      df_prod_acc(a.z, a.w, k.y, k.w, v.x, v.z);      // + Im k Re v
+    }
+  }
+  static __device__ __forceinline__ void flush(acc_t &a, const inner_t &i) {
+    df_add_acc(a.x, a.y, i.x, i.y);
+    df_add_acc(a.z, a.w, i.z, i.w);
+  }
+  // value = (hi + lo) * scale, in FP64 (two conversions and one add per part)
+  static __device__ __forceinline__ double2 finish(const acc_t &a, double scale) {
+    return make_double2(((double)a.x + (double)a.y) * scale, ((double)a.z + (double)a.w) * scale);
+  }
+};
+
+// ---- FP32 storage, FP32-pair accumulation ----------------------------------
+struct PolMixed {
+  using vec_t = float2;
+  using amp_t = float;
+  using coef_t = float2;
+  using acc_t = float4;    // (re_hi, re_lo, im_hi, im_lo)
+  using inner_t = float2;  // FP32 partial sum over the additions of one removal
+  static constexpr bool kInner = true;
+
+  static __device__ __forceinline__ amp_t amul(amp_t a, amp_t b) { return a * b; }
+  static __device__ __forceinline__ void zero(acc_t &a) { a = make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ void izero(inner_t &a) { a = make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ coef_t scale(coef_t c, amp_t x) { return make_float2(c.x * x, c.y * x); }
+  static __device__ __forceinline__ void imac(inner_t &a, coef_t k, vec_t v, bool real) {
+    a.x = fmaf(k.x, v.x, a.x);
+    a.y = fmaf(k.x, v.y, a.y);
+    if (!real) {
+      a.x = fmaf(-k.y, v.y, a.x);
+      a.y = fmaf(k.y, v.x, a.y);
+    }
+  }
+  static __device__ __forceinline__ void flush(acc_t &a, const inner_t &i) {
+    df_add_acc(a.x, a.y, i.x, 0.f);
+    df_add_acc(a.z, a.w, i.y, 0.f);
+  }
+  // FP32 result: no FP64 instruction on this path.
+  static __device__ __forceinline__ float2 finish(const acc_t &a, double scale) {
+    const float f = (float)scale;
+    return make_float2(__fadd_rn(a.x, a.y) * f, __fadd_rn(a.z, a.w) * f);
+  }
+};

@@ -1,0 +1,48 @@
+// fock_device.cuh -- device helpers of libfock: decode (unrank) and rank with
+// the binomial tables of a space.  See fock_common.cuh for the closed form of
+// the hash these implement.
+#pragma once
+
+#include "fock_common.cuh"
+
+// Greedy decoding of the combinatorial-number-system code (Algorithm 2 in
+// closed form).  Fills the prefix sums S[0..M-1] (S[M-1] = N) of the
+// configuration with index gamma.  `sat` is the saturated table of the index
+// width; the inner search walks x downward and never passes C(m, m+1) = 0, so
+// the total number of steps is at most N + M.
+template <class Idx, int MAXM>
+__device__ __forceinline__ void fock_decode_prefix(Idx gamma, int N, int M, Idx nc,
+                                                   const Idx *__restrict__ sat, int xdim,
+                                                   int (&S)[MAXM]) {
+  Idx rem = nc - (Idx)1 - gamma;
+  int x = N + M - 1;
+#pragma unroll
+  for (int m = MAXM - 2; m >= 0; --m) {
+    if (m <= M - 2) {
+      const Idx *row = sat + (size_t)m * xdim;
+      int xx = x - 1;
+      Idx v = row[xx];
+      while (v > rem) {
+        --xx;
+        v = row[xx];
+      }
+      rem -= v;
+      S[m] = xx - m;
+      x = xx;
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < MAXM; ++m)
+    if (m >= M - 1) S[m] = N;
+}
+
+// Index of the configuration with prefix sums S (S[M-1] = N).
+template <class Idx, int MAXM>
+__device__ __forceinline__ Idx fock_rank_prefix(const int (&S)[MAXM], int M, Idx nc,
+                                                const Idx *__restrict__ mod, int xdim) {
+  Idx acc = nc - (Idx)1;
+#pragma unroll
+  for (int m = 0; m < MAXM - 1; ++m)
+    if (m <= M - 2) acc -= mod[(size_t)m * xdim + S[m] + m];
+  return acc;
+}

@@ -1,0 +1,328 @@
+"""Thin Python binding of libfock (include/fock.h): same names, argument
+marshalling only.  Every computation runs in the CUDA library; there is no
+Python or CPU fallback, and a missing library raises at first use.
+
+Device buffers are torch CUDA tensors (their data pointers are passed to the
+C ABI); `stream` defaults to torch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+FOCK_OK = 0
+FOCK_ERR_ARG = -1
+FOCK_ERR_OVERFLOW = -2
+FOCK_ERR_INVALID_CONFIG = -3
+FOCK_ERR_RANGE = -4
+FOCK_ERR_NOMEM = -5
+FOCK_ERR_NOT_HERMITIAN = -6
+FOCK_ERR_ALIAS = -7
+FOCK_ERR_CUDA = -8
+FOCK_ERR_NOCONV = -9
+FOCK_ERR_UNSUPPORTED = -10
+FOCK_ERR_TIMEOUT = -11
+FOCK_ERR_NOT_BUILT = -12
+FOCK_ERR_DEVICE = -13
+
+FOCK_MAP_SINGLE = 1
+FOCK_MAP_DOUBLE = 2
+
+FOCK_PREC_F64 = 0
+FOCK_PREC_F64_NATIVE = 1
+FOCK_PREC_F32_MIXED = 2
+
+FOCK_ARM_AUTO = 0
+FOCK_ARM_HASH = 1
+FOCK_ARM_MAPS = 2
+
+# Every extern "C" symbol declared in include/fock.h.
+EXPORTS = (
+    "fock_strerror", "fock_version",
+    "fock_space_create", "fock_space_destroy", "fock_space_size", "fock_rank", "fock_unrank",
+    "fock_build_jump_maps", "fock_jump_map_get", "fock_jump_maps_free",
+    "fock_hamiltonian_create", "fock_hamiltonian_destroy", "fock_hamiltonian_terms",
+    "fock_hamiltonian_is_real",
+    "fock_apply_workspace_size", "fock_apply_H", "fock_apply_H_host",
+    "fock_lanczos_ground",
+)
+
+
+class FockError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {fock_strerror(status)} ({status})")
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libfock.so (built by ``_build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _build.LIB
+    if not os.path.exists(p):
+        raise RuntimeError(f"libfock is not built ({p}); run __graft_entry__.build() first")
+    lib = ctypes.CDLL(p)
+    vp, i32, i64, sz, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_double
+    P = ctypes.POINTER
+    lib.fock_strerror.restype = ctypes.c_char_p
+    lib.fock_strerror.argtypes = [ctypes.c_int]
+    lib.fock_version.restype = ctypes.c_int
+    sigs = {
+        "fock_space_create": [i32, i32, P(vp)],
+        "fock_space_destroy": [vp],
+        "fock_space_size": [vp, P(i64)],
+        "fock_rank": [vp, vp, i64, vp, vp],
+        "fock_unrank": [vp, vp, i64, vp, vp],
+        "fock_build_jump_maps": [vp, ctypes.c_int, ctypes.c_int, P(sz), vp],
+        "fock_jump_map_get": [vp, ctypes.c_int, P(vp), P(i64), P(i64)],
+        "fock_jump_maps_free": [vp],
+        "fock_hamiltonian_create": [vp, vp, vp, dbl, P(vp)],
+        "fock_hamiltonian_destroy": [vp],
+        "fock_hamiltonian_terms": [vp, P(i64)],
+        "fock_hamiltonian_is_real": [vp, P(ctypes.c_int)],
+        "fock_apply_workspace_size": [vp, vp, i32, ctypes.c_int, P(sz)],
+        "fock_apply_H": [vp, vp, vp, vp, i32, ctypes.c_int, ctypes.c_int, vp, sz, vp],
+        "fock_apply_H_host": [vp, vp, vp, vp, i32, ctypes.c_int, ctypes.c_int, vp],
+        "fock_lanczos_ground": [vp, vp, i32, i32, dbl, ctypes.c_uint64, ctypes.c_int, vp,
+                                P(dbl), P(dbl), vp, P(i32), vp],
+    }
+    for name, args in sigs.items():
+        f = getattr(lib, name)
+        f.restype = ctypes.c_int
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def fock_strerror(status: int) -> str:
+    return load().fock_strerror(int(status)).decode()
+
+
+def fock_version() -> int:
+    return int(load().fock_version())
+
+
+def _check(st: int, where: str, allow=()):
+    if st != FOCK_OK and st not in allow:
+        raise FockError(st, where)
+    return st
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dptr(t):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# --------------------------------------------------------------------------
+# space, hash, maps
+# --------------------------------------------------------------------------
+def fock_space_create(N: int, M: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().fock_space_create(int(N), int(M), ctypes.byref(h)), "fock_space_create")
+    return h
+
+
+def fock_space_destroy(sp) -> None:
+    load().fock_space_destroy(sp)
+
+
+def fock_space_size(sp) -> int:
+    n = ctypes.c_int64()
+    _check(load().fock_space_size(sp, ctypes.byref(n)), "fock_space_size")
+    return n.value
+
+
+def fock_rank(sp, occ, idx=None, stream=None, check: bool = True):
+    """occ: int32 CUDA tensor [count, M]; returns (int64 indices, status)."""
+    import torch
+    count = occ.shape[0]
+    if idx is None:
+        idx = torch.empty(count, dtype=torch.int64, device=occ.device)
+    st = load().fock_rank(sp, _dptr(occ), count, _dptr(idx), _stream(stream))
+    if check:
+        _check(st, "fock_rank")
+    return idx, st
+
+
+def fock_unrank(sp, idx, M: int, occ=None, stream=None, check: bool = True):
+    """idx: int64 CUDA tensor [count]; returns (int32 occupations [count, M], status)."""
+    import torch
+    count = idx.shape[0]
+    if occ is None:
+        occ = torch.empty((count, M), dtype=torch.int32, device=idx.device)
+    st = load().fock_unrank(sp, _dptr(idx), count, _dptr(occ), _stream(stream))
+    if check:
+        _check(st, "fock_unrank")
+    return occ, st
+
+
+def fock_build_jump_maps(sp, which: int, dry_run: bool = False, stream=None) -> int:
+    b = ctypes.c_size_t()
+    _check(load().fock_build_jump_maps(sp, int(which), int(bool(dry_run)), ctypes.byref(b),
+                                       _stream(stream) if not dry_run else None),
+           "fock_build_jump_maps")
+    return b.value
+
+
+class _DeviceArray:
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (ptr, True), "version": 2, "strides": None}
+
+
+def fock_jump_map_get(sp, which: int):
+    """Read-only view [slots, N_c] of a built map as an int32 torch tensor."""
+    import torch
+    p, slots, stride = ctypes.c_void_p(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().fock_jump_map_get(sp, int(which), ctypes.byref(p), ctypes.byref(slots),
+                                    ctypes.byref(stride)), "fock_jump_map_get")
+    return torch.as_tensor(_DeviceArray(p.value, (slots.value, stride.value), "<i4"), device="cuda")
+
+
+def fock_jump_maps_free(sp) -> None:
+    _check(load().fock_jump_maps_free(sp), "fock_jump_maps_free")
+
+
+# --------------------------------------------------------------------------
+# Hamiltonian and apply
+# --------------------------------------------------------------------------
+def fock_hamiltonian_create(sp, h, W=None, tol: float = 1e-12):
+    M = int(round(np.asarray(h).size ** 0.5))
+    hh = np.ascontiguousarray(np.asarray(h, dtype=np.complex128).reshape(M, M))
+    WW = None if W is None else np.ascontiguousarray(np.asarray(W, dtype=np.complex128).reshape(-1))
+    out = ctypes.c_void_p()
+    _check(load().fock_hamiltonian_create(
+        sp, hh.ctypes.data_as(ctypes.c_void_p),
+        None if WW is None else WW.ctypes.data_as(ctypes.c_void_p), float(tol), ctypes.byref(out)),
+        "fock_hamiltonian_create")
+    return out
+
+
+def fock_hamiltonian_destroy(ham) -> None:
+    load().fock_hamiltonian_destroy(ham)
+
+
+def fock_hamiltonian_terms(ham) -> int:
+    n = ctypes.c_int64()
+    _check(load().fock_hamiltonian_terms(ham, ctypes.byref(n)), "fock_hamiltonian_terms")
+    return n.value
+
+
+def fock_hamiltonian_is_real(ham) -> bool:
+    r = ctypes.c_int()
+    _check(load().fock_hamiltonian_is_real(ham, ctypes.byref(r)), "fock_hamiltonian_is_real")
+    return bool(r.value)
+
+
+def fock_apply_workspace_size(sp, ham, nrhs: int, precision: int) -> int:
+    b = ctypes.c_size_t()
+    _check(load().fock_apply_workspace_size(sp, ham, int(nrhs), int(precision), ctypes.byref(b)),
+           "fock_apply_workspace_size")
+    return b.value
+
+
+def fock_apply_H(sp, ham, C, sigma=None, nrhs: int = 1, precision: int = FOCK_PREC_F64,
+                 arm: int = FOCK_ARM_AUTO, workspace=None, stream=None):
+    """sigma = H C.  C: CUDA tensor [N_c] or [N_c, nrhs], complex128 (FOCK_PREC_F64*)
+    or complex64 (FOCK_PREC_F32_MIXED).  Returns sigma (allocated if None)."""
+    import torch
+    if sigma is None:
+        sigma = torch.empty_like(C)
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load().fock_apply_H(sp, ham, _dptr(C), _dptr(sigma), int(nrhs), int(precision), int(arm),
+                               _dptr(workspace), ws_bytes, _stream(stream)), "fock_apply_H")
+    return sigma
+
+
+def fock_apply_H_host(sp, ham, C_host, sigma_host, nrhs: int = 1, precision: int = FOCK_PREC_F64,
+                      arm: int = FOCK_ARM_AUTO, stream=None):
+    """Host-buffer variant: C_host and sigma_host are CPU tensors (pinned for speed)."""
+    _check(load().fock_apply_H_host(sp, ham, ctypes.c_void_p(C_host.data_ptr()),
+                                    ctypes.c_void_p(sigma_host.data_ptr()), int(nrhs), int(precision),
+                                    int(arm), _stream(stream)), "fock_apply_H_host")
+    return sigma_host
+
+
+def fock_lanczos_ground(sp, ham, max_iter: int = 300, restart_len: int = 30, tol: float = 1e-12,
+                        seed: int = 1, precision: int = FOCK_PREC_F64, start=None, want_vector=False,
+                        stream=None):
+    """Returns (E0, residual, iterations, vector-or-None, status)."""
+    import torch
+    E0, res, it = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    vec = None
+    if want_vector:
+        vec = torch.empty(fock_space_size(sp), dtype=torch.complex128, device="cuda")
+    st = load().fock_lanczos_ground(sp, ham, int(max_iter), int(restart_len), float(tol),
+                                    ctypes.c_uint64(int(seed)), int(precision), _dptr(start),
+                                    ctypes.byref(E0), ctypes.byref(res), _dptr(vec), ctypes.byref(it),
+                                    _stream(stream))
+    _check(st, "fock_lanczos_ground", allow=(FOCK_ERR_NOCONV,))
+    return E0.value, res.value, it.value, vec, st
+
+
+# --------------------------------------------------------------------------
+# convenience wrappers (own the handles)
+# --------------------------------------------------------------------------
+class Space:
+    def __init__(self, N: int, M: int):
+        self.N, self.M = int(N), int(M)
+        self.handle = fock_space_create(N, M)
+        self.nc = fock_space_size(self.handle)
+
+    def close(self):
+        if self.handle:
+            fock_space_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Hamiltonian:
+    def __init__(self, space: Space, h, W=None, tol: float = 1e-12):
+        self.space = space
+        self.handle = fock_hamiltonian_create(space.handle, h, W, tol)
+        self.terms = fock_hamiltonian_terms(self.handle)
+        self.real = fock_hamiltonian_is_real(self.handle)
+
+    def apply(self, C, sigma=None, nrhs=1, precision=FOCK_PREC_F64, arm=FOCK_ARM_AUTO, workspace=None):
+        return fock_apply_H(self.space.handle, self.handle, C, sigma, nrhs, precision, arm, workspace)
+
+    def close(self):
+        if self.handle:
+            fock_hamiltonian_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,226 @@
+"""GPU parity of sigma = H C (Eq. Haction) against the oracle, through the C ABI.
+
+Tolerances (relative 2-norm of the difference, ||sigma - sigma_ref|| / ||sigma_ref||):
+  FOCK_PREC_F64 (FP32-pair arithmetic) and FOCK_PREC_F64_NATIVE: 1e-12, the
+  target the FP64 apply must meet; FP32-pair values carry 48-bit significands,
+  so the expected error is a few 1e-15.
+  FOCK_PREC_F32_MIXED: 5e-6; inputs rounded to complex64 carry 2^-24 relative
+  error each and FP32 products add the same order, so a few 1e-7 is expected.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_13679_gb300 import fock, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {fock.FOCK_PREC_F64: 1e-12, fock.FOCK_PREC_F64_NATIVE: 1e-12, fock.FOCK_PREC_F32_MIXED: 5e-6}
+PRECS = list(TOL)
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    fock.load()
+    return t
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def dev_vec(torch, C, prec):
+    t = torch.from_numpy(np.ascontiguousarray(C))
+    if prec == fock.FOCK_PREC_F32_MIXED:
+        t = t.to(torch.complex64)
+    return t.cuda()
+
+
+def hw(kind, M, seed=7, g=1.0):
+    if kind == "ll":
+        return inputs.lieb_liniger_hw(M, g)
+    if kind == "onebody":
+        h, _ = inputs.random_hermitian_hw(M, seed)
+        return h, None
+    return inputs.random_hermitian_hw(M, seed)
+
+
+# (N, M, kind): several tiles of 128 configurations with a ragged tail, the
+# degenerate spaces (N = 1, M = 1, N = 2) and both sparse and dense W.
+SMALL = [
+    (6, 6, "generic"),      # 462 configurations
+    (8, 6, "generic"),      # 1287
+    (10, 5, "ll"),          # 1001
+    (5, 10, "ll"),          # 2002, most orbitals empty
+    (7, 4, "generic"),      # 120
+    (1, 7, "generic"),      # one particle: one-body part only
+    (2, 5, "generic"),      # smallest N with a two-body part
+    (9, 1, "generic"),      # one orbital, one configuration
+    (12, 3, "onebody"),     # W absent
+    (4, 12, "ll"),          # largest M
+    (3, 9, "generic"),
+]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N,M,kind", SMALL)
+def test_apply_full_vector(torch, N, M, kind, prec):
+    h, W = hw(kind, M)
+    sp = fock.Space(N, M)
+    H = fock.Hamiltonian(sp, h, W)
+    C = inputs.random_state(sp.nc, 11)
+    ref = oracle.apply_push(N, M, h, W, C)
+    out = H.apply(dev_vec(torch, C, prec), precision=prec)
+    torch.cuda.synchronize()
+    assert rel(out.cpu().numpy().astype(np.complex128), ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_apply_scale_invariance(torch, prec):
+    # The FP32-pair path rescales C by a power of two; extreme magnitudes
+    # must not lose accuracy (FP32 storage has its own range, tested at 1e-20).
+    N, M = 6, 5
+    h, W = hw("generic", M)
+    sp = fock.Space(N, M)
+    H = fock.Hamiltonian(sp, h, W)
+    C = inputs.random_state(sp.nc, 5)
+    ref = oracle.apply_push(N, M, h, W, C)
+    scales = [1e-20, 1e20] if prec == fock.FOCK_PREC_F32_MIXED else [1e-250, 1e-40, 1e40, 1e250]
+    for s in scales:
+        out = H.apply(dev_vec(torch, C * s, prec), precision=prec).cpu().numpy().astype(np.complex128)
+        assert rel(out / s, ref) <= TOL[prec], s
+    zero = H.apply(dev_vec(torch, np.zeros_like(C), prec), precision=prec).cpu().numpy()
+    assert np.all(zero == 0)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("nrhs", [1, 3, 16])
+def test_block_rhs_matches_single(torch, prec, nrhs):
+    N, M = 8, 6
+    h, W = hw("generic", M, seed=4)
+    sp = fock.Space(N, M)
+    H = fock.Hamiltonian(sp, h, W)
+    B = inputs.random_block(sp.nc, range(40, 40 + nrhs))
+    out = H.apply(dev_vec(torch, B, prec), nrhs=nrhs, precision=prec).cpu().numpy().astype(np.complex128)
+    for j in range(nrhs):
+        ref = oracle.apply_push(N, M, h, W, B[:, j])
+        assert rel(out[:, j], ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N,M,kind", [(6, 6, "generic"), (10, 5, "ll"), (1, 5, "generic"), (12, 3, "onebody")])
+def test_maps_arm_equals_hash_arm(torch, N, M, kind, prec):
+    h, W = hw(kind, M)
+    sp = fock.Space(N, M)
+    H = fock.Hamiltonian(sp, h, W)
+    C = dev_vec(torch, inputs.random_state(sp.nc, 9), prec)
+    with pytest.raises(fock.FockError) as e:
+        H.apply(C, precision=prec, arm=fock.FOCK_ARM_MAPS)
+    assert e.value.status == fock.FOCK_ERR_NOT_BUILT
+    fock.fock_build_jump_maps(sp.handle, fock.FOCK_MAP_SINGLE | fock.FOCK_MAP_DOUBLE)
+    a = H.apply(C, precision=prec, arm=fock.FOCK_ARM_HASH)
+    b = H.apply(C, precision=prec, arm=fock.FOCK_ARM_MAPS)
+    # identical targets and identical arithmetic order: bit-identical sums
+    assert torch.equal(a, b)
+
+
+def test_alias_and_argument_errors(torch):
+    sp = fock.Space(5, 5)
+    h, W = hw("ll", 5)
+    H = fock.Hamiltonian(sp, h, W)
+    C = dev_vec(torch, inputs.random_state(sp.nc, 1), fock.FOCK_PREC_F64)
+    with pytest.raises(fock.FockError) as e:
+        H.apply(C, sigma=C)
+    assert e.value.status == fock.FOCK_ERR_ALIAS
+    with pytest.raises(fock.FockError):
+        H.apply(C, nrhs=17)
+    with pytest.raises(fock.FockError) as e:
+        fock.Hamiltonian(sp, h + np.triu(np.ones((5, 5)), 1), W)
+    assert e.value.status == fock.FOCK_ERR_NOT_HERMITIAN
+
+
+def test_terms_count_matches_oracle_columns(torch):
+    for N, M, kind in [(6, 6, "generic"), (10, 5, "ll"), (1, 7, "generic")]:
+        h, W = hw(kind, M)
+        sp = fock.Space(N, M)
+        H = fock.Hamiltonian(sp, h, W)
+        # Column term counts of the oracle count ordered operator strings; the
+        # library counts one term per distinct (removal, addition) multiset
+        # pair, plus the diagonal and the off-diagonal one-body jumps.
+        P = M * (M + 1) // 2
+        Ws = np.zeros((P, P), dtype=np.complex128)
+        pairs = {(k, q): i for i, (k, q) in enumerate((k, q) for k in range(M) for q in range(k, M))}
+        if W is not None and N >= 2:
+            for k in range(M):
+                for q in range(M):
+                    for s in range(M):
+                        for l in range(M):
+                            Ws[pairs[(min(k, q), max(k, q))], pairs[(min(s, l), max(s, l))]] += W[k, q, s, l]
+        nz = int(np.count_nonzero(Ws))
+        offh = int(np.count_nonzero(h - np.diag(np.diag(h))))
+        expect = sp.nc + oracle.nc(N - 1, M) * offh + (oracle.nc(N - 2, M) * nz if N >= 2 else 0)
+        assert H.terms == expect
+
+
+def test_host_buffer_entry_point(torch):
+    N, M = 8, 6
+    h, W = hw("generic", M)
+    sp = fock.Space(N, M)
+    H = fock.Hamiltonian(sp, h, W)
+    C = inputs.random_state(sp.nc, 2)
+    ref = oracle.apply_push(N, M, h, W, C)
+    Ch = torch.from_numpy(C).pin_memory()
+    out = torch.empty_like(Ch).pin_memory()
+    fock.fock_apply_H_host(sp.handle, H.handle, Ch, out)
+    assert rel(out.numpy(), ref) <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Full-size workloads in the launch configuration of the benchmark: sampled
+# rows against the oracle's row form, plus properties at full size.
+# ---------------------------------------------------------------------------
+def sampled_rows(nc, seed, count):
+    rng = np.random.default_rng(seed)
+    edge = np.concatenate([np.arange(min(512, nc)), nc - 1 - np.arange(min(512, nc))])
+    return np.unique(np.concatenate([edge, rng.integers(0, nc, count)])).astype(np.int64)
+
+
+@pytest.mark.parametrize("name", ["generic_n100_m6", "ll_n30_m10", "ll_n5_m5"])
+def test_full_size_sampled_rows(torch, name):
+    w = inputs.WORKLOADS[name]
+    h, W = w.hamiltonian()
+    sp = fock.Space(w.N, w.M)
+    H = fock.Hamiltonian(sp, h, W)
+    C = w.state()
+    rows = sampled_rows(sp.nc, 1, 3000)
+    ref = oracle.apply_rows(w.N, w.M, h, W, C, rows)
+    Cd = torch.from_numpy(C).cuda()
+    del C
+    sig = H.apply(Cd, precision=fock.FOCK_PREC_F64)
+    got = sig[torch.from_numpy(rows).cuda()].cpu().numpy()
+    assert rel(got, ref) <= 1e-12
+    # Hermiticity at full size: <C, H C> is real
+    q = torch.vdot(Cd, sig).item()
+    assert abs(q.imag) <= 1e-12 * abs(q)
+    del sig
+    sig32 = H.apply(Cd.to(torch.complex64), precision=fock.FOCK_PREC_F32_MIXED)
+    got32 = sig32[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.complex128)
+    assert rel(got32, ref) <= 5e-6
+
+
+def test_full_size_block_rhs_n20_m8(torch):
+    w = inputs.WORKLOADS["generic_n20_m8_rhs16"]
+    h, W = w.hamiltonian()
+    sp = fock.Space(w.N, w.M)
+    H = fock.Hamiltonian(sp, h, W)
+    B = w.state()
+    rows = sampled_rows(sp.nc, 2, 1500)
+    Bd = torch.from_numpy(B).cuda()
+    blk = H.apply(Bd, nrhs=16, precision=fock.FOCK_PREC_F64)
+    for j in (0, 7, 15):
+        ref = oracle.apply_rows(w.N, w.M, h, W, B[:, j], rows)
+        got = blk[:, j][torch.from_numpy(rows).cuda()].cpu().numpy()
+        assert rel(got, ref) <= 1e-12
+        one = H.apply(Bd[:, j].contiguous(), precision=fock.FOCK_PREC_F64)
+        assert torch.allclose(one, blk[:, j], rtol=0, atol=1e-13)
