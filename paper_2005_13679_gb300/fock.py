@@ -192,11 +192,12 @@ def fock_build_jump_maps(sp, which: int, dry_run: bool = False, stream=None) -> 
 class _DeviceArray:
     def __init__(self, ptr: int, shape, typestr: str):
         self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
-                                         "data": (ptr, True), "version": 2, "strides": None}
+                                         "data": (ptr, False), "version": 2, "strides": None}
 
 
 def fock_jump_map_get(sp, which: int):
-    """Read-only view [slots, N_c] of a built map as an int32 torch tensor."""
+    """View [slots, N_c] of a built map as an int32 torch tensor (owned by the
+    space; treat it as read-only)."""
     import torch
     p, slots, stride = ctypes.c_void_p(), ctypes.c_int64(), ctypes.c_int64()
     _check(load().fock_jump_map_get(sp, int(which), ctypes.byref(p), ctypes.byref(slots),
