@@ -62,6 +62,7 @@ extern "C" {
 #define FOCK_ERR_TIMEOUT       -11   /* a bounded device wait gave up            */
 #define FOCK_ERR_NOT_BUILT     -12   /* jump maps requested but not built        */
 #define FOCK_ERR_DEVICE        -13   /* object used on another device            */
+#define FOCK_ERR_SCRATCH_LIMIT -14   /* request exceeds the fixed no-alloc scratch */
 
 /* Human-readable name of a status code (static storage, never NULL). */
 const char *fock_strerror(int status);
@@ -201,6 +202,31 @@ int fock_apply_H(const fock_space *sp, const fock_ham *ham, const void *C_dev,
  * host memory the copies run at full link speed. */
 int fock_apply_H_host(const fock_space *sp, const fock_ham *ham, const void *C_host,
                       void *sigma_host, int32_t nrhs, int precision, int arm, void *stream);
+
+/* sigma = H C with FOCK_PREC_F64 for callers that must not allocate device
+ * memory.  The paper has no counterpart; this is an interface convenience.
+ * Some callers cannot let a library allocate: their device memory belongs to
+ * another allocator (a caching allocator or a fixed pool that must not be
+ * bypassed), or they call in a loop where a cudaMalloc/cudaFree would
+ * synchronise the device and stall their other streams.  This call takes its
+ * scratch (status words plus a hi/lo split copy of C, 256 + 16*N_c*nrhs bytes)
+ * from a fixed array of FOCK_NOALLOC_SCRATCH_BYTES (64 MiB) compiled into the
+ * library; every GPU that loads the library keeps that array until the process
+ * exits.  It calls no cudaMalloc, cudaFree or allocating library routine.
+ * The caller still owns C_dev and sigma_dev (layouts as for fock_apply_H).
+ *   - Requests needing more scratch than the array holds (N_c * nrhs above
+ *     4,194,288) fail with FOCK_ERR_SCRATCH_LIMIT before any device work.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make
+ *     that first call before any stream capture.
+ *   - All calls on a device share the one array and each call rewrites the
+ *     parts it reads, so results do not depend on earlier calls; but calls
+ *     whose work overlaps on the GPU (different streams, or host threads
+ *     without ordering) race on the array and must be serialised.
+ * Asynchronous on `stream`; other errors as for fock_apply_H. */
+#define FOCK_NOALLOC_SCRATCH_BYTES (64u << 20)
+int fock_apply_H_noalloc(const fock_space *sp, const fock_ham *ham, const void *C_dev,
+                         void *sigma_dev, int32_t nrhs, int arm, void *stream);
 
 /* ------------------------------------------------------------------------- */
 /* Lanczos ground state  (Sec. 5)                                            */

@@ -28,6 +28,7 @@ extern "C" const char *fock_strerror(int status) {
     case FOCK_ERR_TIMEOUT: return "bounded device wait expired";
     case FOCK_ERR_NOT_BUILT: return "jump maps not built";
     case FOCK_ERR_DEVICE: return "object belongs to another device";
+    case FOCK_ERR_SCRATCH_LIMIT: return "request exceeds the fixed scratch of the no-allocation entry point";
     default: return "unknown status";
   }
 }

@@ -28,6 +28,8 @@ FOCK_ERR_UNSUPPORTED = -10
 FOCK_ERR_TIMEOUT = -11
 FOCK_ERR_NOT_BUILT = -12
 FOCK_ERR_DEVICE = -13
+FOCK_ERR_SCRATCH_LIMIT = -14
+FOCK_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 FOCK_MAP_SINGLE = 1
 FOCK_MAP_DOUBLE = 2
@@ -47,7 +49,7 @@ EXPORTS = (
     "fock_build_jump_maps", "fock_jump_map_get", "fock_jump_maps_free",
     "fock_hamiltonian_create", "fock_hamiltonian_destroy", "fock_hamiltonian_terms",
     "fock_hamiltonian_is_real",
-    "fock_apply_workspace_size", "fock_apply_H", "fock_apply_H_host",
+    "fock_apply_workspace_size", "fock_apply_H", "fock_apply_H_host", "fock_apply_H_noalloc",
     "fock_lanczos_ground",
 )
 
@@ -95,6 +97,7 @@ def load(path: str | None = None):
         "fock_apply_workspace_size": [vp, vp, i32, ctypes.c_int, P(sz)],
         "fock_apply_H": [vp, vp, vp, vp, i32, ctypes.c_int, ctypes.c_int, vp, sz, vp],
         "fock_apply_H_host": [vp, vp, vp, vp, i32, ctypes.c_int, ctypes.c_int, vp],
+        "fock_apply_H_noalloc": [vp, vp, vp, vp, i32, ctypes.c_int, vp],
         "fock_lanczos_ground": [vp, vp, i32, i32, dbl, ctypes.c_uint64, ctypes.c_int, vp,
                                 P(dbl), P(dbl), vp, P(i32), vp],
     }
@@ -267,6 +270,21 @@ def fock_apply_H_host(sp, ham, C_host, sigma_host, nrhs: int = 1, precision: int
                                     ctypes.c_void_p(sigma_host.data_ptr()), int(nrhs), int(precision),
                                     int(arm), _stream(stream)), "fock_apply_H_host")
     return sigma_host
+
+
+def fock_apply_H_noalloc(sp, ham, C, sigma=None, nrhs: int = 1, arm: int = FOCK_ARM_AUTO,
+                         stream=None, check: bool = True):
+    """FP64-class sigma = H C with the library's fixed scratch instead of an
+    allocation (for callers whose device memory is managed elsewhere).
+    Returns (sigma, status)."""
+    import torch
+    if sigma is None:
+        sigma = torch.empty_like(C)
+    st = load().fock_apply_H_noalloc(sp, ham, _dptr(C), _dptr(sigma), int(nrhs), int(arm),
+                                     _stream(stream))
+    if check:
+        _check(st, "fock_apply_H_noalloc")
+    return sigma, st
 
 
 def fock_lanczos_ground(sp, ham, max_iter: int = 300, restart_len: int = 30, tol: float = 1e-12,
