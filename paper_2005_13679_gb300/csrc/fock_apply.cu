@@ -17,10 +17,60 @@
 #include <vector>
 
 #include "fock_apply_kernel.cuh"
+#include "fock_apply_sparse.cuh"
 
 int fock_launch_apply_f64(const void *, bool, int, bool, bool, int, cudaStream_t);
 int fock_launch_apply_df(const void *, bool, int, bool, bool, int, cudaStream_t);
 int fock_launch_apply_mixed(const void *, bool, int, bool, bool, int, cudaStream_t);
+int fock_launch_dense_df(const ApplyArgs<uint32_t> &, bool, bool, int, cudaStream_t);
+int fock_launch_dense_mixed(const ApplyArgs<uint32_t> &, bool, bool, int, cudaStream_t);
+int fock_launch_sparse_f64(const SparseArgs &, bool, bool, int, cudaStream_t);
+int fock_launch_sparse_df(const SparseArgs &, bool, bool, int, cudaStream_t);
+int fock_launch_sparse_mixed(const SparseArgs &, bool, bool, int, cudaStream_t);
+
+// Segment form of one term (see fock_apply_sparse.cuh): the removal (k, q)
+// (q = -1 for one particle) and the addition (s, l) (s = -1 for one particle)
+// change the prefix sums by d(m) = sum of +1 at and after each added orbital
+// and -1 at and after each removed one.  The sorted breakpoints and the values
+// of d between them become the byte offsets of the six prefix-table reads.
+static FockTerm make_term(int M, int k, int q, int s, int l) {
+  int pos[4], del[4], ne = 0;
+  pos[ne] = k; del[ne++] = -1;
+  if (q >= 0) { pos[ne] = q; del[ne++] = -1; }
+  if (s >= 0) { pos[ne] = s; del[ne++] = +1; }
+  pos[ne] = l; del[ne++] = +1;
+  for (int i = 1; i < ne; ++i)
+    for (int j = i; j > 0 && pos[j - 1] > pos[j]; --j) {
+      int tp = pos[j]; pos[j] = pos[j - 1]; pos[j - 1] = tp;
+      int td = del[j]; del[j] = del[j - 1]; del[j - 1] = td;
+    }
+  int up[4], ud[4], nu = 0, cur = 0;
+  for (int i = 0; i < ne; ++i) {
+    cur += del[i];
+    if (nu > 0 && up[nu - 1] == pos[i]) {
+      ud[nu - 1] = cur;
+    } else {
+      up[nu] = pos[i];
+      ud[nu] = cur;
+      ++nu;
+    }
+  }
+  int x[4], d[3];
+  for (int i = 0; i < 4; ++i) x[i] = i < nu ? up[i] : up[nu - 1];
+  for (int i = 0; i < 3; ++i) d[i] = i < nu - 1 ? ud[i] : 0;
+  const int maxm = fock_sparse_maxm(M);
+  auto off = [&](int dd, int xx) { return (uint16_t)(((dd + 2) * maxm + xx) * FOCK_APPLY_THREADS * 4); };
+  FockTerm T;
+  for (int i = 0; i < 3; ++i) {
+    T.off[2 * i] = off(d[i], x[i + 1]);
+    T.off[2 * i + 1] = off(d[i], x[i]);
+  }
+  T.s = (int8_t)s;
+  T.l = (int8_t)l;
+  T.ds = (int8_t)(s >= 0 ? (s == k) + (q >= 0 && s == q) : 0);
+  T.dl = (int8_t)((l == k) + (q >= 0 && l == q) - (s >= 0 && l == s));
+  return T;
+}
 
 typedef std::complex<double> cplx;
 
@@ -49,6 +99,8 @@ static void free_ham(fock_ham *h) {
   cudaFree(h->d_sqrt64);
   cudaFree(h->d_sqrtdf);
   cudaFree(h->d_sqrt32);
+  cudaFree(h->d_terms);
+  cudaFree(h->d_slots);
   cudaFree(h->ws);
   cudaFree(h->hb_in);
   cudaFree(h->hb_out);
@@ -234,7 +286,16 @@ extern "C" int fock_hamiltonian_create(const fock_space *sp, const double *h_hos
     H->h_coef[2 * i] = coef[i].real();
     H->h_coef[2 * i + 1] = coef[i].imag();
   }
+  std::vector<FockTerm> terms(nadd);
+  std::vector<int32_t> slots(nadd);
+  for (const FockRemoval &e : rem)
+    for (int i = e.a_beg; i < e.a_end; ++i) {
+      terms[i] = make_term(M, e.k, e.q, add[i].s, add[i].l);
+      slots[i] = e.slot_base + add[i].a_index;
+    }
   int st = FOCK_OK;
+  if (!st) st = upload(&H->d_terms, terms.data(), nadd);
+  if (!st) st = upload(&H->d_slots, slots.data(), nadd);
   if (!st) st = upload(&H->d_rem, rem.data(), rem.size());
   if (!st) st = upload(&H->d_add, add.data(), nadd);
   if (!st) st = upload(&H->d_coef64, c64.data(), nadd);
@@ -290,7 +351,8 @@ __global__ void fock_split_kernel(const double2 *__restrict__ x, int64_t n, cons
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double2 v = __ldg(x + i);
-    const double re = ldexp(v.x, sh), im = ldexp(v.y, sh);
+    const double f = fock_pow2(sh);
+    const double re = v.x * f, im = v.y * f;
     const float rh = __double2float_rn(re), ih = __double2float_rn(im);
     const float rl = __double2float_rn(re - (double)rh), il = __double2float_rn(im - (double)ih);
     y[i] = make_float4(rh, ih, rl, il);
@@ -402,6 +464,24 @@ int fock_apply_internal(const fock_space *sp, const fock_ham *ham, const void *C
   if (sp->idx32) {
     ApplyArgs<uint32_t> a;
     fill_args(a, sp, ham, Cin, sigma, nrhs, precision, map, in_exp);
+    // Every reduced coefficient present and M <= 10: the register-resident
+    // kernel with the addition loop unrolled at compile time.
+    if (ham->dense && sp->M <= 10 && !(maps && nrhs16)) {
+      if (precision == FOCK_PREC_F64) return fock_launch_dense_df(a, nrhs16, maps, sp->device, stream);
+      if (precision == FOCK_PREC_F32_MIXED) return fock_launch_dense_mixed(a, nrhs16, maps, sp->device, stream);
+    }
+    // Any sparsity: per-configuration prefix tables, host-precomputed segments
+    // (the term list is staged in shared memory, so it must stay small).
+    if (!(maps && nrhs16) && (size_t)ham->nadd * 48 <= (size_t)96 * 1024) {
+      SparseArgs sa;
+      sa.base = a;
+      sa.terms = ham->d_terms;
+      sa.slots = ham->d_slots;
+      sa.nadd = ham->nadd;
+      if (precision == FOCK_PREC_F64) return fock_launch_sparse_df(sa, nrhs16, maps, sp->device, stream);
+      if (precision == FOCK_PREC_F64_NATIVE) return fock_launch_sparse_f64(sa, nrhs16, maps, sp->device, stream);
+      return fock_launch_sparse_mixed(sa, nrhs16, maps, sp->device, stream);
+    }
     switch (precision) {
       case FOCK_PREC_F64: return fock_launch_apply_df(&a, true, maxm, nrhs16, maps, sp->device, stream);
       case FOCK_PREC_F64_NATIVE: return fock_launch_apply_f64(&a, true, maxm, nrhs16, maps, sp->device, stream);

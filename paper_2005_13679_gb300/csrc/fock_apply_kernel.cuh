@@ -115,7 +115,7 @@ fock_apply_list_kernel(const ApplyArgs<Idx> a) {
   const vec_t *__restrict__ C = (const vec_t *)a.C;
   const coef_t *__restrict__ coef = (const coef_t *)a.coef;
   double out_scale = a.out_scale;
-  if (a.in_exp) out_scale = ldexp(out_scale, __ldg(a.in_exp));
+  if (a.in_exp) out_scale *= fock_pow2(__ldg(a.in_exp));
   const int nrhs = NRHS == 1 ? 1 : a.nrhs;
 
   for (Idx tile = (Idx)blockIdx.x * nt; tile < nc; tile += (Idx)gridDim.x * nt) {
@@ -205,10 +205,10 @@ fock_apply_list_kernel(const ApplyArgs<Idx> a) {
       }
     }
     if (live) {
-      auto *out = (decltype(P::finish(acc[0], 1.0)) *)a.sigma + (size_t)g * nrhs;
+      auto *out = (decltype(P::finish(acc[0], 1.0, false)) *)a.sigma + (size_t)g * nrhs;
 #pragma unroll
       for (int j = 0; j < NRHS; ++j)
-        if (j < nrhs) out[j] = P::finish(acc[j], out_scale);
+        if (j < nrhs) out[j] = P::finish(acc[j], out_scale, a.real);
     }
   }
 }

@@ -15,6 +15,8 @@
 
 #include <cuda_runtime.h>
 
+#include "fock_pack.cuh"
+
 // ---- FP32-pair primitives --------------------------------------------------
 // (h, l) += a * b with a = (ah, al), b = (bh, bl).  The product's high part
 // p = fl(ah*bh) and its rounding error come from one FMA; the cross terms
@@ -72,7 +74,7 @@ struct PolF64 {
     }
   }
   static __device__ __forceinline__ void flush(acc_t &a, const inner_t &i) { a.x += i.x; a.y += i.y; }
-  static __device__ __forceinline__ vec_t finish(const acc_t &a, double scale) {
+  static __device__ __forceinline__ vec_t finish(const acc_t &a, double scale, bool = false) {
     return make_double2(a.x * scale, a.y * scale);
   }
 };
@@ -106,7 +108,7 @@ struct PolDF {
     df_add_acc(a.z, a.w, i.z, i.w);
   }
   // value = (hi + lo) * scale, in FP64 (two conversions and one add per part)
-  static __device__ __forceinline__ double2 finish(const acc_t &a, double scale) {
+  static __device__ __forceinline__ double2 finish(const acc_t &a, double scale, bool = false) {
     return make_double2(((double)a.x + (double)a.y) * scale, ((double)a.z + (double)a.w) * scale);
   }
 };
@@ -137,8 +139,90 @@ struct PolMixed {
     df_add_acc(a.z, a.w, i.y, 0.f);
   }
   // FP32 result: no FP64 instruction on this path.
-  static __device__ __forceinline__ float2 finish(const acc_t &a, double scale) {
+  static __device__ __forceinline__ float2 finish(const acc_t &a, double scale, bool = false) {
     const float f = (float)scale;
     return make_float2(__fadd_rn(a.x, a.y) * f, __fadd_rn(a.z, a.w) * f);
+  }
+};
+
+// ---- packed variants (sparse kernel) ---------------------------------------
+// FP32 pairs on packed lanes.  With a real coefficient K the two lanes hold
+// (Re, Im) of K C directly; with a complex one they hold P1 = (Re K Re C,
+// Im K Im C) and P2 = (Im K Re C, Re K Im C), combined once at the end.
+struct PolDFP {
+  using vec_t = float4;    // (re_hi, im_hi, re_lo, im_lo)
+  using amp_t = float2;
+  using coef_t = float4;   // (re_hi, im_hi, re_lo, im_lo)
+  struct acc_t { fp2_t h1, l1, h2, l2; };
+  using inner_t = acc_t;
+  static constexpr bool kInner = false;
+
+  static __device__ __forceinline__ amp_t amul(amp_t a, amp_t b) { return df_mul(a, b); }
+  static __device__ __forceinline__ void zero(acc_t &a) { a.h1 = a.l1 = a.h2 = a.l2 = 0ull; }
+  static __device__ __forceinline__ coef_t scale(coef_t c, amp_t x) {
+    fp2_t p, e;
+    fp2_dprod(fp2_make(c.x, c.y), fp2_make(c.z, c.w), fp2_make(x.x, x.x), fp2_make(x.y, x.y), p, e);
+    return make_float4(fp2_x(p), fp2_y(p), fp2_x(e), fp2_y(e));
+  }
+  static __device__ __forceinline__ void mac(acc_t &a, coef_t k, vec_t v, bool real) {
+    const fp2_t Ch = fp2_make(v.x, v.y), Cl = fp2_make(v.z, v.w);
+    fp2_t p, e;
+    if (real) {
+      fp2_dprod(fp2_make(k.x, k.x), fp2_make(k.z, k.z), Ch, Cl, p, e);
+      fp2_dacc(a.h1, a.l1, p, e);
+    } else {
+      const fp2_t Kh = fp2_make(k.x, k.y), Kl = fp2_make(k.z, k.w);
+      fp2_dprod(Kh, Kl, Ch, Cl, p, e);
+      fp2_dacc(a.h1, a.l1, p, e);
+      fp2_dprod(fp2_swap(Kh), fp2_swap(Kl), Ch, Cl, p, e);
+      fp2_dacc(a.h2, a.l2, p, e);
+    }
+  }
+  static __device__ __forceinline__ double2 finish(const acc_t &a, double scale, bool real) {
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    if (real) {
+      df_add_acc(rh, rl, fp2_x(a.h1), fp2_x(a.l1));
+      df_add_acc(ih, il, fp2_y(a.h1), fp2_y(a.l1));
+    } else {
+      df_add_acc(rh, rl, fp2_x(a.h1), fp2_x(a.l1));
+      df_add_acc(rh, rl, -fp2_y(a.h1), -fp2_y(a.l1));
+      df_add_acc(ih, il, fp2_x(a.h2), fp2_x(a.l2));
+      df_add_acc(ih, il, fp2_y(a.h2), fp2_y(a.l2));
+    }
+    return make_double2(((double)rh + (double)rl) * scale, ((double)ih + (double)il) * scale);
+  }
+};
+
+struct PolMixedP {
+  using vec_t = float2;
+  using amp_t = float;
+  using coef_t = float2;
+  struct acc_t { fp2_t h, l; };        // (Re, Im) as FP32 pairs
+  struct inner_t { fp2_t i1, i2; };    // FP32 partial sums of one removal
+  static constexpr bool kInner = true;
+
+  static __device__ __forceinline__ amp_t amul(amp_t a, amp_t b) { return a * b; }
+  static __device__ __forceinline__ void zero(acc_t &a) { a.h = a.l = 0ull; }
+  static __device__ __forceinline__ void izero(inner_t &a) { a.i1 = a.i2 = 0ull; }
+  static __device__ __forceinline__ coef_t scale(coef_t c, amp_t x) { return make_float2(c.x * x, c.y * x); }
+  static __device__ __forceinline__ void imac(inner_t &a, coef_t k, vec_t v, bool real) {
+    const fp2_t Cv = fp2_make(v.x, v.y);
+    if (real) {
+      a.i1 = fp2_fma(fp2_make(k.x, k.x), Cv, a.i1);
+    } else {
+      const fp2_t Kp = fp2_make(k.x, k.y);
+      a.i1 = fp2_fma(Kp, Cv, a.i1);
+      a.i2 = fp2_fma(fp2_swap(Kp), Cv, a.i2);
+    }
+  }
+  static __device__ __forceinline__ void flush(acc_t &a, const inner_t &i, bool real) {
+    const fp2_t part = real ? i.i1
+                            : fp2_make(fp2_x(i.i1) - fp2_y(i.i1), fp2_x(i.i2) + fp2_y(i.i2));
+    fp2_dacc(a.h, a.l, part, 0ull);
+  }
+  static __device__ __forceinline__ float2 finish(const acc_t &a, double scale, bool) {
+    const float f = (float)scale;
+    const fp2_t v = fp2_add(a.h, a.l);
+    return make_float2(fp2_x(v) * f, fp2_y(v) * f);
   }
 };

@@ -84,6 +84,8 @@ struct FockAddition {
   int16_t a_index;    // pair index of (s, l) (two-body) or l (one-body)
 };
 
+struct FockTerm;
+
 struct fock_ham {
   const fock_space *sp;
   int device;
@@ -107,6 +109,8 @@ struct fock_ham {
   double *d_sqrt64;         // sqrt(i), i in [0, N+3]
   float2 *d_sqrtdf;         // (hi, lo) split of sqrt(i)
   float *d_sqrt32;
+  FockTerm *d_terms;        // [nadd] prefix-table offsets/corrections of each (removal, addition)
+  int32_t *d_slots;         // [nadd] jump-map slot of each term
   // workspace owned by the Hamiltonian (used when the caller passes none)
   void *ws;
   size_t ws_bytes;

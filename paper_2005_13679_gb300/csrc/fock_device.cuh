@@ -46,3 +46,8 @@ __device__ __forceinline__ Idx fock_rank_prefix(const int (&S)[MAXM], int M, Idx
     if (m <= M - 2) acc -= mod[(size_t)m * xdim + S[m] + m];
   return acc;
 }
+
+// 2^e for -1022 <= e <= 1023, built from the exponent field (exact, no call).
+__device__ __forceinline__ double fock_pow2(int e) {
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}

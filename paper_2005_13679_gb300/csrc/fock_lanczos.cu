@@ -2,10 +2,10 @@
 //
 // Krylov vectors are complex128 in device memory.  Inside a cycle of at most
 // restart_len vectors every new vector is orthogonalised against all previous
-// ones of the cycle (classical Gram-Schmidt applied twice); a cycle ends with
-// the Ritz vector of the lowest Ritz value, which starts the next cycle.  The
-// tridiagonal eigen-problem is solved on the host: Sturm-sequence bisection for
-// the lowest eigenvalue, inverse iteration for its vector.
+// ones of the cycle (classical Gram-Schmidt applied twice, the complete
+// re-orthogonalisation of Sec. 5); a cycle ends with a thick restart that keeps
+// the lowest Ritz vectors.  The small projected eigen-problem is solved on the
+// host by Jacobi rotations.
 //
 // With FOCK_PREC_F32_MIXED products the solver first converges to the mixed
 // floor (the apply's own error), then continues with FOCK_PREC_F64 products
@@ -29,7 +29,9 @@ struct Coeffs {
   double2 c[kChunk];
 };
 
-// partial[b][i] = sum over this block's elements of conj(V_i[x]) w[x]
+// partial[b][i] = sum over this block's elements of conj(V_i[x]) w[x].  With
+// REAL the vectors have zero imaginary parts and only real parts are combined.
+template <bool REAL>
 __global__ void dots_kernel(const double2 *__restrict__ V, int64_t ld, int k, int64_t n,
                             const double2 *__restrict__ w, double2 *__restrict__ partial) {
   double2 acc[kChunk];
@@ -37,14 +39,21 @@ __global__ void dots_kernel(const double2 *__restrict__ V, int64_t ld, int k, in
   for (int i = 0; i < kChunk; ++i) acc[i] = make_double2(0.0, 0.0);
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n;
        x += (int64_t)gridDim.x * blockDim.x) {
-    const double2 wx = w[x];
+    if (REAL) {
+      const double wx = w[x].x;
 #pragma unroll
-    for (int i = 0; i < kChunk; ++i)
-      if (i < k) {
-        const double2 v = V[i * ld + x];
-        acc[i].x = fma(v.x, wx.x, fma(v.y, wx.y, acc[i].x));
-        acc[i].y = fma(v.x, wx.y, fma(-v.y, wx.x, acc[i].y));
-      }
+      for (int i = 0; i < kChunk; ++i)
+        if (i < k) acc[i].x = fma(V[i * ld + x].x, wx, acc[i].x);
+    } else {
+      const double2 wx = w[x];
+#pragma unroll
+      for (int i = 0; i < kChunk; ++i)
+        if (i < k) {
+          const double2 v = V[i * ld + x];
+          acc[i].x = fma(v.x, wx.x, fma(v.y, wx.y, acc[i].x));
+          acc[i].y = fma(v.x, wx.y, fma(-v.y, wx.x, acc[i].y));
+        }
+    }
   }
   __shared__ double2 red[kChunk][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -68,22 +77,35 @@ __global__ void dots_kernel(const double2 *__restrict__ V, int64_t ld, int k, in
   }
 }
 
-// w[x] = beta * w[x] - sum_i c_i V_i[x]
+// w[x] = beta * w[x] - sum_i c_i V_i[x]  (REAL: real parts only; imaginary
+// parts stay exactly zero)
+template <bool REAL>
 __global__ void combine_kernel(const double2 *__restrict__ V, int64_t ld, int k, int64_t n,
                                Coeffs c, double beta, double2 *__restrict__ w) {
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n;
        x += (int64_t)gridDim.x * blockDim.x) {
-    double2 acc = w[x];
-    acc.x *= beta;
-    acc.y *= beta;
+    if (REAL) {
+      double acc = beta == 0.0 ? 0.0 : w[x].x * beta;   // beta = 0: w is write-only
 #pragma unroll
-    for (int i = 0; i < kChunk; ++i)
-      if (i < k) {
-        const double2 v = V[i * ld + x];
-        acc.x -= c.c[i].x * v.x - c.c[i].y * v.y;
-        acc.y -= c.c[i].x * v.y + c.c[i].y * v.x;
+      for (int i = 0; i < kChunk; ++i)
+        if (i < k) acc = fma(-c.c[i].x, V[i * ld + x].x, acc);
+      w[x] = make_double2(acc, 0.0);
+    } else {
+      double2 acc = make_double2(0.0, 0.0);
+      if (beta != 0.0) {
+        acc = w[x];
+        acc.x *= beta;
+        acc.y *= beta;
       }
-    w[x] = acc;
+#pragma unroll
+      for (int i = 0; i < kChunk; ++i)
+        if (i < k) {
+          const double2 v = V[i * ld + x];
+          acc.x -= c.c[i].x * v.x - c.c[i].y * v.y;
+          acc.y -= c.c[i].x * v.y + c.c[i].y * v.x;
+        }
+      w[x] = acc;
+    }
   }
 }
 
@@ -122,16 +144,17 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   return x ^ (x >> 31);
 }
 
-__global__ void random_start_kernel(uint64_t seed, int64_t n, double2 *__restrict__ y) {
+__global__ void random_start_kernel(uint64_t seed, int64_t n, bool real, double2 *__restrict__ y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t a = splitmix64(seed + 2 * (uint64_t)i), b = splitmix64(seed + 2 * (uint64_t)i + 1);
-    y[i] = make_double2((double)(a >> 11) * 0x1.0p-52 - 1.0, (double)(b >> 11) * 0x1.0p-52 - 1.0);
+    y[i] = make_double2((double)(a >> 11) * 0x1.0p-52 - 1.0, real ? 0.0 : (double)(b >> 11) * 0x1.0p-52 - 1.0);
   }
 }
 
 struct Ctx {
   int64_t n;
+  bool real;
   int sms;
   cudaStream_t s;
   double2 *partial_d;
@@ -148,7 +171,8 @@ int dots(Ctx &c, const double2 *V, int64_t ld, int k, const double2 *w, std::vec
   h.assign(k, make_double2(0.0, 0.0));
   for (int i0 = 0; i0 < k; i0 += kChunk) {
     const int kk = k - i0 < kChunk ? k - i0 : kChunk;
-    dots_kernel<<<kDotBlocks, 256, 0, c.s>>>(V + (size_t)i0 * ld, ld, kk, c.n, w, c.partial_d);
+    if (c.real) dots_kernel<true><<<kDotBlocks, 256, 0, c.s>>>(V + (size_t)i0 * ld, ld, kk, c.n, w, c.partial_d);
+    else dots_kernel<false><<<kDotBlocks, 256, 0, c.s>>>(V + (size_t)i0 * ld, ld, kk, c.n, w, c.partial_d);
     FOCK_CUDA_TRY(cudaGetLastError());
     FOCK_CUDA_TRY(cudaMemcpyAsync(c.partial_h.data(), c.partial_d, sizeof(double2) * kDotBlocks * kChunk,
                                   cudaMemcpyDeviceToHost, c.s));
@@ -179,7 +203,8 @@ int combine(Ctx &c, const double2 *V, int64_t ld, int k, const std::vector<doubl
     const int kk = k - i0 < kChunk ? k - i0 : kChunk;
     Coeffs cf;
     for (int i = 0; i < kChunk; ++i) cf.c[i] = i < kk ? h[i0 + i] : make_double2(0.0, 0.0);
-    combine_kernel<<<c.grid(), 256, 0, c.s>>>(V + (size_t)i0 * ld, ld, kk, c.n, cf, i0 == 0 ? beta : 1.0, w);
+    if (c.real) combine_kernel<true><<<c.grid(), 256, 0, c.s>>>(V + (size_t)i0 * ld, ld, kk, c.n, cf, i0 == 0 ? beta : 1.0, w);
+    else combine_kernel<false><<<c.grid(), 256, 0, c.s>>>(V + (size_t)i0 * ld, ld, kk, c.n, cf, i0 == 0 ? beta : 1.0, w);
     FOCK_CUDA_TRY(cudaGetLastError());
   }
   return FOCK_OK;
@@ -191,58 +216,58 @@ double norm(Ctx &c, const double2 *w, int *st) {
   return sqrt(fmax(h[0].x, 0.0));
 }
 
-// Number of eigenvalues of the symmetric tridiagonal (a, b) below x (Sturm count).
-int sturm_below(const std::vector<double> &a, const std::vector<double> &b, double x) {
-  int cnt = 0;
-  double d = 1.0;
-  for (size_t i = 0; i < a.size(); ++i) {
-    const double off = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
-    d = (a[i] - x) - (i > 0 ? off / d : 0.0);
-    if (d == 0.0) d = -1e-300;
-    if (d < 0.0) ++cnt;
+// Eigen-decomposition of a small dense symmetric matrix A (n x n, row-major)
+// by cyclic Jacobi rotations: each rotation zeroes one off-diagonal pair,
+// the sweeps repeat until the off-diagonal norm is negligible.  On return
+// evals[i] ascending and evecs[i*n + k] = component k of eigenvector i.
+void jacobi_eigen(std::vector<double> A, int n, std::vector<double> &evals, std::vector<double> &evecs) {
+  std::vector<double> Q((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        const double v = A[(size_t)i * n + j] * A[(size_t)i * n + j];
+        tot += v;
+        if (i != j) off += v;
+      }
+    if (off <= 1e-30 * tot || off == 0.0) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[(size_t)p * n + q];
+        if (apq == 0.0) continue;
+        const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+        const double th = (aqq - app) / (2.0 * apq);
+        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < n; ++k) {  // columns p, q
+          const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+          A[(size_t)k * n + p] = c * akp - sn * akq;
+          A[(size_t)k * n + q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // rows p, q
+          const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+          A[(size_t)p * n + k] = c * apk - sn * aqk;
+          A[(size_t)q * n + k] = sn * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {  // accumulate Q = Q R
+          const double qkp = Q[(size_t)k * n + p], qkq = Q[(size_t)k * n + q];
+          Q[(size_t)k * n + p] = c * qkp - sn * qkq;
+          Q[(size_t)k * n + q] = sn * qkp + c * qkq;
+        }
+      }
   }
-  return cnt;
-}
-
-// Lowest eigenpair of the symmetric tridiagonal matrix with diagonal a and
-// off-diagonal b (b[i] couples i and i+1).
-void lowest_eigenpair(const std::vector<double> &a, const std::vector<double> &b, double &theta,
-                      std::vector<double> &y) {
-  const size_t m = a.size();
-  double lo = a[0], hi = a[0];
-  for (size_t i = 0; i < m; ++i) {
-    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < m ? fabs(b[i]) : 0.0);
-    lo = fmin(lo, a[i] - r);
-    hi = fmax(hi, a[i] + r);
-  }
-  for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (sturm_below(a, b, mid) >= 1) hi = mid; else lo = mid;
-  }
-  theta = 0.5 * (lo + hi);
-  // inverse iteration on (T - theta I), shifted slightly below the eigenvalue
-  const double shift = theta - 1e-13 * fmax(fabs(theta), 1.0);
-  y.assign(m, 1.0);
-  std::vector<double> dd(m), ll(m), z(m);
-  for (int it = 0; it < 3; ++it) {
-    // LDL^T-free Thomas algorithm on the tridiagonal system
-    std::vector<double> cp(m), rhs(y);
-    double den = a[0] - shift;
-    if (fabs(den) < 1e-300) den = 1e-300;
-    cp[0] = m > 1 ? b[0] / den : 0.0;
-    rhs[0] = rhs[0] / den;
-    for (size_t i = 1; i < m; ++i) {
-      den = (a[i] - shift) - b[i - 1] * cp[i - 1];
-      if (fabs(den) < 1e-300) den = 1e-300;
-      cp[i] = i + 1 < m ? b[i] / den : 0.0;
-      rhs[i] = (rhs[i] - b[i - 1] * rhs[i - 1]) / den;
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  for (int i = 1; i < n; ++i)
+    for (int j = i; j > 0 && A[(size_t)order[j - 1] * n + order[j - 1]] > A[(size_t)order[j] * n + order[j]]; --j) {
+      int t = order[j]; order[j] = order[j - 1]; order[j - 1] = t;
     }
-    for (size_t i = m - 1; i-- > 0;) rhs[i] -= cp[i] * rhs[i + 1];
-    double nr = 0.0;
-    for (size_t i = 0; i < m; ++i) nr += rhs[i] * rhs[i];
-    nr = sqrt(nr);
-    for (size_t i = 0; i < m; ++i) y[i] = rhs[i] / nr;
+  evals.resize(n);
+  evecs.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    evals[i] = A[(size_t)order[i] * n + order[i]];
+    for (int k = 0; k < n; ++k) evecs[(size_t)i * n + k] = Q[(size_t)k * n + order[i]];
   }
 }
 
@@ -260,6 +285,9 @@ extern "C" int fock_lanczos_ground(const fock_space *sp, const fock_ham *ham, in
   if (cur != sp->device) return FOCK_ERR_DEVICE;
   Ctx c;
   c.n = sp->nc;
+  // A real Hamiltonian keeps a real start vector real: every product and every
+  // Gram-Schmidt step then has zero imaginary parts, which are skipped.
+  c.real = ham->real && start_dev == nullptr;
   c.sms = fock_get_sm_count(sp->device);
   c.s = (cudaStream_t)stream;
   c.partial_h.resize((size_t)kDotBlocks * kChunk);
@@ -286,7 +314,7 @@ extern "C" int fock_lanczos_ground(const fock_space *sp, const fock_ham *ham, in
     st = (x);                   \
     if (st) { cleanup(); return st; } \
   } while (0)
-  TRY(cudaMalloc(&V, sizeof(double2) * (size_t)n * (m + 1)) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
+  TRY(cudaMalloc(&V, sizeof(double2) * (size_t)n * (m + 8)) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
   TRY(cudaMalloc(&w, sizeof(double2) * (size_t)n) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
   TRY(cudaMalloc(&c.partial_d, sizeof(double2) * kDotBlocks * kChunk) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
   if (ws_bytes) TRY(cudaMalloc(&ws, ws_bytes) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
@@ -312,68 +340,81 @@ extern "C" int fock_lanczos_ground(const fock_space *sp, const fock_ham *ham, in
     TRY(cudaMemcpyAsync(V, start_dev, sizeof(double2) * n, cudaMemcpyDeviceToDevice, c.s) == cudaSuccess
             ? FOCK_OK : FOCK_ERR_CUDA);
   } else {
-    random_start_kernel<<<c.grid(), 256, 0, c.s>>>(seed, n, V);
+    random_start_kernel<<<c.grid(), 256, 0, c.s>>>(seed, n, c.real, V);
   }
   double nv = norm(c, V, &st);
   if (st) { cleanup(); return st; }
   if (!(nv > 0.0)) { cleanup(); return FOCK_ERR_ARG; }
   scale_copy_kernel<<<c.grid(), 256, 0, c.s>>>(V, 1.0 / nv, n, V);
 
+  // Thick restart (Wu and Simon): a cycle grows the basis V[0..j] of at most m
+  // vectors; at restart the `keep` lowest Ritz vectors and the last residual
+  // direction start the next cycle, with the projected matrix
+  //     T = [ diag(theta_i)  s ;  s^T  alpha ... ]  (arrowhead, then tridiagonal).
   const double mixed_floor = 1e-5;
+  const int keep = m >= 6 ? (m / 3 < 8 ? m / 3 : 8) : 1;
   int phase_prec = precision;
-  int total = 0;
+  int total = 0, p = 0;   // p: Ritz vectors carried into the cycle (V[0..p-1]), V[p] = residual
   double theta = 0.0;
   bool converged = false;
-  std::vector<double> alpha, beta, y;
+  std::vector<double> T((size_t)m * m, 0.0), evals, evecs;
   std::vector<double2> h, h2;
   while (true) {
-    alpha.clear();
-    beta.clear();
-    int j = 0;
-    double cur_tol = phase_prec == FOCK_PREC_F32_MIXED ? fmax(tol, mixed_floor) : tol;
-    bool stop_cycle = false, phase_done = false;
-    for (j = 0; j < m; ++j) {
+    const double cur_tol = phase_prec == FOCK_PREC_F32_MIXED ? fmax(tol, mixed_floor) : tol;
+    bool phase_done = false;
+    int j = p, dim = 0;
+    double b = 0.0;
+    for (j = p; j < m; ++j) {
       double2 *vj = V + (size_t)j * n;
       TRY(apply(phase_prec, vj, w));
       total += 1;
-      // full re-orthogonalisation against v_0..v_j (twice); its first pass
-      // also removes the alpha_j and beta_{j-1} components of the recurrence
+      // full re-orthogonalisation against v_0..v_j (twice)
       TRY(dots(c, V, n, j + 1, w, h));
-      const double a = h[j].x;
       TRY(combine(c, V, n, j + 1, h, 1.0, w));
       TRY(dots(c, V, n, j + 1, w, h2));
       TRY(combine(c, V, n, j + 1, h2, 1.0, w));
-      const double b = norm(c, w, &st);
+      b = norm(c, w, &st);
       if (st) { cleanup(); return st; }
-      alpha.push_back(a + h2[j].x);
-      lowest_eigenpair(alpha, beta, theta, y);
-      const double est = fabs(b * y[j]);
+      T[(size_t)j * m + j] = h[j].x + h2[j].x;
+      dim = j + 1;
+      std::vector<double> Tj((size_t)dim * dim);
+      for (int r = 0; r < dim; ++r)
+        for (int q = 0; q < dim; ++q) Tj[(size_t)r * dim + q] = T[(size_t)r * m + q];
+      jacobi_eigen(Tj, dim, evals, evecs);
+      theta = evals[0];
+      const double est = fabs(b * evecs[(size_t)0 * dim + j]);
       if (est <= cur_tol * fmax(fabs(theta), 1.0) || b <= 1e-300 * fmax(fabs(theta), 1.0)) phase_done = true;
-      if (phase_done || total >= max_iter || j == m - 1) {
-        stop_cycle = true;
-        break;
-      }
-      beta.push_back(b);
+      if (phase_done || total >= max_iter || j == m - 1) break;
+      T[(size_t)(j + 1) * m + j] = T[(size_t)j * m + j + 1] = b;
       scale_copy_kernel<<<c.grid(), 256, 0, c.s>>>(w, 1.0 / b, n, V + (size_t)(j + 1) * n);
     }
-    (void)stop_cycle;
-    // Ritz vector u = sum_i y_i v_i into w, normalised, then moved to v_0
-    const int kk = (int)alpha.size();
-    std::vector<double2> cy(kk);
-    for (int i = 0; i < kk; ++i) cy[i] = make_double2(-y[i], 0.0);
-    TRY(combine(c, V, n, kk, cy, 0.0, w));
-    double nu = norm(c, w, &st);
-    if (st) { cleanup(); return st; }
-    scale_copy_kernel<<<c.grid(), 256, 0, c.s>>>(w, 1.0 / nu, n, V);
-    if (phase_done) {
-      if (phase_prec == FOCK_PREC_F32_MIXED && tol < mixed_floor) {
-        phase_prec = FOCK_PREC_F64;  // final FP64 refinement
-      } else {
-        converged = true;
-        break;
-      }
+    const bool switch_phase = phase_done && phase_prec == FOCK_PREC_F32_MIXED && tol < mixed_floor;
+    const int np = (phase_done || total >= max_iter || switch_phase) ? 1 : (keep < dim ? keep : dim);
+    // Ritz vectors u_i = sum_k y_i[k] v_k into the spare slots V[m..], then V[0..np-1]
+    for (int i = 0; i < np; ++i) {
+      std::vector<double2> cy(dim);
+      for (int k = 0; k < dim; ++k) cy[k] = make_double2(-evecs[(size_t)i * dim + k], 0.0);
+      TRY(combine(c, V, n, dim, cy, 0.0, V + (size_t)(m + i) * n));
     }
+    for (int i = 0; i < np; ++i)
+      TRY(cudaMemcpyAsync(V + (size_t)i * n, V + (size_t)(m + i) * n, sizeof(double2) * n,
+                          cudaMemcpyDeviceToDevice, c.s) == cudaSuccess ? FOCK_OK : FOCK_ERR_CUDA);
+    if (phase_done && !switch_phase) { converged = true; break; }
     if (total >= max_iter) break;
+    std::fill(T.begin(), T.end(), 0.0);
+    if (switch_phase) {
+      phase_prec = FOCK_PREC_F64;  // final FP64 refinement from the current Ritz vector
+      p = 0;
+      continue;
+    }
+    // keep np Ritz pairs and the residual direction w / b
+    for (int i = 0; i < np; ++i) {
+      T[(size_t)i * m + i] = evals[i];
+      const double si = b * evecs[(size_t)i * dim + (dim - 1)];
+      T[(size_t)i * m + np] = T[(size_t)np * m + i] = si;
+    }
+    scale_copy_kernel<<<c.grid(), 256, 0, c.s>>>(w, 1.0 / b, n, V + (size_t)np * n);
+    p = np;
   }
   // Rayleigh quotient and residual with an FP64-class product
   TRY(apply(FOCK_PREC_F64, V, w));

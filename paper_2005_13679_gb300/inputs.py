@@ -154,6 +154,9 @@ WORKLOADS = {
     # Profiling size of the generic N, M = 6 workload: 17,259,390 configurations
     # (complex128 C of 276 MB, larger than L2), same kernel as N = 100.
     "generic_n70_m6": Workload("generic_n70_m6", N=70, M=6, kind="generic", seed=2),
+    # Profiling size of the Lieb-Liniger M = 10 workload: 20,160,075
+    # configurations (complex128 C of 323 MB, larger than L2).
+    "ll_n22_m10": Workload("ll_n22_m10", N=22, M=10, kind="ll", g=0.5, seed=3),
     # Generic Hermitian h/W, 20 bosons in 8 orbitals, a block of 16 vectors.
     "generic_n20_m8_rhs16": Workload("generic_n20_m8_rhs16", N=20, M=8, kind="generic", seed=4,
                                      nrhs=16, rhs_seeds=list(range(4000, 4016))),

@@ -66,3 +66,32 @@ def test_max_iter_reports_noconv(torch):
     E, res, it, _, st = fock.fock_lanczos_ground(sp.handle, H.handle, max_iter=3, restart_len=10,
                                                  tol=1e-14, seed=1)
     assert st == fock.FOCK_ERR_NOCONV and it == 3 and np.isfinite(E)
+
+
+def test_ll_n30_m10_precision_forms(torch):
+    """212M configurations: FP32-mixed products with FP64 orthogonalisation and
+    final FP64 refinement give the FP64 ground energy to 1e-10 relative.  No
+    oracle runs at this size; the energy is bracketed by the Bethe-ansatz energy
+    (variational bound, the plane-wave space is a subspace) and by the energy of
+    the condensate in the zero-momentum orbital, g N (N - 1) / 2L."""
+    w = inputs.WORKLOADS["ll_n30_m10"]
+    h, W = w.hamiltonian()
+    sp = fock.Space(w.N, w.M)
+    H = fock.Hamiltonian(sp, h, W)
+    runs = {}
+    for prec in (fock.FOCK_PREC_F64, fock.FOCK_PREC_F32_MIXED):
+        E, res, it, vec, st = fock.fock_lanczos_ground(sp.handle, H.handle, max_iter=300, restart_len=24,
+                                                       tol=1e-9, seed=w.lanczos_seed, precision=prec,
+                                                       want_vector=(prec == fock.FOCK_PREC_F64))
+        assert st == fock.FOCK_OK, (prec, E, res, it)
+        assert res <= 1e-6 * abs(E)
+        runs[prec] = (E, vec)
+    E64, v = runs[fock.FOCK_PREC_F64]
+    Emix = runs[fock.FOCK_PREC_F32_MIXED][0]
+    assert abs(Emix - E64) <= 1e-10 * abs(E64)
+    E_bethe, _ = oracle.bethe_ground_energy(w.N, w.g)
+    assert E_bethe < E64 < w.g * w.N * (w.N - 1) / 2.0
+    # error of one FP32-mixed product against the FP64-class product on the ground vector
+    s64 = H.apply(v, precision=fock.FOCK_PREC_F64)
+    s32 = H.apply(v.to(torch.complex64), precision=fock.FOCK_PREC_F32_MIXED).to(torch.complex128)
+    assert (torch.linalg.norm(s32 - s64) / torch.linalg.norm(s64)).item() <= 5e-6
