@@ -158,6 +158,65 @@ def run_reference(args, w):
     return 0
 
 
+# FP32 work of one executed term (one removal-addition pair of one configuration).
+# FP32-pair complex term: coefficient x amplitude (one packed pair product, 14
+# flop), two packed pair products with C (28) and two packed TwoSum
+# accumulations (28); real coefficients need one product and one accumulation.
+# FP32-mixed: packed multiply (2) and two packed FMAs (8).  Native FP64 counts its
+# own flops (coefficient scaling 4, complex FMA 8) on the FP64 pipe.
+FLOPS_PER_TERM = {"f64": 70, "f32_mixed": 10, "f64_native": 12}
+FLOPS_PER_TERM_REAL = {"f64": 35, "f32_mixed": 6, "f64_native": 8}
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
+
+
+def executed_terms(w, h, W):
+    """Removal-addition pairs the kernel visits: each listed two-body pair is
+    taken by the N_c(N-2, M) configurations that allow its removal (one-body:
+    N_c(N-1, M))."""
+    import numpy as np
+    N, M = w.N, w.M
+    nc = lambda n: math.comb(n + M - 1, M - 1) if n >= 0 else 0
+    if W is None or N < 2:
+        return nc(N - 1) * int(np.count_nonzero(h))
+    P = M * (M + 1) // 2
+    idx = {}
+    for k in range(M):
+        for q in range(k, M):
+            idx[(k, q)] = len(idx)
+    R = np.zeros((P, P), dtype=np.complex128)
+    for k in range(M):
+        for q in range(M):
+            for s in range(M):
+                for l in range(M):
+                    R[idx[(min(k, q), max(k, q))], idx[(min(s, l), max(s, l))]] += W[k, q, s, l]
+                    if q == s:
+                        R[idx[(min(k, q), max(k, q))], idx[(min(s, l), max(s, l))]] += h[k, l] / (N - 1)
+    return nc(N - 2) * int(np.count_nonzero(R))
+
+
+def load_traffic(workload, precision):
+    """DRAM bytes per launch of the main kernel from the committed ncu summary of
+    this workload, if its kernel sources still match (else None)."""
+    import glob
+    import hashlib
+    src = sorted(glob.glob(os.path.join(ROOT, "paper_2005_13679_gb300", "csrc", "*.cu*")))
+    digest = hashlib.sha256(b"".join(open(f, "rb").read() for f in src)).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}_{precision}.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("csrc_sha256_16") != digest:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def terms_formula(w, h, W):
     """Configuration terms of one apply (same definition as fock_hamiltonian_terms)."""
     import numpy as np
@@ -245,13 +304,35 @@ def main():
     wsz = fock.fock_apply_workspace_size(sp.handle, H.handle, w.nrhs, prec)
     wsb = torch.empty(max(wsz, 16), dtype=torch.uint8, device="cuda")
 
+    # one event pair per timed step around the library's main kernel
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for a_, b_ in kev:                      # materialise the CUDA events
+        a_.record(); b_.record()
+    torch.cuda.synchronize()
+    counter = {"i": -1}
+
     def step():
+        i = counter["i"]
+        if 0 <= i < len(kev):
+            fock.fock_apply_set_events(H.handle, kev[i][0], kev[i][1])
+        else:
+            fock.fock_apply_set_events(H.handle, None, None)
         fock.fock_apply_H(sp.handle, H.handle, Cd, sig, w.nrhs, prec, fock.FOCK_ARM_AUTO, wsb)
+
+    def step_timed():
+        counter["i"] += 1
+        step()
 
     clk = ClockSampler(local)
     clk.start()
-    ms = time_steps(torch, step, args.steps, args.warmup, barrier)
+    for _ in range(args.warmup):
+        step()
+    counter["i"] = -1
+    ms = time_steps(torch, step_timed, args.steps, 0, barrier)
     clocks = clk.stop()
+    fock.fock_apply_set_events(H.handle, None, None)
+    kernel_ms = sum(a_.elapsed_time(b_) for a_, b_ in kev) / len(kev)
     ms_all = ms
     if ws > 1:
         import torch.distributed as dist
@@ -275,6 +356,10 @@ def main():
 
     nbytes = w.nc * w.nrhs * elem
     hbm_gbs = 2 * nbytes / (ms * 1e-3) / 1e9
+    executed = executed_terms(w, h, W) * w.nrhs
+    flops_term = FLOPS_PER_TERM[args.precision] if not H.real else FLOPS_PER_TERM_REAL[args.precision]
+    achieved = executed * flops_term / (kernel_ms * 1e-3) / 1e12
+    traffic = load_traffic(w.name, args.precision)
     out = {
         "metric": METRIC, "value": value, "unit": "config-terms/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all,
@@ -286,6 +371,10 @@ def main():
         "applies_per_s": applies,
         "config_terms_per_apply": terms,
         "gpu_launches": (3 if prec == 0 else 1) * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                     "kernel_ms": kernel_ms, "executed_terms": executed, "flops_per_term": flops_term,
+                     "pipe": "FP32 (fma.rn.f32x2 and scalar); peak = 152 SMs x 128 lanes x 2 flop x 2070 MHz"},
         "hbm": {"compulsory_bytes": 2 * nbytes, "achieved_gbs": hbm_gbs, "peak_gbs": peaks["hbm_gbs"],
                 "frac": hbm_gbs / peaks["hbm_gbs"], "peak_source": peak_src},
         "e2e": {"value": terms / (e2e_ms * 1e-3), "unit": "config-terms/s",

@@ -178,6 +178,14 @@ int fock_hamiltonian_is_real(const fock_ham *ham, int *is_real);
 #define FOCK_ARM_HASH 1         /* target indices from the hash on the fly    */
 #define FOCK_ARM_MAPS 2         /* target indices from the built jump maps    */
 
+/* Profiling hook: when set, every apply with this Hamiltonian records
+ * start_event immediately before and stop_event immediately after its main
+ * H C kernel, on the apply's stream (the input preparation of FOCK_PREC_F64 is
+ * outside the pair).  Events are cudaEvent_t passed as void*, owned by the
+ * caller; NULL, NULL clears the hook.  Not thread-safe with concurrent applies
+ * on the same Hamiltonian. */
+int fock_apply_set_events(fock_ham *ham, void *start_event, void *stop_event);
+
 /* Device workspace (bytes) an apply with these options needs; 0 if none. */
 int fock_apply_workspace_size(const fock_space *sp, const fock_ham *ham, int32_t nrhs,
                               int precision, size_t *bytes);

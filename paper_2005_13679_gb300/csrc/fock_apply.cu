@@ -367,6 +367,13 @@ size_t fock_apply_ws_bytes(const fock_space *sp, const fock_ham *ham, int nrhs, 
   return kWsHeader + (size_t)sp->nc * (size_t)nrhs * sizeof(float4);
 }
 
+extern "C" int fock_apply_set_events(fock_ham *ham, void *start_event, void *stop_event) {
+  if (!ham || (!start_event) != (!stop_event)) return FOCK_ERR_ARG;
+  ham->ev_start = (cudaEvent_t)start_event;
+  ham->ev_stop = (cudaEvent_t)stop_event;
+  return FOCK_OK;
+}
+
 extern "C" int fock_apply_workspace_size(const fock_space *sp, const fock_ham *ham, int32_t nrhs,
                                          int precision, size_t *bytes) {
   if (!sp || !ham || !bytes || nrhs < 1 || nrhs > FOCK_MAX_NRHS) return FOCK_ERR_ARG;
@@ -419,6 +426,10 @@ static void fill_args(ApplyArgs<Idx> &a, const fock_space *sp, const fock_ham *h
   }
 }
 
+static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Cin, void *sigma, int nrhs,
+                       int precision, const int32_t *map, const int *in_exp, bool maps, bool nrhs16, int maxm,
+                       cudaStream_t stream);
+
 int fock_apply_internal(const fock_space *sp, const fock_ham *ham, const void *C, void *sigma,
                         int nrhs, int precision, int arm, void *ws, size_t ws_bytes,
                         cudaStream_t stream) {
@@ -461,6 +472,15 @@ int fock_apply_internal(const fock_space *sp, const fock_ham *ham, const void *C
     Cin = split;
   }
   const bool maps = map != nullptr;
+  if (ham->ev_start) FOCK_CUDA_TRY(cudaEventRecord(ham->ev_start, stream));
+  const int st = launch_main(sp, ham, Cin, sigma, nrhs, precision, map, in_exp, maps, nrhs16, maxm, stream);
+  if (st == FOCK_OK && ham->ev_stop) FOCK_CUDA_TRY(cudaEventRecord(ham->ev_stop, stream));
+  return st;
+}
+
+static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Cin, void *sigma, int nrhs,
+                       int precision, const int32_t *map, const int *in_exp, bool maps, bool nrhs16, int maxm,
+                       cudaStream_t stream) {
   if (sp->idx32) {
     ApplyArgs<uint32_t> a;
     fill_args(a, sp, ham, Cin, sigma, nrhs, precision, map, in_exp);

@@ -114,6 +114,8 @@ struct fock_ham {
   // workspace owned by the Hamiltonian (used when the caller passes none)
   void *ws;
   size_t ws_bytes;
+  // profiling hook (fock_apply_set_events)
+  cudaEvent_t ev_start, ev_stop;
   // buffers for fock_apply_H_host
   void *hb_in, *hb_out;
   size_t hb_bytes;

@@ -49,7 +49,7 @@ EXPORTS = (
     "fock_build_jump_maps", "fock_jump_map_get", "fock_jump_maps_free",
     "fock_hamiltonian_create", "fock_hamiltonian_destroy", "fock_hamiltonian_terms",
     "fock_hamiltonian_is_real",
-    "fock_apply_workspace_size", "fock_apply_H", "fock_apply_H_host", "fock_apply_H_noalloc",
+    "fock_apply_set_events", "fock_apply_workspace_size", "fock_apply_H", "fock_apply_H_host", "fock_apply_H_noalloc",
     "fock_lanczos_ground",
 )
 
@@ -94,6 +94,7 @@ def load(path: str | None = None):
         "fock_hamiltonian_destroy": [vp],
         "fock_hamiltonian_terms": [vp, P(i64)],
         "fock_hamiltonian_is_real": [vp, P(ctypes.c_int)],
+        "fock_apply_set_events": [vp, vp, vp],
         "fock_apply_workspace_size": [vp, vp, i32, ctypes.c_int, P(sz)],
         "fock_apply_H": [vp, vp, vp, vp, i32, ctypes.c_int, ctypes.c_int, vp, sz, vp],
         "fock_apply_H_host": [vp, vp, vp, vp, i32, ctypes.c_int, ctypes.c_int, vp],
@@ -241,6 +242,13 @@ def fock_hamiltonian_is_real(ham) -> bool:
     r = ctypes.c_int()
     _check(load().fock_hamiltonian_is_real(ham, ctypes.byref(r)), "fock_hamiltonian_is_real")
     return bool(r.value)
+
+
+def fock_apply_set_events(ham, start_event=None, stop_event=None) -> None:
+    """Record torch.cuda.Event objects around the main kernel of later applies."""
+    a = None if start_event is None else ctypes.c_void_p(start_event.cuda_event)
+    b = None if stop_event is None else ctypes.c_void_p(stop_event.cuda_event)
+    _check(load().fock_apply_set_events(ham, a, b), "fock_apply_set_events")
 
 
 def fock_apply_workspace_size(sp, ham, nrhs: int, precision: int) -> int:
