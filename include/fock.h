@@ -256,6 +256,59 @@ int fock_lanczos_ground(const fock_space *sp, const fock_ham *ham, int32_t max_i
                         const void *start_dev, double *E0, double *residual,
                         void *vec_dev, int32_t *iters, void *stream);
 
+/* ------------------------------------------------------------------------- */
+/* Uneven batches of independent problems                                    */
+/* ------------------------------------------------------------------------- */
+typedef struct fock_batch fock_batch;
+
+/* Stage `count` independent problems (N[i] bosons in M[i] orbitals with h[i],
+ * W[i] as for fock_hamiltonian_create; W[i] may be NULL) on the current
+ * device.  Their coefficient vectors are concatenated in instance order
+ * (instance i at offsets[i]..offsets[i+1], see fock_batch_offsets), complex
+ * interleaved.  One apply covers every instance in one persistent launch: a
+ * block takes work items (a range of configurations of one instance, largest
+ * instances first) from an atomic queue and stages that instance's tables in
+ * shared memory when the instance changes.  Requires N_c < 2^32 - 1 per
+ * instance.  Hermiticity is checked as in fock_hamiltonian_create with tol. */
+int fock_batch_create(int32_t count, const int32_t *N, const int32_t *M, const double *const *h_host,
+                      const double *const *W_host, double tol, fock_batch **out);
+int fock_batch_destroy(fock_batch *b);
+
+/* offsets[0..count] of the instances in concatenated vectors (host array). */
+int fock_batch_offsets(const fock_batch *b, int64_t *offsets);
+
+/* Sum of the instances' configuration terms (see fock_hamiltonian_terms). */
+int fock_batch_terms(const fock_batch *b, int64_t *config_terms);
+
+/* sigma = H_i C_i for every instance i, precision FOCK_PREC_F64 (complex128,
+ * FP32-pair arithmetic; one scale for the whole batch, so the instances'
+ * vectors should lie within 2^100 of each other in magnitude) or
+ * FOCK_PREC_F32_MIXED (complex64).  Buffers as for fock_apply_H, concatenated.
+ * Device scratch (queue counter, FP32-pair split copy) is owned by the batch.
+ * Asynchronous on `stream`. */
+int fock_batch_apply(fock_batch *b, const void *C_dev, void *sigma_dev, int precision, void *stream);
+
+/* Autotuner: times fock_batch_apply on the caller's buffers (contents are
+ * overwritten in sigma only) for work items of 1..32 tiles of 128
+ * configurations and 1..4 resident blocks per SM, keeps the fastest for this
+ * batch and precision, and reports it.  If cache_path is not NULL the choice
+ * is read from / appended to that text file, keyed by the instance sizes, the
+ * precision and the SM count.  Synchronous. */
+int fock_batch_autotune(fock_batch *b, const void *C_dev, void *sigma_dev, int precision,
+                        const char *cache_path, int32_t *tiles_per_item, int32_t *blocks_per_sm,
+                        void *stream);
+
+/* Lanczos ground state of every instance (as fock_lanczos_ground, FP64 Krylov
+ * vectors, FP64-class products, thick restart with restart_len vectors).  Each
+ * restart cycle of every instance runs as one CUDA graph replay: the batched
+ * apply, the segmented re-orthogonalisation, the norms and the scalings stay
+ * on the device; the host only solves the small projected problems between
+ * cycles.  E0_out, residual_out and iters_out have `count` entries.  Returns
+ * FOCK_ERR_NOCONV if any instance stopped at max_iter.  Synchronous. */
+int fock_batch_lanczos_ground(fock_batch *b, int32_t max_iter, int32_t restart_len, double tol,
+                              uint64_t seed, double *E0_out, double *residual_out, int32_t *iters_out,
+                              void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,7 @@ int fock_launch_sparse_mixed(const SparseArgs &, bool, bool, int, cudaStream_t);
 // change the prefix sums by d(m) = sum of +1 at and after each added orbital
 // and -1 at and after each removed one.  The sorted breakpoints and the values
 // of d between them become the byte offsets of the six prefix-table reads.
-static FockTerm make_term(int M, int k, int q, int s, int l) {
+static FockTerm make_term(int M, int k, int q, int s, int l, int maxm) {
   int pos[4], del[4], ne = 0;
   pos[ne] = k; del[ne++] = -1;
   if (q >= 0) { pos[ne] = q; del[ne++] = -1; }
@@ -58,7 +58,7 @@ static FockTerm make_term(int M, int k, int q, int s, int l) {
   int x[4], d[3];
   for (int i = 0; i < 4; ++i) x[i] = i < nu ? up[i] : up[nu - 1];
   for (int i = 0; i < 3; ++i) d[i] = i < nu - 1 ? ud[i] : 0;
-  const int maxm = fock_sparse_maxm(M);
+  (void)M;
   auto off = [&](int dd, int xx) { return (uint16_t)(((dd + 2) * maxm + xx) * FOCK_APPLY_THREADS * 4); };
   FockTerm T;
   for (int i = 0; i < 3; ++i) {
@@ -290,7 +290,7 @@ extern "C" int fock_hamiltonian_create(const fock_space *sp, const double *h_hos
   std::vector<int32_t> slots(nadd);
   for (const FockRemoval &e : rem)
     for (int i = e.a_beg; i < e.a_end; ++i) {
-      terms[i] = make_term(M, e.k, e.q, add[i].s, add[i].l);
+      terms[i] = make_term(M, e.k, e.q, add[i].s, add[i].l, fock_sparse_maxm(M));
       slots[i] = e.slot_base + add[i].a_index;
     }
   int st = FOCK_OK;
@@ -309,6 +309,19 @@ extern "C" int fock_hamiltonian_create(const fock_space *sp, const double *h_hos
     return st;
   }
   *out = H;
+  return FOCK_OK;
+}
+
+// Term records of a staged Hamiltonian encoded for prefix tables of `maxm`
+// rows (the batched kernel uses one width for all instances).
+int fock_make_terms(const fock_ham *ham, int maxm, FockTerm *out) {
+  const int M = ham->sp->M;
+  if (maxm < M) return FOCK_ERR_ARG;
+  for (int r = 0; r < ham->nrem; ++r) {
+    const FockRemoval &e = ham->h_rem[r];
+    for (int i = e.a_beg; i < e.a_end; ++i)
+      out[i] = make_term(M, e.k, e.q, ham->h_add[i].s, ham->h_add[i].l, maxm);
+  }
   return FOCK_OK;
 }
 
@@ -360,6 +373,25 @@ __global__ void fock_split_kernel(const double2 *__restrict__ x, int64_t n, cons
 }
 
 static const size_t kWsHeader = 256;
+
+
+// FP32-pair preparation of n complex128 values: max exponent, then the scaled
+// hi/lo split into ws + 256; ws[1] receives the output scale exponent.
+int fock_prepare_df(const void *C, int64_t n, void *ws, int device, cudaStream_t stream) {
+  int *words = (int *)ws;
+  float4 *split = (float4 *)((char *)ws + kWsHeader);
+  FOCK_CUDA_TRY(cudaMemsetAsync(words, 0, 8, stream));
+  const int sms = fock_get_sm_count(device);
+  int64_t blocks = (2 * n + 255) / 256;
+  if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+  fock_max_exponent_kernel<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, stream>>>((const double *)C, 2 * n, words);
+  blocks = (n + 255) / 256;
+  if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+  fock_split_kernel<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, stream>>>((const double2 *)C, n, words, split,
+                                                                             words + 1);
+  FOCK_CUDA_TRY(cudaGetLastError());
+  return FOCK_OK;
+}
 
 size_t fock_apply_ws_bytes(const fock_space *sp, const fock_ham *ham, int nrhs, int precision) {
   (void)ham;
@@ -455,21 +487,10 @@ int fock_apply_internal(const fock_space *sp, const fock_ham *ham, const void *C
     const size_t need = fock_apply_ws_bytes(sp, ham, nrhs, precision);
     if (!ws || ws_bytes < need) return FOCK_ERR_ARG;
     int *words = (int *)ws;  // [0] exponent bits, [1] output exponent
-    float4 *split = (float4 *)((char *)ws + kWsHeader);
-    const int64_t n = sp->nc * (int64_t)nrhs;
-    FOCK_CUDA_TRY(cudaMemsetAsync(words, 0, 8, stream));
-    const int sms = fock_get_sm_count(sp->device);
-    int64_t blocks = (2 * n + 255) / 256;
-    if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
-    fock_max_exponent_kernel<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, stream>>>(
-        (const double *)C, 2 * n, words);
-    blocks = (n + 255) / 256;
-    if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
-    fock_split_kernel<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, stream>>>(
-        (const double2 *)C, n, words, split, words + 1);
-    FOCK_CUDA_TRY(cudaGetLastError());
+    const int st0 = fock_prepare_df(C, sp->nc * (int64_t)nrhs, ws, sp->device, stream);
+    if (st0) return st0;
     in_exp = words + 1;
-    Cin = split;
+    Cin = (const char *)ws + kWsHeader;
   }
   const bool maps = map != nullptr;
   if (ham->ev_start) FOCK_CUDA_TRY(cudaEventRecord(ham->ev_start, stream));

@@ -51,6 +51,8 @@ EXPORTS = (
     "fock_hamiltonian_is_real",
     "fock_apply_set_events", "fock_apply_workspace_size", "fock_apply_H", "fock_apply_H_host", "fock_apply_H_noalloc",
     "fock_lanczos_ground",
+    "fock_batch_create", "fock_batch_destroy", "fock_batch_offsets", "fock_batch_terms", "fock_batch_apply",
+    "fock_batch_autotune", "fock_batch_lanczos_ground",
 )
 
 
@@ -102,6 +104,15 @@ def load(path: str | None = None):
         "fock_lanczos_ground": [vp, vp, i32, i32, dbl, ctypes.c_uint64, ctypes.c_int, vp,
                                 P(dbl), P(dbl), vp, P(i32), vp],
     }
+    sigs.update({
+        "fock_batch_create": [i32, vp, vp, vp, vp, dbl, P(vp)],
+        "fock_batch_destroy": [vp],
+        "fock_batch_offsets": [vp, vp],
+        "fock_batch_terms": [vp, P(i64)],
+        "fock_batch_apply": [vp, vp, vp, ctypes.c_int, vp],
+        "fock_batch_autotune": [vp, vp, vp, ctypes.c_int, ctypes.c_char_p, P(i32), P(i32), vp],
+        "fock_batch_lanczos_ground": [vp, i32, i32, dbl, ctypes.c_uint64, vp, vp, vp, vp],
+    })
     for name, args in sigs.items():
         f = getattr(lib, name)
         f.restype = ctypes.c_int
@@ -346,6 +357,71 @@ class Hamiltonian:
     def close(self):
         if self.handle:
             fock_hamiltonian_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------------
+# uneven batches
+# --------------------------------------------------------------------------
+class Batch:
+    """Independent problems [(N, M, h, W), ...] applied and solved together."""
+
+    def __init__(self, problems, tol: float = 1e-12):
+        self.count = len(problems)
+        Ns = np.array([p[0] for p in problems], dtype=np.int32)
+        Ms = np.array([p[1] for p in problems], dtype=np.int32)
+        self._h = [np.ascontiguousarray(np.asarray(p[2], dtype=np.complex128).reshape(-1)) for p in problems]
+        self._W = [None if p[3] is None else np.ascontiguousarray(np.asarray(p[3], dtype=np.complex128).reshape(-1))
+                   for p in problems]
+        hp = (ctypes.c_void_p * self.count)(*[a.ctypes.data for a in self._h])
+        Wp = (ctypes.c_void_p * self.count)(*[None if a is None else a.ctypes.data for a in self._W])
+        self.handle = ctypes.c_void_p()
+        _check(load().fock_batch_create(self.count, Ns.ctypes.data_as(ctypes.c_void_p),
+                                        Ms.ctypes.data_as(ctypes.c_void_p), hp, Wp, float(tol),
+                                        ctypes.byref(self.handle)), "fock_batch_create")
+        off = np.zeros(self.count + 1, dtype=np.int64)
+        _check(load().fock_batch_offsets(self.handle, off.ctypes.data_as(ctypes.c_void_p)), "fock_batch_offsets")
+        self.offsets = off
+        self.total = int(off[-1])
+        t = ctypes.c_int64()
+        _check(load().fock_batch_terms(self.handle, ctypes.byref(t)), "fock_batch_terms")
+        self.terms = t.value
+
+    def apply(self, C, sigma=None, precision=FOCK_PREC_F64, stream=None):
+        import torch
+        if sigma is None:
+            sigma = torch.empty_like(C)
+        _check(load().fock_batch_apply(self.handle, _dptr(C), _dptr(sigma), int(precision), _stream(stream)),
+               "fock_batch_apply")
+        return sigma
+
+    def autotune(self, C, sigma, precision=FOCK_PREC_F64, cache_path=None, stream=None):
+        t, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().fock_batch_autotune(self.handle, _dptr(C), _dptr(sigma), int(precision),
+                                          None if cache_path is None else str(cache_path).encode(),
+                                          ctypes.byref(t), ctypes.byref(b), _stream(stream)), "fock_batch_autotune")
+        return t.value, b.value
+
+    def lanczos_ground(self, max_iter=300, restart_len=12, tol=1e-10, seed=1, stream=None):
+        E = np.zeros(self.count)
+        R = np.zeros(self.count)
+        it = np.zeros(self.count, dtype=np.int32)
+        st = load().fock_batch_lanczos_ground(self.handle, int(max_iter), int(restart_len), float(tol),
+                                              ctypes.c_uint64(int(seed)), E.ctypes.data_as(ctypes.c_void_p),
+                                              R.ctypes.data_as(ctypes.c_void_p), it.ctypes.data_as(ctypes.c_void_p),
+                                              _stream(stream))
+        _check(st, "fock_batch_lanczos_ground", allow=(FOCK_ERR_NOCONV,))
+        return E, R, it, st
+
+    def close(self):
+        if self.handle:
+            load().fock_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
