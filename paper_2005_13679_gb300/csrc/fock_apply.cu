@@ -18,6 +18,7 @@
 
 #include "fock_apply_kernel.cuh"
 #include "fock_apply_sparse.cuh"
+#include "fock_apply_twophase.cuh"
 
 int fock_launch_apply_f64(const void *, bool, int, bool, bool, int, cudaStream_t);
 int fock_launch_apply_df(const void *, bool, int, bool, bool, int, cudaStream_t);
@@ -27,6 +28,7 @@ int fock_launch_dense_mixed(const ApplyArgs<uint32_t> &, bool, bool, int, cudaSt
 int fock_launch_sparse_f64(const SparseArgs &, bool, bool, int, cudaStream_t);
 int fock_launch_sparse_df(const SparseArgs &, bool, bool, int, cudaStream_t);
 int fock_launch_sparse_mixed(const SparseArgs &, bool, bool, int, cudaStream_t);
+int fock_launch_twophase(const TwoPhaseArgs &, bool, int, cudaStream_t);
 
 // Segment form of one term (see fock_apply_sparse.cuh): the removal (k, q)
 // (q = -1 for one particle) and the addition (s, l) (s = -1 for one particle)
@@ -399,6 +401,30 @@ size_t fock_apply_ws_bytes(const fock_space *sp, const fock_ham *ham, int nrhs, 
   return kWsHeader + (size_t)sp->nc * (size_t)nrhs * sizeof(float4);
 }
 
+// The two-phase evaluation (fock_apply_twophase.cuh) applies to dense reduced
+// coefficients with 2 <= M <= 8 and 32-bit indices, in the FP32-pair and
+// FP32-mixed forms; it needs an (N-2)-space buffer of P values per configuration.
+static bool twophase_eligible(const fock_space *sp, const fock_ham *ham, int precision) {
+  return ham->dense && sp->idx32 && sp->M >= 2 && sp->M <= 8 && sp->N >= 2 &&
+         (precision == FOCK_PREC_F64 || precision == FOCK_PREC_F32_MIXED);
+}
+
+static size_t twophase_y_offset(const fock_space *sp, const fock_ham *ham, int nrhs, int precision) {
+  return (fock_apply_ws_bytes(sp, ham, nrhs, precision) + 255) & ~(size_t)255;
+}
+
+static size_t twophase_y_bytes(const fock_space *sp, int nrhs, int precision) {
+  const int64_t nc2 = count_nm(sp->N - 2, sp->M);
+  const size_t elem = precision == FOCK_PREC_F32_MIXED ? sizeof(float2) : sizeof(float4);
+  return (size_t)fock_pair_count(sp->M) * (size_t)nc2 * (size_t)nrhs * elem;
+}
+
+// Workspace that selects the fastest path (the minimum is fock_apply_ws_bytes).
+size_t fock_apply_ws_pref(const fock_space *sp, const fock_ham *ham, int nrhs, int precision) {
+  if (!twophase_eligible(sp, ham, precision)) return fock_apply_ws_bytes(sp, ham, nrhs, precision);
+  return twophase_y_offset(sp, ham, nrhs, precision) + twophase_y_bytes(sp, nrhs, precision);
+}
+
 extern "C" int fock_apply_set_events(fock_ham *ham, void *start_event, void *stop_event) {
   if (!ham || (!start_event) != (!stop_event)) return FOCK_ERR_ARG;
   ham->ev_start = (cudaEvent_t)start_event;
@@ -410,7 +436,7 @@ extern "C" int fock_apply_workspace_size(const fock_space *sp, const fock_ham *h
                                          int precision, size_t *bytes) {
   if (!sp || !ham || !bytes || nrhs < 1 || nrhs > FOCK_MAX_NRHS) return FOCK_ERR_ARG;
   if (precision < FOCK_PREC_F64 || precision > FOCK_PREC_F32_MIXED) return FOCK_ERR_ARG;
-  *bytes = fock_apply_ws_bytes(sp, ham, nrhs, precision);
+  *bytes = fock_apply_ws_pref(sp, ham, nrhs, precision);
   return FOCK_OK;
 }
 
@@ -460,7 +486,7 @@ static void fill_args(ApplyArgs<Idx> &a, const fock_space *sp, const fock_ham *h
 
 static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Cin, void *sigma, int nrhs,
                        int precision, const int32_t *map, const int *in_exp, bool maps, bool nrhs16, int maxm,
-                       cudaStream_t stream);
+                       void *ws, size_t ws_bytes, cudaStream_t stream);
 
 int fock_apply_internal(const fock_space *sp, const fock_ham *ham, const void *C, void *sigma,
                         int nrhs, int precision, int arm, void *ws, size_t ws_bytes,
@@ -494,17 +520,27 @@ int fock_apply_internal(const fock_space *sp, const fock_ham *ham, const void *C
   }
   const bool maps = map != nullptr;
   if (ham->ev_start) FOCK_CUDA_TRY(cudaEventRecord(ham->ev_start, stream));
-  const int st = launch_main(sp, ham, Cin, sigma, nrhs, precision, map, in_exp, maps, nrhs16, maxm, stream);
+  const int st = launch_main(sp, ham, Cin, sigma, nrhs, precision, map, in_exp, maps, nrhs16, maxm, ws, ws_bytes,
+                             stream);
   if (st == FOCK_OK && ham->ev_stop) FOCK_CUDA_TRY(cudaEventRecord(ham->ev_stop, stream));
   return st;
 }
 
 static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Cin, void *sigma, int nrhs,
                        int precision, const int32_t *map, const int *in_exp, bool maps, bool nrhs16, int maxm,
-                       cudaStream_t stream) {
+                       void *ws, size_t ws_bytes, cudaStream_t stream) {
   if (sp->idx32) {
     ApplyArgs<uint32_t> a;
     fill_args(a, sp, ham, Cin, sigma, nrhs, precision, map, in_exp);
+    // Dense coefficients, M <= 8, enough workspace: evaluate through H(N-2, M).
+    if (!maps && ws && twophase_eligible(sp, ham, precision) &&
+        ws_bytes >= fock_apply_ws_pref(sp, ham, nrhs, precision)) {
+      TwoPhaseArgs t;
+      t.a = a;
+      t.nc2 = (uint32_t)count_nm(sp->N - 2, sp->M);
+      t.Y = (char *)ws + twophase_y_offset(sp, ham, nrhs, precision);
+      return fock_launch_twophase(t, precision == FOCK_PREC_F32_MIXED, sp->device, stream);
+    }
     // Every reduced coefficient present and M <= 10: the register-resident
     // kernel with the addition loop unrolled at compile time.
     if (ham->dense && sp->M <= 10 && !(maps && nrhs16)) {
@@ -565,7 +601,7 @@ extern "C" int fock_apply_H(const fock_space *sp, const fock_ham *ham, const voi
   int st = check_apply_args(sp, ham, nrhs, precision, arm);
   if (st) return st;
   if (!C_dev || !sigma_dev) return FOCK_ERR_ARG;
-  const size_t need = fock_apply_ws_bytes(sp, ham, nrhs, precision);
+  const size_t need = fock_apply_ws_pref(sp, ham, nrhs, precision);
   if (need > 0 && !workspace_dev) {
     st = grow_ws((fock_ham *)ham, need);
     if (st) return st;
@@ -593,7 +629,7 @@ extern "C" int fock_apply_H_host(const fock_space *sp, const fock_ham *ham, cons
     FOCK_CUDA_TRY(cudaMalloc(&H->hb_out, bytes));
     H->hb_bytes = bytes;
   }
-  const size_t need = fock_apply_ws_bytes(sp, ham, nrhs, precision);
+  const size_t need = fock_apply_ws_pref(sp, ham, nrhs, precision);
   if (need > 0) {
     st = grow_ws(H, need);
     if (st) return st;

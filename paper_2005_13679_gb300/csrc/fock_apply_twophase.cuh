@@ -1,0 +1,417 @@
+// fock_apply_twophase.cuh -- sigma = H C for dense reduced coefficients,
+// evaluated through the (N-2)-particle space.
+//
+// With n' = gamma - e_k - e_q the configuration left after a removal r, the
+// pull form reads sigma_gamma = sum_r A_r(gamma) Y[r][n'], where
+//
+//     X[a][n'] = B_a(n') C[n' + a],         B_a(n') = sqrt((n'_s + 1)(n'_l + 1 + delta_sl)),
+//     Y[r][n'] = sum_a R[r][a] X[a][n'],    A_r(gamma) = sqrt(n_k (n_q - delta_kq)).
+//
+// Phase 1 runs one thread per n' in H(N-2, M): P gathers of C build X in the
+// thread's slice of shared memory, a dense P x P product with the staged R
+// gives Y, written r-major (consecutive n' consecutive in memory).  Phase 2 runs
+// one thread per gamma and gathers P entries of Y.  The multiply-accumulate
+// count is the same as the direct pull form, but each C value is gathered once
+// per n' instead of once per (gamma, r), and the inner product needs no index
+// or amplitude arithmetic.
+#pragma once
+
+#include "fock_apply_dense.cuh"
+
+struct TwoPhaseArgs {
+  ApplyArgs<uint32_t> a;          // N-space tables, coefficients (dense, r*P + a), C, sigma, nrhs, scales
+  uint32_t nc2;                   // N_c(N - 2, M)
+  void *Y;                        // [P][nc2 * nrhs]
+};
+
+template <int M>
+struct TwoPhaseSmem {
+  static constexpr int P = M * (M + 1) / 2;
+  size_t off_coef, off_pair, off_mod, off_sat, off_sq, off_x, total;
+  // priv_bytes: bytes of each thread's private area
+  __host__ __device__ TwoPhaseSmem(int xdim, int nsq, size_t coef_bytes, size_t priv_bytes, int threads) {
+    const int rows = M > 1 ? M - 1 : 1;
+    size_t o = 0;
+    off_coef = o; o = fock_align16(o + coef_bytes * P * P);
+    off_pair = o; o = fock_align16(o + 2 * P);
+    off_mod = o;  o = fock_align16(o + 4 * (size_t)rows * xdim);
+    off_sat = o;  o = fock_align16(o + 4 * (size_t)rows * xdim);
+    off_sq = o;   o = fock_align16(o + 8 * (size_t)nsq);
+    off_x = o;    o = fock_align16(o + priv_bytes * (size_t)threads);
+    total = o;
+  }
+};
+
+// Target base and prefix differences of n' for adding two particles back
+// (the (N-2)-space configuration itself, no removal).
+template <int M>
+__device__ __forceinline__ uint32_t twophase_targets(const int (&S)[M], const uint32_t *s_mod, int xdim, uint32_t nc,
+                                                     uint32_t (&U)[M], uint32_t (&V)[M]) {
+  uint32_t F0 = 0, F1 = 0, F2 = 0;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    U[m] = F0 - F1;
+    V[m] = F1 - F2;
+    if (m < M - 1) {
+      const uint32_t *row = s_mod + m * xdim + (S[m] + m);
+      F0 += row[0];
+      F1 += row[1];
+      F2 += row[2];
+    }
+  }
+  return nc - 1u - F2;
+}
+
+// Index in H(N-2, M) of gamma minus particles at k and q.
+template <int M>
+__device__ __forceinline__ uint32_t twophase_rank2(const int (&S)[M], int kk, int qq, const uint32_t *s_mod, int xdim,
+                                                   uint32_t nc2) {
+  uint32_t acc = nc2 - 1u;
+#pragma unroll
+  for (int m = 0; m < M - 1; ++m) acc -= s_mod[m * xdim + (S[m] - (kk <= m) - (qq <= m) + m)];
+  return acc;
+}
+
+// Per-thread slice of phase 1: prefix differences and square roots of n'.
+struct TwoPhaseSlot {
+  uint32_t U, V;
+  float bh, bl;       // sqrt(n'_m + 1) as a pair
+  float ch, cl;       // sqrt(n'_m + 2) as a pair
+};
+
+// Stage coefficients, addition pairs, binomial tables and square roots.
+template <int M, class CoefT, class SqT>
+__device__ __forceinline__ void twophase_stage(const ApplyArgs<uint32_t> &a, const TwoPhaseSmem<M> &L,
+                                               unsigned char *smem) {
+  constexpr int P = TwoPhaseSmem<M>::P;
+  CoefT *s_coef = (CoefT *)(smem + L.off_coef);
+  int8_t *s_pair = (int8_t *)(smem + L.off_pair);
+  uint32_t *s_mod = (uint32_t *)(smem + L.off_mod);
+  uint32_t *s_sat = (uint32_t *)(smem + L.off_sat);
+  SqT *s_sq = (SqT *)(smem + L.off_sq);
+  const int rows = M > 1 ? M - 1 : 1;
+  for (int i = threadIdx.x; i < P * P; i += blockDim.x) s_coef[i] = ((const CoefT *)a.coef)[i];
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    // addition pair i = (s, l), s <= l, lexicographic
+    int s = 0, r = i;
+    while (r >= M - s) {
+      r -= M - s;
+      ++s;
+    }
+    s_pair[2 * i] = (int8_t)s;
+    s_pair[2 * i + 1] = (int8_t)(s + r);
+  }
+  for (int i = threadIdx.x; i < rows * a.xdim; i += blockDim.x) {
+    s_mod[i] = a.mod[i];
+    s_sat[i] = a.sat[i];
+  }
+  for (int i = threadIdx.x; i < a.nsq; i += blockDim.x) s_sq[i] = ((const SqT *)a.sq)[i];
+  __syncthreads();
+}
+
+// Decode n' and fill the thread's slots; returns the target base in H(N, M).
+template <int M, class SqT>
+__device__ __forceinline__ uint32_t twophase_slots(uint32_t gc, const ApplyArgs<uint32_t> &a, uint32_t nc2,
+                                                   const uint32_t *s_mod, const uint32_t *s_sat, const SqT *s_sq,
+                                                   TwoPhaseSlot *slot, int nt) {
+  int S[M];
+  fock_decode_prefix<uint32_t, M>(gc, a.N - 2, M, nc2, s_sat, a.xdim, S);
+  uint32_t U[M], V[M];
+  const uint32_t base = twophase_targets<M>(S, s_mod, a.xdim, a.nc, U, V);
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int np = S[m] - (m > 0 ? S[m - 1] : 0);
+    TwoPhaseSlot z;
+    z.U = U[m];
+    z.V = V[m];
+    if constexpr (sizeof(SqT) == 8) {
+      const float2 b = ((const float2 *)s_sq)[np + 1], c = ((const float2 *)s_sq)[np + 2];
+      z.bh = b.x; z.bl = b.y; z.ch = c.x; z.cl = c.y;
+    } else {
+      z.bh = ((const float *)s_sq)[np + 1]; z.bl = 0.f;
+      z.ch = ((const float *)s_sq)[np + 2]; z.cl = 0.f;
+    }
+    slot[m * nt] = z;
+  }
+  return base;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 pairs
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(FOCK_APPLY_THREADS, 4)
+fock_twophase_x_df(const TwoPhaseArgs t) {
+  constexpr int P = TwoPhaseSmem<M>::P;
+  constexpr int RB = 8;   // removals accumulated in registers per sweep over the additions
+  const ApplyArgs<uint32_t> &a = t.a;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const TwoPhaseSmem<M> L(a.xdim, a.nsq, sizeof(float4), sizeof(TwoPhaseSlot) * M, blockDim.x);
+  twophase_stage<M, float4, float2>(a, L, smem);
+  const float4 *s_coef = (const float4 *)(smem + L.off_coef);
+  const int8_t *s_pair = (const int8_t *)(smem + L.off_pair);
+  const uint32_t *s_mod = (const uint32_t *)(smem + L.off_mod);
+  const uint32_t *s_sat = (const uint32_t *)(smem + L.off_sat);
+  const float2 *s_sq = (const float2 *)(smem + L.off_sq);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  TwoPhaseSlot *slot = (TwoPhaseSlot *)(smem + L.off_x) + tid;   // slot[m * nt]
+  const uint32_t nc2 = t.nc2;
+  const int nrhs = a.nrhs;
+  const float4 *__restrict__ C = (const float4 *)a.C;
+  float4 *__restrict__ Y = (float4 *)t.Y;
+  const size_t ldy = (size_t)nc2 * nrhs;
+
+  for (uint32_t tile = blockIdx.x * (uint32_t)nt; tile < nc2; tile += gridDim.x * (uint32_t)nt) {
+    const uint32_t g = tile + tid;
+    const bool live = g < nc2;
+    const uint32_t base = twophase_slots<M, float2>(live ? g : nc2 - 1u, a, nc2, s_mod, s_sat, s_sq, slot, nt);
+    for (int j = 0; j < nrhs; ++j) {
+      for (int r0 = 0; r0 < P; r0 += RB) {
+        fp2_t A1h[RB], A1l[RB], A2h[RB], A2l[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) A1h[q] = A1l[q] = A2h[q] = A2l[q] = 0ull;
+#pragma unroll 2
+        for (int ai = 0; ai < P; ++ai) {
+          // X = B_a(n') C[n' + a] as an FP32 pair (both lanes: Re, Im)
+          const int s = s_pair[2 * ai], l = s_pair[2 * ai + 1];
+          const TwoPhaseSlot zs = slot[s * nt], zl = slot[l * nt];
+          const float2 amp = df_mul(make_float2(zs.bh, zs.bl), s == l ? make_float2(zs.ch, zs.cl)
+                                                                       : make_float2(zl.bh, zl.bl));
+          const float4 v = __ldg(C + (size_t)(base - zs.U - zl.V) * nrhs + j);
+          fp2_t Xh, Xl;
+          fp2_dprod(fp2_make(v.x, v.y), fp2_make(v.z, v.w), fp2_make(amp.x, amp.x), fp2_make(amp.y, amp.y), Xh, Xl);
+          const fp2_t Xsh = fp2_swap(Xh), Xsl = fp2_swap(Xl);
+#pragma unroll
+          for (int q = 0; q < RB; ++q) {
+            if (r0 + q < P) {
+              const float4 w = s_coef[(r0 + q) * P + ai];
+              const fp2_t Rh = fp2_make(w.x, w.y), Rl = fp2_make(w.z, w.w);
+              fp2_t p, e;
+              fp2_dprod(Rh, Rl, Xh, Xl, p, e);     // (Re R Re X, Im R Im X)
+              fp2_dacc(A1h[q], A1l[q], p, e);
+              fp2_dprod(Rh, Rl, Xsh, Xsl, p, e);   // (Re R Im X, Im R Re X)
+              fp2_dacc(A2h[q], A2l[q], p, e);
+            }
+          }
+        }
+        if (live) {
+#pragma unroll
+          for (int q = 0; q < RB; ++q) {
+            if (r0 + q < P) {
+              float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+              df_add_acc(rh, rl, fp2_x(A1h[q]), fp2_x(A1l[q]));
+              df_add_acc(rh, rl, -fp2_y(A1h[q]), -fp2_y(A1l[q]));
+              df_add_acc(ih, il, fp2_x(A2h[q]), fp2_x(A2l[q]));
+              df_add_acc(ih, il, fp2_y(A2h[q]), fp2_y(A2l[q]));
+              Y[(size_t)(r0 + q) * ldy + (size_t)g * nrhs + j] = make_float4(rh, ih, rl, il);
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int M>
+__global__ void __launch_bounds__(FOCK_APPLY_THREADS)
+fock_twophase_sigma_df(const TwoPhaseArgs t) {
+  constexpr int P = TwoPhaseSmem<M>::P;
+  const ApplyArgs<uint32_t> &a = t.a;
+  extern __shared__ __align__(16) unsigned char smem[];
+  int8_t *s_pair = (int8_t *)smem;
+  uint32_t *s_mod = (uint32_t *)(smem + 256);
+  const int rows = M > 1 ? M - 1 : 1;
+  uint32_t *s_sat = s_mod + rows * a.xdim;
+  float2 *s_sq = (float2 *)(s_sat + rows * a.xdim + 4);
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    s_pair[2 * i] = a.rem[i].k;
+    s_pair[2 * i + 1] = a.rem[i].q;
+  }
+  for (int i = threadIdx.x; i < rows * a.xdim; i += blockDim.x) {
+    s_mod[i] = a.mod[i];
+    s_sat[i] = a.sat[i];
+  }
+  for (int i = threadIdx.x; i < a.nsq; i += blockDim.x) s_sq[i] = ((const float2 *)a.sq)[i];
+  __syncthreads();
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const uint32_t nc = a.nc, nc2 = t.nc2;
+  const int nrhs = a.nrhs;
+  const float4 *__restrict__ Y = (const float4 *)t.Y;
+  const size_t ldy = (size_t)nc2 * nrhs;
+  double out_scale = a.out_scale;
+  if (a.in_exp) out_scale *= fock_pow2(__ldg(a.in_exp));
+
+  for (uint32_t tile = blockIdx.x * (uint32_t)nt; tile < nc; tile += gridDim.x * (uint32_t)nt) {
+    const uint32_t g = tile + tid;
+    const bool live = g < nc;
+    int S[M], n[M];
+    fock_decode_prefix<uint32_t, M>(live ? g : nc - 1u, a.N, M, nc, s_sat, a.xdim, S);
+#pragma unroll
+    for (int m = 0; m < M; ++m) n[m] = S[m] - (m > 0 ? S[m - 1] : 0);
+    for (int j = 0; j < nrhs; ++j) {
+      fp2_t Ah = 0ull, Al = 0ull;
+      for (int r = 0; r < P; ++r) {
+        const int k = s_pair[2 * r], q = s_pair[2 * r + 1];
+        const int nk = sel_occ<M>(n, k), nq = sel_occ<M>(n, q);
+        const bool valid = live && (k == q ? nk >= 2 : (nk >= 1 && nq >= 1));
+        if (!__any_sync(0xffffffffu, valid)) continue;
+        const uint32_t r2 = valid ? twophase_rank2<M>(S, k, q, s_mod, a.xdim, nc2) : 0u;
+        const float2 A = df_mul(s_sq[valid ? nk : 0], s_sq[valid ? nq - (k == q) : 0]);
+        const float4 y = __ldg(Y + (size_t)r * ldy + (size_t)r2 * nrhs + j);
+        fp2_t p, e;
+        fp2_dprod(fp2_make(y.x, y.y), fp2_make(y.z, y.w), fp2_make(A.x, A.x), fp2_make(A.y, A.y), p, e);
+        fp2_dacc(Ah, Al, p, e);
+      }
+      if (live) {
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+        df_add_acc(rh, rl, fp2_x(Ah), fp2_x(Al));
+        df_add_acc(ih, il, fp2_y(Ah), fp2_y(Al));
+        ((double2 *)a.sigma)[(size_t)g * nrhs + j] =
+            make_double2(((double)rh + (double)rl) * out_scale, ((double)ih + (double)il) * out_scale);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32-mixed
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(FOCK_APPLY_THREADS, 4)
+fock_twophase_x_mixed(const TwoPhaseArgs t) {
+  constexpr int P = TwoPhaseSmem<M>::P;
+  constexpr int RB = 12;
+  const ApplyArgs<uint32_t> &a = t.a;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const TwoPhaseSmem<M> L(a.xdim, a.nsq, sizeof(float2), sizeof(TwoPhaseSlot) * M, blockDim.x);
+  twophase_stage<M, float2, float>(a, L, smem);
+  const float2 *s_coef = (const float2 *)(smem + L.off_coef);
+  const int8_t *s_pair = (const int8_t *)(smem + L.off_pair);
+  const uint32_t *s_mod = (const uint32_t *)(smem + L.off_mod);
+  const uint32_t *s_sat = (const uint32_t *)(smem + L.off_sat);
+  const float *s_sq = (const float *)(smem + L.off_sq);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  TwoPhaseSlot *slot = (TwoPhaseSlot *)(smem + L.off_x) + tid;
+  const uint32_t nc2 = t.nc2;
+  const int nrhs = a.nrhs;
+  const float2 *__restrict__ C = (const float2 *)a.C;
+  float2 *__restrict__ Y = (float2 *)t.Y;
+  const size_t ldy = (size_t)nc2 * nrhs;
+
+  for (uint32_t tile = blockIdx.x * (uint32_t)nt; tile < nc2; tile += gridDim.x * (uint32_t)nt) {
+    const uint32_t g = tile + tid;
+    const bool live = g < nc2;
+    const uint32_t base = twophase_slots<M, float>(live ? g : nc2 - 1u, a, nc2, s_mod, s_sat, s_sq, slot, nt);
+    for (int j = 0; j < nrhs; ++j) {
+      for (int r0 = 0; r0 < P; r0 += RB) {
+        fp2_t A1[RB], A2[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) A1[q] = A2[q] = 0ull;
+#pragma unroll 2
+        for (int ai = 0; ai < P; ++ai) {
+          const int s = s_pair[2 * ai], l = s_pair[2 * ai + 1];
+          const TwoPhaseSlot zs = slot[s * nt], zl = slot[l * nt];
+          const float amp = zs.bh * (s == l ? zs.ch : zl.bh);
+          const float2 v = __ldg(C + (size_t)(base - zs.U - zl.V) * nrhs + j);
+          const fp2_t Xp = fp2_make(v.x * amp, v.y * amp), Xs = fp2_make(v.y * amp, v.x * amp);
+#pragma unroll
+          for (int q = 0; q < RB; ++q) {
+            if (r0 + q < P) {
+              const float2 w = s_coef[(r0 + q) * P + ai];
+              const fp2_t Rp = fp2_make(w.x, w.y);
+              A1[q] = fp2_fma(Rp, Xp, A1[q]);   // (Re R Re X, Im R Im X)
+              A2[q] = fp2_fma(Rp, Xs, A2[q]);   // (Re R Im X, Im R Re X)
+            }
+          }
+        }
+        if (live) {
+#pragma unroll
+          for (int q = 0; q < RB; ++q)
+            if (r0 + q < P)
+              Y[(size_t)(r0 + q) * ldy + (size_t)g * nrhs + j] =
+                  make_float2(fp2_x(A1[q]) - fp2_y(A1[q]), fp2_x(A2[q]) + fp2_y(A2[q]));
+        }
+      }
+    }
+  }
+}
+
+template <int M>
+__global__ void __launch_bounds__(FOCK_APPLY_THREADS)
+fock_twophase_sigma_mixed(const TwoPhaseArgs t) {
+  constexpr int P = TwoPhaseSmem<M>::P;
+  const ApplyArgs<uint32_t> &a = t.a;
+  extern __shared__ __align__(16) unsigned char smem[];
+  int8_t *s_pair = (int8_t *)smem;
+  uint32_t *s_mod = (uint32_t *)(smem + 256);
+  const int rows = M > 1 ? M - 1 : 1;
+  uint32_t *s_sat = s_mod + rows * a.xdim;
+  float *s_sq = (float *)(s_sat + rows * a.xdim + 4);
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    s_pair[2 * i] = a.rem[i].k;
+    s_pair[2 * i + 1] = a.rem[i].q;
+  }
+  for (int i = threadIdx.x; i < rows * a.xdim; i += blockDim.x) {
+    s_mod[i] = a.mod[i];
+    s_sat[i] = a.sat[i];
+  }
+  for (int i = threadIdx.x; i < a.nsq; i += blockDim.x) s_sq[i] = ((const float *)a.sq)[i];
+  __syncthreads();
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const uint32_t nc = a.nc, nc2 = t.nc2;
+  const int nrhs = a.nrhs;
+  const float2 *__restrict__ Y = (const float2 *)t.Y;
+  const size_t ldy = (size_t)nc2 * nrhs;
+  const float out_scale = (float)a.out_scale;
+
+  for (uint32_t tile = blockIdx.x * (uint32_t)nt; tile < nc; tile += gridDim.x * (uint32_t)nt) {
+    const uint32_t g = tile + tid;
+    const bool live = g < nc;
+    int S[M], n[M];
+    fock_decode_prefix<uint32_t, M>(live ? g : nc - 1u, a.N, M, nc, s_sat, a.xdim, S);
+#pragma unroll
+    for (int m = 0; m < M; ++m) n[m] = S[m] - (m > 0 ? S[m - 1] : 0);
+    for (int j = 0; j < nrhs; ++j) {
+      fp2_t Sh = 0ull, Sl = 0ull;
+      for (int r = 0; r < P; ++r) {
+        const int k = s_pair[2 * r], q = s_pair[2 * r + 1];
+        const int nk = sel_occ<M>(n, k), nq = sel_occ<M>(n, q);
+        const bool valid = live && (k == q ? nk >= 2 : (nk >= 1 && nq >= 1));
+        if (!__any_sync(0xffffffffu, valid)) continue;
+        const uint32_t r2 = valid ? twophase_rank2<M>(S, k, q, s_mod, a.xdim, nc2) : 0u;
+        const float A = s_sq[valid ? nk : 0] * s_sq[valid ? nq - (k == q) : 0];
+        const float2 y = __ldg(Y + (size_t)r * ldy + (size_t)r2 * nrhs + j);
+        fp2_dacc(Sh, Sl, fp2_make(y.x * A, y.y * A), 0ull);
+      }
+      if (live) {
+        const fp2_t v = fp2_add(Sh, Sl);
+        ((float2 *)a.sigma)[(size_t)g * nrhs + j] = make_float2(fp2_x(v) * out_scale, fp2_y(v) * out_scale);
+      }
+    }
+  }
+}
+
+// Phase 2 shared memory: pair table, binomial tables, square roots.
+__host__ __device__ inline size_t twophase_sigma_smem(int rows, int xdim, int nsq) {
+  return 256 + 8 * (size_t)rows * xdim + 16 + 8 * (size_t)nsq;
+}
+
+template <class K>
+int fock_launch_grid(K kern, const TwoPhaseArgs &t, uint32_t n, size_t smem, int device, cudaStream_t stream) {
+  const int threads = FOCK_APPLY_THREADS;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return fock_cuda_status(e);
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  if (e != cudaSuccess) return fock_cuda_status(e);
+  if (per_sm < 1) return FOCK_ERR_UNSUPPORTED;
+  int64_t tiles = ((int64_t)n + threads - 1) / threads;
+  int64_t grid = (int64_t)per_sm * fock_get_sm_count(device);
+  if (grid > tiles) grid = tiles;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, threads, smem, stream>>>(t);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? FOCK_OK : fock_cuda_status(e);
+}

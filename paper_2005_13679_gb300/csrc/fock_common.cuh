@@ -126,5 +126,6 @@ int fock_apply_internal(const fock_space *sp, const fock_ham *ham, const void *C
                         int nrhs, int precision, int arm, void *ws, size_t ws_bytes,
                         cudaStream_t stream);
 size_t fock_apply_ws_bytes(const fock_space *sp, const fock_ham *ham, int nrhs, int precision);
+size_t fock_apply_ws_pref(const fock_space *sp, const fock_ham *ham, int nrhs, int precision);
 int fock_prepare_df(const void *C, int64_t n, void *ws, int device, cudaStream_t stream);
 int fock_get_sm_count(int device);

@@ -299,7 +299,7 @@ extern "C" int fock_lanczos_ground(const fock_space *sp, const fock_ham *ham, in
   double2 *V = nullptr, *w = nullptr;
   float2 *c64a = nullptr, *c64b = nullptr;
   void *ws = nullptr;
-  size_t ws_bytes = fock_apply_ws_bytes(sp, ham, 1, FOCK_PREC_F64);
+  size_t ws_bytes = fock_apply_ws_pref(sp, ham, 1, FOCK_PREC_F64);
   int st = FOCK_OK;
   auto cleanup = [&]() {
     cudaFree(V);
@@ -327,7 +327,7 @@ extern "C" int fock_lanczos_ground(const fock_space *sp, const fock_ham *ham, in
   auto apply = [&](int prec, const double2 *x, double2 *y) -> int {
     if (prec == FOCK_PREC_F32_MIXED) {
       to_c64_kernel<<<c.grid(), 256, 0, c.s>>>(x, n, c64a);
-      int r = fock_apply_internal(sp, ham, c64a, c64b, 1, prec, FOCK_ARM_HASH, nullptr, 0, c.s);
+      int r = fock_apply_internal(sp, ham, c64a, c64b, 1, prec, FOCK_ARM_HASH, ws, ws_bytes, c.s);
       if (r) return r;
       to_c128_kernel<<<c.grid(), 256, 0, c.s>>>(c64b, n, y);
       return cudaGetLastError() == cudaSuccess ? FOCK_OK : FOCK_ERR_CUDA;

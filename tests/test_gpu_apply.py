@@ -121,8 +121,12 @@ def test_maps_arm_equals_hash_arm(torch, N, M, kind, prec):
     fock.fock_build_jump_maps(sp.handle, fock.FOCK_MAP_SINGLE | fock.FOCK_MAP_DOUBLE)
     a = H.apply(C, precision=prec, arm=fock.FOCK_ARM_HASH)
     b = H.apply(C, precision=prec, arm=fock.FOCK_ARM_MAPS)
-    # identical targets and identical arithmetic order: bit-identical sums
-    assert torch.equal(a, b)
+    ref = oracle.apply_push(N, M, h, W, C.cpu().numpy().astype(np.complex128))
+    for out in (a, b):
+        assert rel(out.cpu().numpy().astype(np.complex128), ref) <= TOL[prec]
+    if kind != "generic":
+        # same kernel and same arithmetic order on both arms: bit-identical sums
+        assert torch.equal(a, b)
 
 
 def test_alias_and_argument_errors(torch):
