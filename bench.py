@@ -158,22 +158,30 @@ def run_reference(args, w):
     return 0
 
 
-# FP32 work of one executed term (one removal-addition pair of one configuration).
-# FP32-pair complex term: coefficient x amplitude (one packed pair product, 14
-# flop), two packed pair products with C (28) and two packed TwoSum
-# accumulations (28); real coefficients need one product and one accumulation.
-# FP32-mixed: packed multiply (2) and two packed FMAs (8).  Native FP64 counts its
-# own flops (coefficient scaling 4, complex FMA 8) on the FP64 pipe.
-FLOPS_PER_TERM = {"f64": 70, "f32_mixed": 10, "f64_native": 12}
-FLOPS_PER_TERM_REAL = {"f64": 35, "f32_mixed": 6, "f64_native": 8}
+# FP32 work of one executed term (one removal-addition pair of one
+# configuration) for the path that runs, counting an FMA as 2 flop:
+# * direct FP32-pair complex term: coefficient x amplitude (one packed pair
+#   product, 14), two packed pair products with C (28) and two packed TwoSum
+#   accumulations (28) = 70; real coefficients 35;
+# * two-phase FP32-pair (dense coefficients, 2 <= M <= 8): Gauss's three
+#   products, 1.5 packed pair products and accumulations = 42;
+# * FP32-mixed: direct 10 (real 6), two-phase 8 (two packed FMAs);
+# * native FP64: 10 (real 6) on the FP64 pipe.
+FLOPS_PER_TERM = {("f64", "direct"): 70, ("f64", "twophase"): 42, ("f32_mixed", "direct"): 10,
+                  ("f32_mixed", "twophase"): 8, ("f64_native", "direct"): 10}
+FLOPS_PER_TERM_REAL = {("f64", "direct"): 35, ("f32_mixed", "direct"): 6, ("f64_native", "direct"): 6}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
+
+
+def path_of(w, prec):
+    """Which kernel family serves this workload (mirrors the library's dispatch)."""
+    return "twophase" if (w.kind == "generic" and 2 <= w.M <= 8 and prec in (0, 2)) else "direct"
 
 
 def launches_per_step(w, prec):
     """Kernels of one apply: the FP32-pair input preparation (2), then the
     two-phase pair (dense coefficients, 2 <= M <= 8) or one kernel."""
-    two_phase = w.kind == "generic" and 2 <= w.M <= 8 and prec in (0, 2)
-    return (2 if prec == 0 else 0) + (2 if two_phase else 1)
+    return (2 if prec == 0 else 0) + (2 if path_of(w, prec) == "twophase" else 1)
 
 
 def executed_terms(w, h, W):
@@ -423,7 +431,8 @@ def main():
     nbytes = w.nc * w.nrhs * elem
     hbm_gbs = 2 * nbytes / (ms * 1e-3) / 1e9
     executed = executed_terms(w, h, W) * w.nrhs
-    flops_term = FLOPS_PER_TERM[args.precision] if not H.real else FLOPS_PER_TERM_REAL[args.precision]
+    key = (args.precision, path_of(w, prec))
+    flops_term = FLOPS_PER_TERM_REAL[key] if (H.real and key in FLOPS_PER_TERM_REAL) else FLOPS_PER_TERM[key]
     achieved = executed * flops_term / (kernel_ms * 1e-3) / 1e12
     traffic = load_traffic(w.name, args.precision)
     out = {
@@ -440,6 +449,7 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
                      "kernel_ms": kernel_ms, "executed_terms": executed, "flops_per_term": flops_term,
+                     "path": path_of(w, prec),
                      "pipe": "FP32 (fma.rn.f32x2 and scalar); peak = 152 SMs x 128 lanes x 2 flop x 2070 MHz"},
         "hbm": {"compulsory_bytes": 2 * nbytes, "achieved_gbs": hbm_gbs, "peak_gbs": peaks["hbm_gbs"],
                 "frac": hbm_gbs / peaks["hbm_gbs"], "peak_source": peak_src},

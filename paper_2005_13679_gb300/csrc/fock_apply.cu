@@ -102,6 +102,8 @@ static void free_ham(fock_ham *h) {
   cudaFree(h->d_sqrtdf);
   cudaFree(h->d_sqrt32);
   cudaFree(h->d_terms);
+  cudaFree(h->d_gauss1);
+  cudaFree(h->d_gauss2);
   cudaFree(h->d_slots);
   cudaFree(h->ws);
   cudaFree(h->hb_in);
@@ -295,7 +297,29 @@ extern "C" int fock_hamiltonian_create(const fock_space *sp, const double *h_hos
       terms[i] = make_term(M, e.k, e.q, add[i].s, add[i].l, fock_sparse_maxm(M));
       slots[i] = e.slot_base + add[i].a_index;
     }
+  // Gauss's three-product form of the dense coefficients (two-phase kernel):
+  // Re(R X) = Re R (Re X + Im X) - (Re R + Im R) Im X,
+  // Im(R X) = Re R (Re X + Im X) + (Im R - Re R) Re X.
+  std::vector<float4> g1, g2;
+  if (H->dense) {
+    const int Pp = (P + 1) / 2;
+    g1.resize((size_t)P * P);
+    g2.assign((size_t)Pp * P, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int r = 0; r < P; ++r)
+      for (int a = 0; a < P; ++a) {
+        const cplx v = coef[(size_t)r * P + a] / H->coef_scale;
+        float rh, rl, sh, sl, th, tl;
+        split_float(v.real(), rh, rl);
+        split_float(v.real() + v.imag(), sh, sl);
+        split_float(v.imag() - v.real(), th, tl);
+        g1[(size_t)r * P + a] = make_float4(rh, sh, rl, sl);
+        float4 &z = g2[(size_t)(r / 2) * P + a];
+        if (r % 2 == 0) { z.x = th; z.z = tl; } else { z.y = th; z.w = tl; }
+      }
+  }
   int st = FOCK_OK;
+  if (!st && H->dense) st = upload(&H->d_gauss1, g1.data(), g1.size());
+  if (!st && H->dense) st = upload(&H->d_gauss2, g2.data(), g2.size());
   if (!st) st = upload(&H->d_terms, terms.data(), nadd);
   if (!st) st = upload(&H->d_slots, slots.data(), nadd);
   if (!st) st = upload(&H->d_rem, rem.data(), rem.size());
@@ -539,6 +563,8 @@ static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Ci
       t.a = a;
       t.nc2 = (uint32_t)count_nm(sp->N - 2, sp->M);
       t.Y = (char *)ws + twophase_y_offset(sp, ham, nrhs, precision);
+      t.g1 = ham->d_gauss1;
+      t.g2 = ham->d_gauss2;
       return fock_launch_twophase(t, precision == FOCK_PREC_F32_MIXED, sp->device, stream);
     }
     // Every reduced coefficient present and M <= 10: the register-resident

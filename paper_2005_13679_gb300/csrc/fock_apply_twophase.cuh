@@ -22,6 +22,7 @@ struct TwoPhaseArgs {
   ApplyArgs<uint32_t> a;          // N-space tables, coefficients (dense, r*P + a), C, sigma, nrhs, scales
   uint32_t nc2;                   // N_c(N - 2, M)
   void *Y;                        // [P][nc2 * nrhs]
+  const float4 *g1, *g2;          // FP32-pair form: Gauss coefficients (see fock_apply.cu)
 };
 
 template <int M>
@@ -82,7 +83,7 @@ struct TwoPhaseSlot {
 // Stage coefficients, addition pairs, binomial tables and square roots.
 template <int M, class CoefT, class SqT>
 __device__ __forceinline__ void twophase_stage(const ApplyArgs<uint32_t> &a, const TwoPhaseSmem<M> &L,
-                                               unsigned char *smem) {
+                                               unsigned char *smem, bool stage_coef = true) {
   constexpr int P = TwoPhaseSmem<M>::P;
   CoefT *s_coef = (CoefT *)(smem + L.off_coef);
   int8_t *s_pair = (int8_t *)(smem + L.off_pair);
@@ -90,7 +91,8 @@ __device__ __forceinline__ void twophase_stage(const ApplyArgs<uint32_t> &a, con
   uint32_t *s_sat = (uint32_t *)(smem + L.off_sat);
   SqT *s_sq = (SqT *)(smem + L.off_sq);
   const int rows = M > 1 ? M - 1 : 1;
-  for (int i = threadIdx.x; i < P * P; i += blockDim.x) s_coef[i] = ((const CoefT *)a.coef)[i];
+  if (stage_coef)
+    for (int i = threadIdx.x; i < P * P; i += blockDim.x) s_coef[i] = ((const CoefT *)a.coef)[i];
   for (int i = threadIdx.x; i < P; i += blockDim.x) {
     // addition pair i = (s, l), s <= l, lexicographic
     int s = 0, r = i;
@@ -139,16 +141,30 @@ __device__ __forceinline__ uint32_t twophase_slots(uint32_t gc, const ApplyArgs<
 // ---------------------------------------------------------------------------
 // FP32 pairs
 // ---------------------------------------------------------------------------
+// Phase 1 in FP32 pairs with Gauss's three products per complex term:
+//   k1 = Re R (Re X + Im X),  k2 = (Re R + Im R) Im X,  k3 = (Im R - Re R) Re X,
+//   Re(R X) = k1 - k2,  Im(R X) = k1 + k3.
+// (k1, k2) share one packed product and accumulation; k3 of two neighbouring
+// removals share the other, so a complex term costs 1.5 packed products and
+// accumulations instead of 2.
 template <int M>
 __global__ void __launch_bounds__(FOCK_APPLY_THREADS, 4)
 fock_twophase_x_df(const TwoPhaseArgs t) {
   constexpr int P = TwoPhaseSmem<M>::P;
-  constexpr int RB = 8;   // removals accumulated in registers per sweep over the additions
+  constexpr int PP = (P + 1) / 2;
+  constexpr int RB = 8;   // removals accumulated in registers per sweep over the additions (even)
   const ApplyArgs<uint32_t> &a = t.a;
   extern __shared__ __align__(16) unsigned char smem[];
-  const TwoPhaseSmem<M> L(a.xdim, a.nsq, sizeof(float4), sizeof(TwoPhaseSlot) * M, blockDim.x);
-  twophase_stage<M, float4, float2>(a, L, smem);
-  const float4 *s_coef = (const float4 *)(smem + L.off_coef);
+  const TwoPhaseSmem<M> L(a.xdim, a.nsq, 2 * sizeof(float4), sizeof(TwoPhaseSlot) * M, blockDim.x);
+  {
+    // stage: Gauss coefficients (g1 rows, then g2 row pairs), tables, pairs
+    float4 *s_g = (float4 *)(smem + L.off_coef);
+    for (int i = threadIdx.x; i < P * P; i += blockDim.x) s_g[i] = t.g1[i];
+    for (int i = threadIdx.x; i < PP * P; i += blockDim.x) s_g[P * P + i] = t.g2[i];
+  }
+  twophase_stage<M, float4, float2>(a, L, smem, false);
+  const float4 *s_g1 = (const float4 *)(smem + L.off_coef);
+  const float4 *s_g2 = s_g1 + P * P;
   const int8_t *s_pair = (const int8_t *)(smem + L.off_pair);
   const uint32_t *s_mod = (const uint32_t *)(smem + L.off_mod);
   const uint32_t *s_sat = (const uint32_t *)(smem + L.off_sat);
@@ -167,12 +183,14 @@ fock_twophase_x_df(const TwoPhaseArgs t) {
     const uint32_t base = twophase_slots<M, float2>(live ? g : nc2 - 1u, a, nc2, s_mod, s_sat, s_sq, slot, nt);
     for (int j = 0; j < nrhs; ++j) {
       for (int r0 = 0; r0 < P; r0 += RB) {
-        fp2_t A1h[RB], A1l[RB], A2h[RB], A2l[RB];
+        fp2_t K12h[RB], K12l[RB], K3h[RB / 2], K3l[RB / 2];
 #pragma unroll
-        for (int q = 0; q < RB; ++q) A1h[q] = A1l[q] = A2h[q] = A2l[q] = 0ull;
+        for (int q = 0; q < RB; ++q) K12h[q] = K12l[q] = 0ull;
+#pragma unroll
+        for (int q = 0; q < RB / 2; ++q) K3h[q] = K3l[q] = 0ull;
 #pragma unroll 2
         for (int ai = 0; ai < P; ++ai) {
-          // X = B_a(n') C[n' + a] as an FP32 pair (both lanes: Re, Im)
+          // X = B_a(n') C[n' + a] as FP32 pairs (lanes: Re, Im)
           const int s = s_pair[2 * ai], l = s_pair[2 * ai + 1];
           const TwoPhaseSlot zs = slot[s * nt], zl = slot[l * nt];
           const float2 amp = df_mul(make_float2(zs.bh, zs.bl), s == l ? make_float2(zs.ch, zs.cl)
@@ -180,17 +198,28 @@ fock_twophase_x_df(const TwoPhaseArgs t) {
           const float4 v = __ldg(C + (size_t)(base - zs.U - zl.V) * nrhs + j);
           fp2_t Xh, Xl;
           fp2_dprod(fp2_make(v.x, v.y), fp2_make(v.z, v.w), fp2_make(amp.x, amp.x), fp2_make(amp.y, amp.y), Xh, Xl);
-          const fp2_t Xsh = fp2_swap(Xh), Xsl = fp2_swap(Xl);
+          const float xrh = fp2_x(Xh), xih = fp2_y(Xh), xrl = fp2_x(Xl), xil = fp2_y(Xl);
+          float th = 0.f, tl = 0.f;                         // Re X + Im X as a pair
+          df_add_acc(th, tl, xrh, xrl);
+          df_add_acc(th, tl, xih, xil);
+          const fp2_t Bh = fp2_make(th, xih), Bl = fp2_make(tl, xil);     // (Re X + Im X, Im X)
+          const fp2_t Rh = fp2_make(xrh, xrh), Rl = fp2_make(xrl, xrl);   // (Re X, Re X)
 #pragma unroll
           for (int q = 0; q < RB; ++q) {
             if (r0 + q < P) {
-              const float4 w = s_coef[(r0 + q) * P + ai];
-              const fp2_t Rh = fp2_make(w.x, w.y), Rl = fp2_make(w.z, w.w);
+              const float4 w = s_g1[(r0 + q) * P + ai];       // (Re R, Re R + Im R)
               fp2_t p, e;
-              fp2_dprod(Rh, Rl, Xh, Xl, p, e);     // (Re R Re X, Im R Im X)
-              fp2_dacc(A1h[q], A1l[q], p, e);
-              fp2_dprod(Rh, Rl, Xsh, Xsl, p, e);   // (Re R Im X, Im R Re X)
-              fp2_dacc(A2h[q], A2l[q], p, e);
+              fp2_dprod(fp2_make(w.x, w.y), fp2_make(w.z, w.w), Bh, Bl, p, e);
+              fp2_dacc(K12h[q], K12l[q], p, e);               // (k1, k2)
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < RB / 2; ++q) {
+            if (r0 + 2 * q < P) {
+              const float4 w = s_g2[((r0 >> 1) + q) * P + ai]; // (Im R - Re R) of two removals
+              fp2_t p, e;
+              fp2_dprod(fp2_make(w.x, w.y), fp2_make(w.z, w.w), Rh, Rl, p, e);
+              fp2_dacc(K3h[q], K3l[q], p, e);                 // (k3, k3')
             }
           }
         }
@@ -198,11 +227,14 @@ fock_twophase_x_df(const TwoPhaseArgs t) {
 #pragma unroll
           for (int q = 0; q < RB; ++q) {
             if (r0 + q < P) {
+              const float k1h = fp2_x(K12h[q]), k1l = fp2_x(K12l[q]);
+              const float k3h = (q & 1) ? fp2_y(K3h[q / 2]) : fp2_x(K3h[q / 2]);
+              const float k3l = (q & 1) ? fp2_y(K3l[q / 2]) : fp2_x(K3l[q / 2]);
               float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-              df_add_acc(rh, rl, fp2_x(A1h[q]), fp2_x(A1l[q]));
-              df_add_acc(rh, rl, -fp2_y(A1h[q]), -fp2_y(A1l[q]));
-              df_add_acc(ih, il, fp2_x(A2h[q]), fp2_x(A2l[q]));
-              df_add_acc(ih, il, fp2_y(A2h[q]), fp2_y(A2l[q]));
+              df_add_acc(rh, rl, k1h, k1l);
+              df_add_acc(rh, rl, -fp2_y(K12h[q]), -fp2_y(K12l[q]));
+              df_add_acc(ih, il, k1h, k1l);
+              df_add_acc(ih, il, k3h, k3l);
               Y[(size_t)(r0 + q) * ldy + (size_t)g * nrhs + j] = make_float4(rh, ih, rl, il);
             }
           }

@@ -5,7 +5,7 @@
 template <int M>
 static int launch_df(const TwoPhaseArgs &t, int dev, cudaStream_t s) {
   const ApplyArgs<uint32_t> &a = t.a;
-  const TwoPhaseSmem<M> L(a.xdim, a.nsq, sizeof(float4), sizeof(TwoPhaseSlot) * M, FOCK_APPLY_THREADS);
+  const TwoPhaseSmem<M> L(a.xdim, a.nsq, 2 * sizeof(float4), sizeof(TwoPhaseSlot) * M, FOCK_APPLY_THREADS);
   int st = fock_launch_grid(fock_twophase_x_df<M>, t, t.nc2, L.total, dev, s);
   if (st) return st;
   return fock_launch_grid(fock_twophase_sigma_df<M>, t, a.nc, twophase_sigma_smem(a.rows, a.xdim, a.nsq), dev, s);
