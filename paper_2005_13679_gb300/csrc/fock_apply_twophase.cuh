@@ -138,6 +138,31 @@ __device__ __forceinline__ uint32_t twophase_slots(uint32_t gc, const ApplyArgs<
   return base;
 }
 
+
+// Phase 2 per configuration: with Q = N_c(N-2,M) - 1 - sum_m C(S_m + m, m+1)
+// and prefix sums P1[j], P2[j] of C(S_m + m - d, m+1) - C(S_m + m, m+1)
+// (d = 1, 2) over m < j, removing particles at k <= q gives the index
+//     rank2 = Q - (P1[q] - P1[k]) - (P2[M-1] - P2[q])
+// (S_m drops by one on [k, q) and by two from q on).
+template <int M>
+__device__ __forceinline__ uint32_t twophase_prefix2(const int (&S)[M], const uint32_t *s_mod, int xdim,
+                                                     uint32_t nc2, uint32_t (&P1)[M], uint32_t (&P2)[M]) {
+  uint32_t q0 = nc2 - 1u, a1 = 0u, a2 = 0u;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    P1[m] = a1;
+    P2[m] = a2;
+    if (m < M - 1) {
+      const int x = S[m] + m;
+      const uint32_t t0 = s_mod[m * xdim + x];
+      q0 -= t0;
+      a1 += (x >= 1 ? s_mod[m * xdim + x - 1] : 0u) - t0;
+      a2 += (x >= 2 ? s_mod[m * xdim + x - 2] : 0u) - t0;
+    }
+  }
+  return q0;
+}
+
 // ---------------------------------------------------------------------------
 // FP32 pairs
 // ---------------------------------------------------------------------------
@@ -244,21 +269,19 @@ fock_twophase_x_df(const TwoPhaseArgs t) {
   }
 }
 
+// Phase 2 is a gather: each target reads up to P rows of Y at hashed
+// addresses, so latency is hidden by residency. The minimum-block hint keeps
+// 8 blocks of 128 threads per SM (64 registers) for M <= 6 and 5 blocks for
+// M = 7, 8, where the unrolled removal loops need up to 93 registers.
 template <int M>
-__global__ void __launch_bounds__(FOCK_APPLY_THREADS)
+__global__ void __launch_bounds__(FOCK_APPLY_THREADS, (M <= 6 ? 8 : 5))
 fock_twophase_sigma_df(const TwoPhaseArgs t) {
-  constexpr int P = TwoPhaseSmem<M>::P;
   const ApplyArgs<uint32_t> &a = t.a;
   extern __shared__ __align__(16) unsigned char smem[];
-  int8_t *s_pair = (int8_t *)smem;
   uint32_t *s_mod = (uint32_t *)(smem + 256);
   const int rows = M > 1 ? M - 1 : 1;
   uint32_t *s_sat = s_mod + rows * a.xdim;
   float2 *s_sq = (float2 *)(s_sat + rows * a.xdim + 4);
-  for (int i = threadIdx.x; i < P; i += blockDim.x) {
-    s_pair[2 * i] = a.rem[i].k;
-    s_pair[2 * i + 1] = a.rem[i].q;
-  }
   for (int i = threadIdx.x; i < rows * a.xdim; i += blockDim.x) {
     s_mod[i] = a.mod[i];
     s_sat[i] = a.sat[i];
@@ -280,19 +303,24 @@ fock_twophase_sigma_df(const TwoPhaseArgs t) {
     fock_decode_prefix<uint32_t, M>(live ? g : nc - 1u, a.N, M, nc, s_sat, a.xdim, S);
 #pragma unroll
     for (int m = 0; m < M; ++m) n[m] = S[m] - (m > 0 ? S[m - 1] : 0);
+    uint32_t P1[M], P2[M];
+    const uint32_t q0 = twophase_prefix2<M>(S, s_mod, a.xdim, nc2, P1, P2);
     for (int j = 0; j < nrhs; ++j) {
       fp2_t Ah = 0ull, Al = 0ull;
-      for (int r = 0; r < P; ++r) {
-        const int k = s_pair[2 * r], q = s_pair[2 * r + 1];
-        const int nk = sel_occ<M>(n, k), nq = sel_occ<M>(n, q);
-        const bool valid = live && (k == q ? nk >= 2 : (nk >= 1 && nq >= 1));
-        if (!__any_sync(0xffffffffu, valid)) continue;
-        const uint32_t r2 = valid ? twophase_rank2<M>(S, k, q, s_mod, a.xdim, nc2) : 0u;
-        const float2 A = df_mul(s_sq[valid ? nk : 0], s_sq[valid ? nq - (k == q) : 0]);
-        const float4 y = __ldg(Y + (size_t)r * ldy + (size_t)r2 * nrhs + j);
-        fp2_t p, e;
-        fp2_dprod(fp2_make(y.x, y.y), fp2_make(y.z, y.w), fp2_make(A.x, A.x), fp2_make(A.y, A.y), p, e);
-        fp2_dacc(Ah, Al, p, e);
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+#pragma unroll
+        for (int q = k; q < M; ++q) {
+          const int r = k * M - (k * (k - 1)) / 2 + (q - k);
+          const bool valid = live && (k == q ? n[k] >= 2 : (n[k] >= 1 && n[q] >= 1));
+          if (!__any_sync(0xffffffffu, valid)) continue;
+          const uint32_t r2 = valid ? q0 - (P1[q] - P1[k]) - (P2[M - 1] - P2[q]) : 0u;
+          const float2 A = df_mul(s_sq[valid ? n[k] : 0], s_sq[valid ? n[q] - (k == q) : 0]);
+          const float4 y = __ldg(Y + (size_t)r * ldy + (size_t)r2 * nrhs + j);
+          fp2_t p, e;
+          fp2_dprod(fp2_make(y.x, y.y), fp2_make(y.z, y.w), fp2_make(A.x, A.x), fp2_make(A.y, A.y), p, e);
+          fp2_dacc(Ah, Al, p, e);
+        }
       }
       if (live) {
         float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
@@ -369,20 +397,14 @@ fock_twophase_x_mixed(const TwoPhaseArgs t) {
 }
 
 template <int M>
-__global__ void __launch_bounds__(FOCK_APPLY_THREADS)
+__global__ void __launch_bounds__(FOCK_APPLY_THREADS, (M <= 6 ? 8 : 5))
 fock_twophase_sigma_mixed(const TwoPhaseArgs t) {
-  constexpr int P = TwoPhaseSmem<M>::P;
   const ApplyArgs<uint32_t> &a = t.a;
   extern __shared__ __align__(16) unsigned char smem[];
-  int8_t *s_pair = (int8_t *)smem;
   uint32_t *s_mod = (uint32_t *)(smem + 256);
   const int rows = M > 1 ? M - 1 : 1;
   uint32_t *s_sat = s_mod + rows * a.xdim;
   float *s_sq = (float *)(s_sat + rows * a.xdim + 4);
-  for (int i = threadIdx.x; i < P; i += blockDim.x) {
-    s_pair[2 * i] = a.rem[i].k;
-    s_pair[2 * i + 1] = a.rem[i].q;
-  }
   for (int i = threadIdx.x; i < rows * a.xdim; i += blockDim.x) {
     s_mod[i] = a.mod[i];
     s_sat[i] = a.sat[i];
@@ -403,17 +425,22 @@ fock_twophase_sigma_mixed(const TwoPhaseArgs t) {
     fock_decode_prefix<uint32_t, M>(live ? g : nc - 1u, a.N, M, nc, s_sat, a.xdim, S);
 #pragma unroll
     for (int m = 0; m < M; ++m) n[m] = S[m] - (m > 0 ? S[m - 1] : 0);
+    uint32_t P1[M], P2[M];
+    const uint32_t q0 = twophase_prefix2<M>(S, s_mod, a.xdim, nc2, P1, P2);
     for (int j = 0; j < nrhs; ++j) {
       fp2_t Sh = 0ull, Sl = 0ull;
-      for (int r = 0; r < P; ++r) {
-        const int k = s_pair[2 * r], q = s_pair[2 * r + 1];
-        const int nk = sel_occ<M>(n, k), nq = sel_occ<M>(n, q);
-        const bool valid = live && (k == q ? nk >= 2 : (nk >= 1 && nq >= 1));
-        if (!__any_sync(0xffffffffu, valid)) continue;
-        const uint32_t r2 = valid ? twophase_rank2<M>(S, k, q, s_mod, a.xdim, nc2) : 0u;
-        const float A = s_sq[valid ? nk : 0] * s_sq[valid ? nq - (k == q) : 0];
-        const float2 y = __ldg(Y + (size_t)r * ldy + (size_t)r2 * nrhs + j);
-        fp2_dacc(Sh, Sl, fp2_make(y.x * A, y.y * A), 0ull);
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+#pragma unroll
+        for (int q = k; q < M; ++q) {
+          const int r = k * M - (k * (k - 1)) / 2 + (q - k);
+          const bool valid = live && (k == q ? n[k] >= 2 : (n[k] >= 1 && n[q] >= 1));
+          if (!__any_sync(0xffffffffu, valid)) continue;
+          const uint32_t r2 = valid ? q0 - (P1[q] - P1[k]) - (P2[M - 1] - P2[q]) : 0u;
+          const float A = s_sq[valid ? n[k] : 0] * s_sq[valid ? n[q] - (k == q) : 0];
+          const float2 y = __ldg(Y + (size_t)r * ldy + (size_t)r2 * nrhs + j);
+          fp2_dacc(Sh, Sl, fp2_make(y.x * A, y.y * A), 0ull);
+        }
       }
       if (live) {
         const fp2_t v = fp2_add(Sh, Sl);
