@@ -154,6 +154,10 @@ WORKLOADS = {
     # Profiling size of the generic N, M = 6 workload: 17,259,390 configurations
     # (complex128 C of 276 MB, larger than L2), same kernel as N = 100.
     "generic_n70_m6": Workload("generic_n70_m6", N=70, M=6, kind="generic", seed=2),
+    # Profiling size for the two-phase kernels of the generic M = 6 workload:
+    # 8,259,888 configurations (complex128 C of 132 MB, larger than L2) and an
+    # (N-2)-space intermediate of 21 x 7,028,847 FP32-pair rows (2.4 GB).
+    "generic_n60_m6": Workload("generic_n60_m6", N=60, M=6, kind="generic", seed=2),
     # Profiling size of the Lieb-Liniger M = 10 workload: 20,160,075
     # configurations (complex128 C of 323 MB, larger than L2).
     "ll_n22_m10": Workload("ll_n22_m10", N=22, M=10, kind="ll", g=0.5, seed=3),
