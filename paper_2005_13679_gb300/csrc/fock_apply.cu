@@ -29,6 +29,9 @@ int fock_launch_sparse_f64(const SparseArgs &, bool, bool, int, cudaStream_t);
 int fock_launch_sparse_df(const SparseArgs &, bool, bool, int, cudaStream_t);
 int fock_launch_sparse_mixed(const SparseArgs &, bool, bool, int, cudaStream_t);
 int fock_launch_twophase(const TwoPhaseArgs &, bool, int, cudaStream_t);
+int fock_launch_twophase_tc(const TwoPhaseArgs &, int, cudaStream_t);
+int fock_tc_image(int M, const std::complex<double> *R, std::vector<unsigned char> &img, std::vector<int> &er);
+size_t fock_tc_smem(int M, int xdim, int nsq);
 
 // Segment form of one term (see fock_apply_sparse.cuh): the removal (k, q)
 // (q = -1 for one particle) and the addition (s, l) (s = -1 for one particle)
@@ -104,6 +107,8 @@ static void free_ham(fock_ham *h) {
   cudaFree(h->d_terms);
   cudaFree(h->d_gauss1);
   cudaFree(h->d_gauss2);
+  cudaFree(h->d_tc_a);
+  cudaFree(h->d_tc_er);
   cudaFree(h->d_slots);
   cudaFree(h->ws);
   cudaFree(h->hb_in);
@@ -320,6 +325,15 @@ extern "C" int fock_hamiltonian_create(const fock_space *sp, const double *h_hos
   int st = FOCK_OK;
   if (!st && H->dense) st = upload(&H->d_gauss1, g1.data(), g1.size());
   if (!st && H->dense) st = upload(&H->d_gauss2, g2.data(), g2.size());
+  if (!st && H->dense && M >= 2 && M <= 6) {
+    std::vector<cplx> Rs((size_t)P * P);
+    for (size_t i = 0; i < Rs.size(); ++i) Rs[i] = coef[i] / H->coef_scale;
+    std::vector<unsigned char> img;
+    std::vector<int> er;
+    st = fock_tc_image(M, Rs.data(), img, er);
+    if (!st) st = upload(&H->d_tc_a, img.data(), img.size());
+    if (!st) st = upload(&H->d_tc_er, er.data(), er.size());
+  }
   if (!st) st = upload(&H->d_terms, terms.data(), nadd);
   if (!st) st = upload(&H->d_slots, slots.data(), nadd);
   if (!st) st = upload(&H->d_rem, rem.data(), rem.size());
@@ -406,7 +420,7 @@ static const size_t kWsHeader = 256;
 int fock_prepare_df(const void *C, int64_t n, void *ws, int device, cudaStream_t stream) {
   int *words = (int *)ws;
   float4 *split = (float4 *)((char *)ws + kWsHeader);
-  FOCK_CUDA_TRY(cudaMemsetAsync(words, 0, 8, stream));
+  FOCK_CUDA_TRY(cudaMemsetAsync(words, 0, 12, stream));   // [0] exponent bits, [1] output exponent, [2] status
   const int sms = fock_get_sm_count(device);
   int64_t blocks = (2 * n + 255) / 256;
   if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
@@ -441,6 +455,18 @@ static size_t twophase_y_bytes(const fock_space *sp, int nrhs, int precision) {
   const int64_t nc2 = count_nm(sp->N - 2, sp->M);
   const size_t elem = precision == FOCK_PREC_F32_MIXED ? sizeof(float2) : sizeof(float4);
   return (size_t)fock_pair_count(sp->M) * (size_t)nc2 * (size_t)nrhs * elem;
+}
+
+// Phase 1 on the tensor cores: FP64-class precision, dense coefficients with
+// 2 <= M <= 6 (their digit image exists), its shared-memory layout within the
+// device's per-block limit and fewer than 2^31 (configuration, rhs) columns.
+static bool tc_eligible(const fock_space *sp, const fock_ham *ham, const ApplyArgs<uint32_t> &a, int nrhs,
+                        int precision) {
+  if (precision != FOCK_PREC_F64 || !ham->d_tc_a || sp->M < 2 || sp->M > 6) return false;
+  if ((uint64_t)count_nm(sp->N - 2, sp->M) * (uint64_t)nrhs >= (1ull << 31)) return false;
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, sp->device) != cudaSuccess) return false;
+  return fock_tc_smem(sp->M, a.xdim, a.nsq) <= (size_t)optin;
 }
 
 // Workspace that selects the fastest path (the minimum is fock_apply_ws_bytes).
@@ -565,6 +591,15 @@ static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Ci
       t.Y = (char *)ws + twophase_y_offset(sp, ham, nrhs, precision);
       t.g1 = ham->d_gauss1;
       t.g2 = ham->d_gauss2;
+      t.tc_a = nullptr;
+      t.tc_er = nullptr;
+      t.status = nullptr;
+      if (tc_eligible(sp, ham, a, nrhs, precision)) {
+        t.tc_a = ham->d_tc_a;
+        t.tc_er = ham->d_tc_er;
+        t.status = (int *)ws + 2;
+        return fock_launch_twophase_tc(t, sp->device, stream);
+      }
       return fock_launch_twophase(t, precision == FOCK_PREC_F32_MIXED, sp->device, stream);
     }
     // Every reduced coefficient present and M <= 10: the register-resident
@@ -666,5 +701,10 @@ extern "C" int fock_apply_H_host(const fock_space *sp, const fock_ham *ham, cons
   if (st) return st;
   FOCK_CUDA_TRY(cudaMemcpyAsync(sigma_host, H->hb_out, bytes, cudaMemcpyDeviceToHost, s));
   FOCK_CUDA_TRY(cudaStreamSynchronize(s));
+  if (precision == FOCK_PREC_F64) {
+    int status = 0;
+    FOCK_CUDA_TRY(cudaMemcpy(&status, (const int *)H->ws + 2, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status) return FOCK_ERR_TIMEOUT;
+  }
   return FOCK_OK;
 }

@@ -1,0 +1,509 @@
+// fock_apply_tc.cuh -- phase 1 of the two-phase apply (fock_apply_twophase.cuh)
+// on the fifth-generation tensor cores, with FP64-class accuracy.
+//
+// Phase 1 is the dense product Y = R X with R the P x P reduced coefficients
+// and X[a][n'] = B_a(n') C[n' + a] over the (N-2)-particle configurations.  In
+// real form (rows and columns interleaved as (Re, Im)) it is a 2P x 2P matrix
+// times a 2P x (configurations x rhs) matrix.  Both factors are split into five
+// signed base-2^9 digits with a power-of-two scale per row of R and per column
+// of X (the error-free splitting of Ozaki, Ogita, Oishi and Rump, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix
+// multiplication", Numer. Algorithms 59 (2012)):
+//
+//     R~[rho][k] = 2^(e_rho - 8) sum_{i=1..5} rho_i 2^(-9(i-1)),   |rho_i| <= 256,
+//     X~[k][c]   = 2^(e_c - 8)   sum_{j=1..5} xi_j  2^(-9(j-1)),   |xi_j|  <= 265.
+//
+// Digits are integers held exactly in fp16.  For a level l = i + j the sum
+// S_l = sum_{i+j=l} sum_k rho_i xi_j has at most 5 pairs x 42 terms of
+// magnitude <= 256 * 265, below 2^24, so the tensor core's FP32 accumulation
+// of S_l is exact whatever its internal order.  Levels 2..6 are kept:
+//
+//     Y = 2^(e_rho + e_c - 16) sum_{l=2..6} 2^(-9(l-2)) S_l,
+//
+// whose dropped terms and digit remainders are below 2^-44 of
+// max|R~ row| * max|X~ column| * 2P; the five level sums are combined into an
+// FP32 pair (TwoSum) for phase 2.
+//
+// Tensor memory holds the level sums: an MMA of M = 128 rows computes 128
+// (real row, level) combinations at once.  Warp quarter q of tensor memory
+// (lanes 32q .. 32q+31) serves real rows q*RW .. q*RW + RW - 1 and their five
+// levels: slot s = (6 - l) * RW + i (i the row within the quarter) is lane s of
+// chain 1 for s < 32 and lane s - 32 of chain 2 otherwise.  Chain 1 holds
+// levels 6, 5 and part of 4 and contracts over all digits; chain 2 holds the
+// rest of 4, 3 and 2 and needs only digits 1..3.  K is ordered
+// [digits 1..3 of every real index, interleaved | digits 4, 5 interleaved] so
+// chain 2 reads the first part only.
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include "fock_apply_twophase.cuh"
+#include "fock_tc.cuh"
+
+constexpr int kTcCols = 128;        // (configuration, rhs) columns per tile = MMA N
+constexpr int kTcProducers = 128;   // producer group: 4 warps, one thread per column
+constexpr int kTcThreads = 416;     // two producer groups (warps 0-3 even tiles, 4-7 odd tiles),
+                                    // warps 8-11 epilogue (one per tensor-memory quarter), warp 12 MMA
+constexpr int kTcTmemCols = 512;    // two tiles x (chain 1 + chain 2) x 128 columns
+constexpr uint32_t kTcPolls = 1u << 20;
+constexpr int kTcStageRow = 20;     // floats per staged row (16 columns + 4 of padding against bank conflicts)
+constexpr int kTcStageBytes = 4 * 64 * kTcStageRow * 4;
+constexpr int kTcExpSlot = 60;      // chain-2 lane 28 of every quarter carries the column exponents
+
+// Shape of the real-form product for M orbitals (2 <= M <= 6).
+struct TcShape {
+  int P, R2, RW, K1, K2, KT;
+  __host__ __device__ constexpr explicit TcShape(int m)
+      : P(m * (m + 1) / 2), R2(m * (m + 1)), RW(2 * ((m * (m + 1) + 7) / 8)),
+        K1((3 * m * (m + 1) + 15) / 16 * 16), K2((2 * m * (m + 1) + 15) / 16 * 16),
+        KT((3 * m * (m + 1) + 15) / 16 * 16 + (2 * m * (m + 1) + 15) / 16 * 16) {}
+  // bytes of the A image: chain 1 (128 x KT) then chain 2 (128 x K1), fp16
+  __host__ __device__ constexpr int a1_bytes() const { return 128 * KT * 2; }
+  __host__ __device__ constexpr int a_bytes() const { return 128 * (KT + K1) * 2; }
+  __host__ __device__ constexpr int b_bytes() const { return kTcCols * KT * 2; }
+  // K position of the column exponent (the last of part 1, never a digit)
+  __host__ __device__ constexpr int exp_pos() const { return K1 - 1; }
+  // additions swept by the producer, padding included, so that every 16-byte
+  // chunk of both K parts is written
+  __host__ __device__ constexpr int a_end() const {
+    const int c1 = (K1 + 5) / 6, c2 = K2 / 4;
+    const int m = P > c1 ? (P > c2 ? P : c2) : (c1 > c2 ? c1 : c2);
+    return (m + 3) / 4 * 4;
+  }
+};
+
+struct TcSmem {
+  size_t off_a, off_b0, off_b1, off_stg, off_er, off_mod, off_sat, off_sq, off_bar, total;
+  __host__ __device__ TcSmem(int M, int xdim, int nsq) {
+    const TcShape sh(M);
+    const int rows = M > 1 ? M - 1 : 1;
+    size_t o = 0;
+    off_a = o;    o += sh.a_bytes();
+    off_b0 = o;   o += sh.b_bytes();
+    off_b1 = o;   o += sh.b_bytes();
+    off_stg = o;  o += kTcStageBytes;
+    off_er = o;   o = fock_align16(o + 4 * (size_t)sh.R2);
+    off_mod = o;  o = fock_align16(o + 4 * (size_t)rows * xdim);
+    off_sat = o;  o = fock_align16(o + 4 * (size_t)rows * xdim);
+    off_sq = o;   o = fock_align16(o + 8 * (size_t)nsq);
+    off_bar = o;  o = fock_align16(o + 6 * 8 + 8);
+    total = o;
+  }
+};
+
+// 2^e as a float for -126 <= e <= 127.
+__device__ __forceinline__ float tc_pow2(int e) { return __int_as_float((e + 127) << 23); }
+
+// Multiply a pair by 2^e exactly for any e (two factors when e leaves the
+// single-float range; that happens only for columns or rows ~2^-118 below the
+// largest amplitude).
+__device__ __forceinline__ void tc_scale(float &h, float &l, int e) {
+  if (e >= -126 && e <= 127) {
+    const float f = tc_pow2(e);
+    h = __fmul_rn(h, f);
+    l = __fmul_rn(l, f);
+  } else {
+    const int e1 = max(-126, min(127, e)), e2 = max(-126, min(127, e - e1));
+    const float f1 = tc_pow2(e1), f2 = tc_pow2(e2);
+    h = __fmul_rn(__fmul_rn(h, f1), f2);
+    l = __fmul_rn(__fmul_rn(l, f1), f2);
+  }
+}
+
+constexpr float kTcMagic = 12582912.f;   // 1.5 * 2^23
+
+// d = x m rounded to the nearest integer (ties to even) and the exact
+// remainder r = x m - d, for m a power of two and |x m| < 2^22.
+__device__ __forceinline__ float tc_digit(float x, float m, float &r) {
+  const float d = __fsub_rn(__fmaf_rn(x, m, kTcMagic), kTcMagic);
+  r = __fmaf_rn(x, m, -d);
+  return d;
+}
+
+__device__ __forceinline__ float tc_round(float x, float m) {
+  return __fsub_rn(__fmaf_rn(x, m, kTcMagic), kTcMagic);
+}
+
+// Digits of v = vh + vl with |vh| < 256 and |vl| <= 2^-15 (the scaled low word
+// of a pair): v = sum_j c_j 2^(-9(j-1)) + r, |r| <= 2^-36.  The high word gives
+// five digits with exact remainders, the low word adds to digits 3..5, and two
+// carries bring digits 4 and 5 back into [-256, 256] (digit 3 stays <= 265).
+__device__ __forceinline__ void tc_digits(float vh, float vl, float (&c)[5]) {
+  float r, q;
+  c[0] = tc_digit(vh, 1.f, r);
+  c[1] = tc_digit(r, 512.f, r);
+  float d3 = tc_digit(r, 512.f, r);
+  float d4 = tc_digit(r, 512.f, r);
+  float d5 = tc_round(r, 512.f);
+  d3 = __fadd_rn(d3, tc_digit(vl, 262144.f, r));
+  d4 = __fadd_rn(d4, tc_digit(r, 512.f, r));
+  d5 = __fadd_rn(d5, tc_round(r, 512.f));
+  q = tc_round(d5, 1.f / 512.f);
+  d5 = __fmaf_rn(q, -512.f, d5);
+  d4 = __fadd_rn(d4, q);
+  q = tc_round(d4, 1.f / 512.f);
+  d4 = __fmaf_rn(q, -512.f, d4);
+  d3 = __fadd_rn(d3, q);
+  c[2] = d3; c[3] = d4; c[4] = d5;
+}
+
+__device__ __forceinline__ uint32_t tc_pack(float a, float b) {
+  const __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// Addition pair (s, l), s <= l, of index a in lexicographic order.
+__host__ __device__ constexpr int tc_pair_s(int M, int a) {
+  int s = 0;
+  while (a >= M - s) { a -= M - s; ++s; }
+  return s;
+}
+__host__ __device__ constexpr int tc_pair_l(int M, int a) {
+  int s = 0;
+  while (a >= M - s) { a -= M - s; ++s; }
+  return s + a;
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier helpers of the pipeline
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tc_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc_smem_addr(bar)) : "memory");
+}
+
+// Bounded wait that also gives up as soon as another role raised the abort flag.
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile int *flag) {
+  for (uint32_t i = 0; i < kTcPolls; ++i) {
+    if (tc_mbar_try_wait(bar, parity)) return true;
+    if (*flag) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_abort(volatile int *flag, int *status) {
+  *flag = 1;
+  atomicExch(status, 1);
+}
+
+// ---------------------------------------------------------------------------
+// Decode of a configuration index into prefix sums S_m (Algorithm 2 read as a
+// search): for m = M-2 .. 0 the largest x with C(x, m+1) <= remaining rank,
+// found by a branch-free binary search with power-of-two steps (top = largest
+// power of two <= xdim) instead of a linear walk over N + M table entries.
+// ---------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ void tc_decode(uint32_t g, int N, uint32_t nc, const uint32_t *sat, int xdim, int top,
+                                          int (&S)[M]) {
+  uint32_t rem = nc - 1u - g;
+  int x = N + M - 1;
+#pragma unroll
+  for (int m = M - 2; m >= 0; --m) {
+    const uint32_t *row = sat + m * xdim;
+    int pos = m;                                          // C(m, m+1) = 0 <= rem
+    for (int step = top; step > 0; step >>= 1) {
+      const int c = pos + step;
+      if (c <= x - 1 && row[c] <= rem) pos = c;
+    }
+    rem -= row[pos];
+    S[m] = pos - m;
+    x = pos;
+  }
+  S[M - 1] = N;
+}
+
+// ---------------------------------------------------------------------------
+// Producer: digits of one column of X (all P additions) into the B operand
+// (K-major, 128 columns x KT), the column exponent at K position exp_pos().
+// ---------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ void tc_produce(const TwoPhaseArgs &t, uint32_t tile, uint32_t total, int cl, int top,
+                                           unsigned char *bbuf, const uint32_t *s_mod, const uint32_t *s_sat,
+                                           const float2 *s_sq) {
+  constexpr TcShape sh(M);
+  constexpr int P = sh.P;
+  constexpr int AE = sh.a_end();
+  constexpr int CH1 = sh.K1 / 8, CH2 = sh.K2 / 8, CHT = sh.KT / 8;
+  const ApplyArgs<uint32_t> &a = t.a;
+  const uint32_t col = tile * (uint32_t)kTcCols + cl;
+  const uint32_t cc = col < total ? col : total - 1u;
+  const uint32_t nrhs = (uint32_t)a.nrhs;
+  const uint32_t np = nrhs == 1u ? cc : cc / nrhs;
+  const int jr = (int)(cc - np * nrhs);
+
+  int S[M];
+  tc_decode<M>(np, a.N - 2, t.nc2, s_sat, a.xdim, top, S);
+  uint32_t U[M], V[M];
+  const uint32_t base = twophase_targets<M>(S, s_mod, a.xdim, a.nc, U, V);
+  int occ[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) occ[m] = S[m] - (m > 0 ? S[m - 1] : 0);
+
+  // all P gathers first, then X = B_a(n') C[n' + a] as FP32 pairs in place
+  const float4 *__restrict__ C = (const float4 *)a.C;
+  float4 v[P];
+#pragma unroll
+  for (int ai = 0; ai < P; ++ai) {
+    const int s = tc_pair_s(M, ai), l = tc_pair_l(M, ai);
+    v[ai] = __ldg(C + (size_t)(base - U[s] - V[l]) * nrhs + jr);
+  }
+  uint32_t ebits = 0;
+#pragma unroll
+  for (int ai = 0; ai < P; ++ai) {
+    const int s = tc_pair_s(M, ai), l = tc_pair_l(M, ai);
+    const float2 b1 = s_sq[occ[s] + 1];
+    const float2 b2 = s == l ? s_sq[occ[s] + 2] : s_sq[occ[l] + 1];
+    const float2 amp = df_mul(b1, b2);
+    fp2_t Xh, Xl;
+    fp2_dprod(fp2_make(v[ai].x, v[ai].y), fp2_make(v[ai].z, v[ai].w), fp2_make(amp.x, amp.x),
+              fp2_make(amp.y, amp.y), Xh, Xl);
+    v[ai] = make_float4(fp2_x(Xh), fp2_y(Xh), fp2_x(Xl), fp2_y(Xl));   // (Re hi, Im hi, Re lo, Im lo)
+    ebits = max(ebits, max(__float_as_uint(v[ai].x) & 0x7f800000u, __float_as_uint(v[ai].y) & 0x7f800000u));
+  }
+  const int field = (int)(ebits >> 23);
+  const int e_c = field > 0 ? field - 126 : 0;         // |X| < 2^e_c; all-zero column: digits 0
+  const int E = 8 - e_c;                                // v = X 2^E, |v| < 256
+  const bool wide = E > 127;                            // columns ~2^-119 below the largest amplitude
+  const float f1 = tc_pow2(min(E, 127)), f2 = tc_pow2(wide ? E - 127 : 0);
+
+  unsigned char *colbase = bbuf + (size_t)(cl >> 3) * (CHT * 128) + (cl & 7) * 16;
+#pragma unroll
+  for (int bi = 0; bi < AE / 4; ++bi) {
+    float dig[8][5];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int k = 8 * bi + r;                         // real index 2a + (0 Re, 1 Im)
+      if (k < 2 * P) {
+        const float4 x = v[k >> 1];
+        float vh = __fmul_rn((k & 1) ? x.y : x.x, f1), vl = __fmul_rn((k & 1) ? x.w : x.z, f1);
+        if (wide) {
+          vh = __fmul_rn(vh, f2);
+          vl = __fmul_rn(vl, f2);
+        }
+        tc_digits(vh, vl, dig[r]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 5; ++j) dig[r][j] = 0.f;
+      }
+    }
+    // part 1: positions 3k + (j - 1), j = 1..3; the exponent at exp_pos()
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      const int chunk = 3 * bi + ch;
+      if (chunk < CH1) {
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int p0 = 8 * ch + 2 * e, p1 = p0 + 1;
+          const float lo = dig[p0 / 3][p0 % 3];
+          const float hi = 8 * chunk + 2 * e + 1 == sh.exp_pos() ? (float)e_c : dig[p1 / 3][p1 % 3];
+          w[e] = tc_pack(lo, hi);
+        }
+        *(uint4 *)(colbase + chunk * 128) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+    // part 2: positions 2k + (j - 4), j = 4, 5
+#pragma unroll
+    for (int ch = 0; ch < 2; ++ch) {
+      const int chunk = 2 * bi + ch;
+      if (chunk < CH2) {
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) w[e] = tc_pack(dig[(8 * ch + 2 * e) / 2][3], dig[(8 * ch + 2 * e) / 2][4]);
+        *(uint4 *)(colbase + (CH1 + chunk) * 128) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+  }
+}
+
+// Combination of the five level sums of one real row into an FP32 pair.
+__device__ __forceinline__ void tc_combine(float s2, float s3, float s4, float s5, float s6, float &hi, float &lo) {
+  const float a3 = __fmul_rn(s3, 1.f / 512.f);
+  const float a4 = __fmul_rn(s4, 1.f / 262144.f);
+  const float a56 = __fmaf_rn(s6, 1.f / 68719476736.f, __fmul_rn(s5, 1.f / 134217728.f));
+  float s = __fadd_rn(s2, a3);
+  float bb = __fsub_rn(s, s2);
+  float e = __fadd_rn(__fsub_rn(s2, __fsub_rn(s, bb)), __fsub_rn(a3, bb));
+  const float s1 = __fadd_rn(s, a4);
+  bb = __fsub_rn(s1, s);
+  e = __fadd_rn(e, __fadd_rn(__fsub_rn(s, __fsub_rn(s1, bb)), __fsub_rn(a4, bb)));
+  e = __fadd_rn(e, a56);
+  hi = __fadd_rn(s1, e);
+  lo = __fsub_rn(e, __fsub_rn(hi, s1));
+}
+
+// ---------------------------------------------------------------------------
+// The kernel: persistent, one CTA per SM, tiles of 128 columns, three roles
+// joined by mbarriers (slot s = tile & 1 for the B buffer and the tensor
+// memory of a tile):
+//   producers (warps 0-3 for even k, warps 4-7 for odd k)
+//                           wait done[s] of tile k-2, write B[s], arrive full[s]
+//   MMA (warp 12, one lane) wait full[s] and empty[s] of tile k-2, issue, commit done[s]
+//   epilogue (warps 8-11)   wait done[s], drain tensor memory, write Y, arrive empty[s]
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPhaseArgs t) {
+  constexpr TcShape sh(M);
+  constexpr int RW = sh.RW, R2 = sh.R2, CH1 = sh.K1 / 8, CHT = sh.KT / 8;
+  constexpr int SROW = kTcStageRow;
+  const ApplyArgs<uint32_t> &a = t.a;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const TcSmem L(M, a.xdim, a.nsq);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rows = M > 1 ? M - 1 : 1;
+
+  // stage the A image, row exponents and tables
+  {
+    const uint4 *src = (const uint4 *)t.tc_a;
+    uint4 *dst = (uint4 *)(smem + L.off_a);
+    for (int i = tid; i < sh.a_bytes() / 16; i += kTcThreads) dst[i] = __ldg(src + i);
+    int *s_er = (int *)(smem + L.off_er);
+    for (int i = tid; i < R2; i += kTcThreads) s_er[i] = __ldg(t.tc_er + i);
+    uint32_t *s_mod = (uint32_t *)(smem + L.off_mod), *s_sat = (uint32_t *)(smem + L.off_sat);
+    for (int i = tid; i < rows * a.xdim; i += kTcThreads) {
+      s_mod[i] = a.mod[i];
+      s_sat[i] = a.sat[i];
+    }
+    float2 *s_sq = (float2 *)(smem + L.off_sq);
+    for (int i = tid; i < a.nsq; i += kTcThreads) s_sq[i] = ((const float2 *)a.sq)[i];
+  }
+  tc_fence_proxy_async();                                // the A image is read by the tensor core
+  uint64_t *full = (uint64_t *)(smem + L.off_bar), *done = full + 2, *empty = full + 4;
+  uint32_t *tslot = (uint32_t *)(full + 6);
+  volatile int *flag = (volatile int *)(tslot + 1);
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      tc_mbar_init(&full[i], kTcProducers);
+      tc_mbar_init(&done[i], 1);
+      tc_mbar_init(&empty[i], 4);
+    }
+    *flag = 0;
+    tc_fence_mbar_init();
+  }
+  if (warp == 12) tc_tmem_alloc(tslot, kTcTmemCols);
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  const uint32_t tbase = *tslot;
+
+  const uint32_t total = t.nc2 * (uint32_t)a.nrhs;
+  const uint32_t ntiles = (total + kTcCols - 1) / kTcCols;
+  const uint32_t mytiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  uint32_t issued = 0;                                   // MMA role: tiles committed
+
+  if (warp < 8) {
+    // ---------------- producers: group g = warp / 4 takes tiles k = g, g + 2, ... ----------------
+    const int g = warp >> 2, cl = tid & (kTcProducers - 1);
+    const uint32_t *s_mod = (const uint32_t *)(smem + L.off_mod);
+    const uint32_t *s_sat = (const uint32_t *)(smem + L.off_sat);
+    const float2 *s_sq = (const float2 *)(smem + L.off_sq);
+    int top = 1;
+    while (2 * top <= a.xdim) top *= 2;
+    unsigned char *bbuf = smem + (g ? L.off_b1 : L.off_b0);
+    for (uint32_t k = g; k < mytiles; k += 2) {
+      if (k >= 2 && !tc_wait(&done[g], ((k - 2) >> 1) & 1u, flag)) {
+        tc_abort(flag, t.status);
+        break;
+      }
+      tc_produce<M>(t, blockIdx.x + k * gridDim.x, total, cl, top, bbuf, s_mod, s_sat, s_sq);
+      tc_fence_proxy_async();
+      tc_arrive(&full[g]);
+    }
+  } else if (warp == 12) {
+    // ---------------- MMA issue ----------------
+    if (lane == 0) {
+      const uint32_t idesc = tc_idesc_f16(128, kTcCols);
+      const uint32_t a1_addr = tc_smem_addr(smem + L.off_a), a2_addr = a1_addr + sh.a1_bytes();
+      for (uint32_t k = 0; k < mytiles; ++k) {
+        const int s = k & 1;
+        if (!tc_wait(&full[s], (k >> 1) & 1u, flag) ||
+            (k >= 2 && !tc_wait(&empty[s], ((k - 2) >> 1) & 1u, flag))) {
+          tc_abort(flag, t.status);
+          break;
+        }
+        tc_fence_after_sync();
+        const uint32_t d1 = tbase + (uint32_t)s * 256u, d2 = d1 + 128u;
+        const uint32_t b_addr = tc_smem_addr(smem + (s ? L.off_b1 : L.off_b0));
+#pragma unroll
+        for (int kk = 0; kk < sh.KT / 16; ++kk)
+          tc_mma_f16(d1, tc_desc_kmajor(a1_addr + kk * 256, 128, CHT * 128),
+                     tc_desc_kmajor(b_addr + kk * 256, 128, CHT * 128), idesc, kk > 0);
+#pragma unroll
+        for (int kk = 0; kk < sh.K1 / 16; ++kk)
+          tc_mma_f16(d2, tc_desc_kmajor(a2_addr + kk * 256, 128, CH1 * 128),
+                     tc_desc_kmajor(b_addr + kk * 256, 128, CHT * 128), idesc, kk > 0);
+        tc_commit(&done[s]);
+        issued = k + 1;
+      }
+    }
+  } else {
+    // ---------------- epilogue: quarter q, real rows q*RW .. ----------------
+    // Lane l works on column l & 15 of each 16-column group and on complex
+    // rows (l >> 4) + 2i of the quarter.
+    const int q = warp - 8;
+    const int *s_er = (const int *)(smem + L.off_er);
+    float *stg = (float *)(smem + L.off_stg) + q * 64 * SROW;
+    const int nrow = min(RW, R2 - q * RW);               // real rows of this quarter (even, may be <= 0)
+    const int cx = lane & 15, r0 = lane >> 4;
+    float4 *__restrict__ Y = (float4 *)t.Y;
+    const size_t ldy = (size_t)total;
+    for (uint32_t k = 0; k < mytiles; ++k) {
+      const int s = k & 1;
+      if (!tc_wait(&done[s], (k >> 1) & 1u, flag)) {
+        tc_abort(flag, t.status);
+        break;
+      }
+      tc_fence_after_sync();
+      const uint32_t tile = blockIdx.x + k * gridDim.x;
+#pragma unroll 1
+      for (int g = 0; g < kTcCols / 16; ++g) {
+        float v1[16], v2[16];
+        const uint32_t ta = tbase + (uint32_t)s * 256u + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * g);
+        tc_ld_x16(ta, v1);
+        tc_ld_x16(ta + 128u, v2);
+        tc_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          *(float4 *)(stg + lane * SROW + 4 * i) = make_float4(v1[4 * i], v1[4 * i + 1], v1[4 * i + 2], v1[4 * i + 3]);
+          *(float4 *)(stg + (32 + lane) * SROW + 4 * i) =
+              make_float4(v2[4 * i], v2[4 * i + 1], v2[4 * i + 2], v2[4 * i + 3]);
+        }
+        __syncwarp();
+        const int ec = (int)stg[kTcExpSlot * SROW + cx] - 16;
+        const uint32_t colg = tile * (uint32_t)kTcCols + (uint32_t)(16 * g + cx);
+#pragma unroll
+        for (int it = 0; it < (RW + 2) / 4; ++it) {
+          const int rl = r0 + 2 * it;                    // complex row within the quarter
+          if (2 * rl < nrow) {
+            float hv[2], lv[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              const int i = 2 * rl + c;
+              tc_combine(stg[(4 * RW + i) * SROW + cx], stg[(3 * RW + i) * SROW + cx], stg[(2 * RW + i) * SROW + cx],
+                         stg[(1 * RW + i) * SROW + cx], stg[(0 * RW + i) * SROW + cx], hv[c], lv[c]);
+              tc_scale(hv[c], lv[c], s_er[q * RW + i] + ec);
+            }
+            if (colg < total)
+              Y[(size_t)((q * RW) / 2 + rl) * ldy + colg] = make_float4(hv[0], hv[1], lv[0], lv[1]);
+          }
+        }
+        __syncwarp();
+      }
+      tc_fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc_arrive(&empty[s]);
+    }
+  }
+
+  __syncthreads();
+  if (warp == 12) {
+    // after an abort, let the MMAs already committed finish before the
+    // columns are released
+    if (*flag && lane == 0 && issued > 0) {
+      const uint32_t last = issued - 1;
+      tc_mbar_wait(&done[last & 1], (last >> 1) & 1u, kTcPolls);
+    }
+    __syncwarp();
+    tc_fence_after_sync();
+    tc_tmem_dealloc(tbase, kTcTmemCols);
+  }
+}

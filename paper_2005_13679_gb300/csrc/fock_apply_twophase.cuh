@@ -23,6 +23,9 @@ struct TwoPhaseArgs {
   uint32_t nc2;                   // N_c(N - 2, M)
   void *Y;                        // [P][nc2 * nrhs]
   const float4 *g1, *g2;          // FP32-pair form: Gauss coefficients (see fock_apply.cu)
+  const void *tc_a;               // tensor-core phase 1: digit image of R (fock_apply_tc.cuh), or NULL
+  const int *tc_er;               // its row exponents
+  int *status;                    // nonzero after a bounded wait of phase 1 expired, or NULL
 };
 
 template <int M>
@@ -295,6 +298,8 @@ fock_twophase_sigma_df(const TwoPhaseArgs t) {
   const size_t ldy = (size_t)nc2 * nrhs;
   double out_scale = a.out_scale;
   if (a.in_exp) out_scale *= fock_pow2(__ldg(a.in_exp));
+  // Y is incomplete if phase 1 gave up a wait: report NaN rather than a wrong sigma
+  if (t.status && *(volatile const int *)t.status) out_scale = __longlong_as_double(0x7ff8000000000000ll);
 
   for (uint32_t tile = blockIdx.x * (uint32_t)nt; tile < nc; tile += gridDim.x * (uint32_t)nt) {
     const uint32_t g = tile + tid;

@@ -1,0 +1,118 @@
+// fock_twophase_tc.cu -- the two-phase apply with its phase 1 on the tensor
+// cores (fock_apply_tc.cuh), M = 2..6: host construction of the digit image
+// of R, launch of phase 1 and of the FP32-pair phase 2.
+#include <limits.h>
+#include <math.h>
+#include <string.h>
+
+#include <complex>
+#include <vector>
+
+#include "fock_apply_tc.cuh"
+
+// Digit image of the real form of R (P x P complex, row r = removal pair,
+// column a = addition pair, already divided by the coefficient scale):
+// rows 2r, 2r+1 are (Re, Im) of Y_r, columns 2a, 2a+1 multiply (Re, Im) of X_a.
+// Each real row rho gets e_rho with |R~[rho][k]| < 2^e_rho for all k and five
+// base-2^9 digits of R~ 2^(8 - e_rho), computed exactly in FP64.  The image is
+// the A operand of both chains in tensor-core shared-memory layout.
+int fock_tc_image(int M, const std::complex<double> *R, std::vector<unsigned char> &img, std::vector<int> &er) {
+  if (M < 2 || M > 6) return FOCK_ERR_UNSUPPORTED;
+  const TcShape sh(M);
+  const int P = sh.P, R2 = sh.R2;
+  std::vector<double> Rt((size_t)R2 * R2);
+  for (int r = 0; r < P; ++r)
+    for (int a = 0; a < P; ++a) {
+      const std::complex<double> v = R[(size_t)r * P + a];
+      Rt[(size_t)(2 * r) * R2 + 2 * a] = v.real();
+      Rt[(size_t)(2 * r) * R2 + 2 * a + 1] = -v.imag();
+      Rt[(size_t)(2 * r + 1) * R2 + 2 * a] = v.imag();
+      Rt[(size_t)(2 * r + 1) * R2 + 2 * a + 1] = v.real();
+    }
+  er.assign(R2, 0);
+  std::vector<float> dig((size_t)R2 * R2 * 5, 0.f);
+  for (int rho = 0; rho < R2; ++rho) {
+    int e = INT_MIN;
+    for (int k = 0; k < R2; ++k) {
+      const double x = Rt[(size_t)rho * R2 + k];
+      if (x != 0.0) {
+        int ex;
+        frexp(x, &ex);   // |x| < 2^ex
+        if (ex > e) e = ex;
+      }
+    }
+    if (e == INT_MIN) e = 0;
+    er[rho] = e;
+    for (int k = 0; k < R2; ++k) {
+      double v = ldexp(Rt[(size_t)rho * R2 + k], 8 - e);
+      for (int i = 0; i < 5; ++i) {
+        const double d = nearbyint(v);
+        dig[((size_t)rho * R2 + k) * 5 + i] = (float)d;
+        v = (v - d) * 512.0;
+      }
+    }
+  }
+  const int CH1 = sh.K1 / 8, CHT = sh.KT / 8;
+  img.assign(sh.a_bytes(), 0);
+  for (int chain = 0; chain < 2; ++chain) {
+    const int klen = chain == 0 ? sh.KT : sh.K1;
+    const int chunks = chain == 0 ? CHT : CH1;
+    unsigned char *base = img.data() + (chain == 0 ? 0 : sh.a1_bytes());
+    for (int lane = 0; lane < 128; ++lane) {
+      const int q = lane / 32, s = lane % 32 + 32 * chain;
+      if (s >= 5 * sh.RW) continue;
+      const int level = 6 - s / sh.RW, rho = q * sh.RW + s % sh.RW;
+      if (rho >= R2) continue;
+      for (int p = 0; p < klen; ++p) {
+        int k, j;
+        if (p < sh.K1) {
+          k = p / 3;
+          j = p % 3 + 1;
+        } else {
+          k = (p - sh.K1) / 2;
+          j = 4 + (p - sh.K1) % 2;
+        }
+        const int i = level - j;
+        if (k >= R2 || i < 1 || i > 5) continue;
+        const __half h = __float2half(dig[((size_t)rho * R2 + k) * 5 + (i - 1)]);
+        memcpy(base + tc_kmajor_offset(lane, p, chunks), &h, 2);
+      }
+    }
+  }
+  // chain-2 lane 28 of each quarter copies the column exponent that the
+  // producer stores at K position exp_pos()
+  const __half one = __float2half(1.f);
+  for (int q = 0; q < 4; ++q)
+    memcpy(img.data() + sh.a1_bytes() + tc_kmajor_offset(32 * q + (kTcExpSlot - 32), sh.exp_pos(), CH1), &one, 2);
+  return FOCK_OK;
+}
+
+size_t fock_tc_smem(int M, int xdim, int nsq) { return TcSmem(M, xdim, nsq).total; }
+
+template <int M>
+static int launch_tc(const TwoPhaseArgs &t, int dev, cudaStream_t s) {
+  const ApplyArgs<uint32_t> &a = t.a;
+  const size_t smem = TcSmem(M, a.xdim, a.nsq).total;
+  cudaError_t e = cudaFuncSetAttribute(fock_twophase_x_tc<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return fock_cuda_status(e);
+  const uint64_t total = (uint64_t)t.nc2 * (uint64_t)a.nrhs;
+  const uint64_t tiles = (total + kTcCols - 1) / kTcCols;
+  uint64_t grid = (uint64_t)fock_get_sm_count(dev);
+  if (grid > tiles) grid = tiles;
+  if (grid < 1) grid = 1;
+  fock_twophase_x_tc<M><<<(unsigned)grid, kTcThreads, smem, s>>>(t);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fock_cuda_status(e);
+  return fock_launch_grid(fock_twophase_sigma_df<M>, t, a.nc, twophase_sigma_smem(a.rows, a.xdim, a.nsq), dev, s);
+}
+
+int fock_launch_twophase_tc(const TwoPhaseArgs &t, int dev, cudaStream_t s) {
+  switch (t.a.M) {
+    case 2: return launch_tc<2>(t, dev, s);
+    case 3: return launch_tc<3>(t, dev, s);
+    case 4: return launch_tc<4>(t, dev, s);
+    case 5: return launch_tc<5>(t, dev, s);
+    case 6: return launch_tc<6>(t, dev, s);
+  }
+  return FOCK_ERR_UNSUPPORTED;
+}
