@@ -124,27 +124,26 @@ __device__ __forceinline__ float tc_round(float x, float m) {
   return __fsub_rn(__fmaf_rn(x, m, kTcMagic), kTcMagic);
 }
 
-// Digits of v = vh + vl with |vh| < 256 and |vl| <= 2^-15 (the scaled low word
-// of a pair): v = sum_j c_j 2^(-9(j-1)) + r, |r| <= 2^-36.  The high word gives
-// five digits with exact remainders, the low word adds to digits 3..5, and two
-// carries bring digits 4 and 5 back into [-256, 256] (digit 3 stays <= 265).
-__device__ __forceinline__ void tc_digits(float vh, float vl, float (&c)[5]) {
-  float r, q;
-  c[0] = tc_digit(vh, 1.f, r);
+// Digits of v = (xh + xl) 2^E, the pair of one real value of X at its column
+// scale (f = 2^E, f18 = 2^(E+18), |xh f| < 256, |xl f| <= 3 2^-16):
+//     v = c1 + c2 2^-9 + c3 2^-18 + c4 2^-27 + c5 2^-36 + r,   |r| <= 2^-37 (+ 2^-51).
+// The high word gives c1..c4 with exact remainders, the low word adds to c3
+// and c4, the two remainders share c5 (their FP32 sum is rounded far below
+// the digit's unit), and one carry folds c5 back into [-256, 256]:
+// |c1|, |c2|, |c5| <= 256, |c3| <= 268, |c4| <= 513.
+__device__ __forceinline__ void tc_digits(float xh, float xl, float f, float f18, float (&c)[5]) {
+  float r, u;
+  c[0] = tc_digit(xh, f, r);
   c[1] = tc_digit(r, 512.f, r);
-  float d3 = tc_digit(r, 512.f, r);
-  float d4 = tc_digit(r, 512.f, r);
-  float d5 = tc_round(r, 512.f);
-  d3 = __fadd_rn(d3, tc_digit(vl, 262144.f, r));
-  d4 = __fadd_rn(d4, tc_digit(r, 512.f, r));
-  d5 = __fadd_rn(d5, tc_round(r, 512.f));
-  q = tc_round(d5, 1.f / 512.f);
-  d5 = __fmaf_rn(q, -512.f, d5);
-  d4 = __fadd_rn(d4, q);
-  q = tc_round(d4, 1.f / 512.f);
-  d4 = __fmaf_rn(q, -512.f, d4);
-  d3 = __fadd_rn(d3, q);
-  c[2] = d3; c[3] = d4; c[4] = d5;
+  const float d3 = tc_digit(r, 512.f, r);
+  const float d4 = tc_digit(r, 512.f, r);
+  const float e3 = tc_digit(xl, f18, u);
+  const float e4 = tc_digit(u, 512.f, u);
+  const float c5 = tc_round(__fadd_rn(r, u), 512.f);
+  const float q = tc_round(c5, 1.f / 512.f);
+  c[4] = __fmaf_rn(q, -512.f, c5);
+  c[3] = __fadd_rn(__fadd_rn(d4, e4), q);
+  c[2] = __fadd_rn(d3, e3);
 }
 
 __device__ __forceinline__ uint32_t tc_pack(float a, float b) {
@@ -214,6 +213,7 @@ __device__ __forceinline__ void tc_decode(uint32_t g, int N, uint32_t nc, const 
 // ---------------------------------------------------------------------------
 // Producer: digits of one column of X (all P additions) into the B operand
 // (K-major, 128 columns x KT), the column exponent at K position exp_pos().
+// The P gathers of C are issued together before any arithmetic.
 // ---------------------------------------------------------------------------
 template <int M>
 __device__ __forceinline__ void tc_produce(const TwoPhaseArgs &t, uint32_t tile, uint32_t total, int cl, int top,
@@ -261,9 +261,16 @@ __device__ __forceinline__ void tc_produce(const TwoPhaseArgs &t, uint32_t tile,
   }
   const int field = (int)(ebits >> 23);
   const int e_c = field > 0 ? field - 126 : 0;         // |X| < 2^e_c; all-zero column: digits 0
-  const int E = 8 - e_c;                                // v = X 2^E, |v| < 256
-  const bool wide = E > 127;                            // columns ~2^-119 below the largest amplitude
-  const float f1 = tc_pow2(min(E, 127)), f2 = tc_pow2(wide ? E - 127 : 0);
+  int E = 8 - e_c;                                      // v = X 2^E, |v| < 256
+  if (E > 109) {                                        // columns ~2^-100 below the largest amplitude:
+#pragma unroll                                          // pre-scale so that 2^(E+18) stays a float
+    for (int ai = 0; ai < P; ++ai) {
+      v[ai].x = __fmul_rn(v[ai].x, 0x1p64f); v[ai].y = __fmul_rn(v[ai].y, 0x1p64f);
+      v[ai].z = __fmul_rn(v[ai].z, 0x1p64f); v[ai].w = __fmul_rn(v[ai].w, 0x1p64f);
+    }
+    E -= 64;
+  }
+  const float f = tc_pow2(E), f18 = tc_pow2(E + 18);
 
   unsigned char *colbase = bbuf + (size_t)(cl >> 3) * (CHT * 128) + (cl & 7) * 16;
 #pragma unroll
@@ -274,12 +281,7 @@ __device__ __forceinline__ void tc_produce(const TwoPhaseArgs &t, uint32_t tile,
       const int k = 8 * bi + r;                         // real index 2a + (0 Re, 1 Im)
       if (k < 2 * P) {
         const float4 x = v[k >> 1];
-        float vh = __fmul_rn((k & 1) ? x.y : x.x, f1), vl = __fmul_rn((k & 1) ? x.w : x.z, f1);
-        if (wide) {
-          vh = __fmul_rn(vh, f2);
-          vl = __fmul_rn(vl, f2);
-        }
-        tc_digits(vh, vl, dig[r]);
+        tc_digits((k & 1) ? x.y : x.x, (k & 1) ? x.w : x.z, f, f18, dig[r]);
       } else {
 #pragma unroll
         for (int j = 0; j < 5; ++j) dig[r][j] = 0.f;
@@ -438,12 +440,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
   } else {
     // ---------------- epilogue: quarter q, real rows q*RW .. ----------------
     // Lane l works on column l & 15 of each 16-column group and on complex
-    // rows (l >> 4) + 2i of the quarter.
+    // rows (l >> 4) + 2 it of the quarter; the load of the next group from
+    // tensor memory overlaps the combination of the current one.
+    constexpr int NIT = (RW + 2) / 4;
     const int q = warp - 8;
     const int *s_er = (const int *)(smem + L.off_er);
     float *stg = (float *)(smem + L.off_stg) + q * 64 * SROW;
     const int nrow = min(RW, R2 - q * RW);               // real rows of this quarter (even, may be <= 0)
     const int cx = lane & 15, r0 = lane >> 4;
+    int erow[NIT][2];                                    // e_rho - 16 of the rows of this lane
+#pragma unroll
+    for (int it = 0; it < NIT; ++it)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int i = 2 * (r0 + 2 * it) + c;
+        erow[it][c] = (i < nrow ? s_er[q * RW + i] : 0) - 16;
+      }
     float4 *__restrict__ Y = (float4 *)t.Y;
     const size_t ldy = (size_t)total;
     for (uint32_t k = 0; k < mytiles; ++k) {
@@ -454,12 +466,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
       }
       tc_fence_after_sync();
       const uint32_t tile = blockIdx.x + k * gridDim.x;
+      const uint32_t tq = tbase + (uint32_t)s * 256u + ((uint32_t)(32 * q) << 16);
+      float v1[16], v2[16];
+      tc_ld_x16(tq, v1);
+      tc_ld_x16(tq + 128u, v2);
 #pragma unroll 1
       for (int g = 0; g < kTcCols / 16; ++g) {
-        float v1[16], v2[16];
-        const uint32_t ta = tbase + (uint32_t)s * 256u + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * g);
-        tc_ld_x16(ta, v1);
-        tc_ld_x16(ta + 128u, v2);
         tc_wait_ld();
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -467,11 +479,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
           *(float4 *)(stg + (32 + lane) * SROW + 4 * i) =
               make_float4(v2[4 * i], v2[4 * i + 1], v2[4 * i + 2], v2[4 * i + 3]);
         }
+        if (g + 1 < kTcCols / 16) {
+          tc_ld_x16(tq + (uint32_t)(16 * (g + 1)), v1);
+          tc_ld_x16(tq + 128u + (uint32_t)(16 * (g + 1)), v2);
+        }
         __syncwarp();
-        const int ec = (int)stg[kTcExpSlot * SROW + cx] - 16;
+        const int ec = (int)stg[kTcExpSlot * SROW + cx];
         const uint32_t colg = tile * (uint32_t)kTcCols + (uint32_t)(16 * g + cx);
 #pragma unroll
-        for (int it = 0; it < (RW + 2) / 4; ++it) {
+        for (int it = 0; it < NIT; ++it) {
           const int rl = r0 + 2 * it;                    // complex row within the quarter
           if (2 * rl < nrow) {
             float hv[2], lv[2];
@@ -480,7 +496,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
               const int i = 2 * rl + c;
               tc_combine(stg[(4 * RW + i) * SROW + cx], stg[(3 * RW + i) * SROW + cx], stg[(2 * RW + i) * SROW + cx],
                          stg[(1 * RW + i) * SROW + cx], stg[(0 * RW + i) * SROW + cx], hv[c], lv[c]);
-              tc_scale(hv[c], lv[c], s_er[q * RW + i] + ec);
+              const int e = erow[it][c] + ec;
+              if (e >= -126) {
+                const float sc = tc_pow2(e);
+                hv[c] = __fmul_rn(hv[c], sc);
+                lv[c] = __fmul_rn(lv[c], sc);
+              } else {
+                tc_scale(hv[c], lv[c], e);
+              }
             }
             if (colg < total)
               Y[(size_t)((q * RW) / 2 + rl) * ldy + colg] = make_float4(hv[0], hv[1], lv[0], lv[1]);
