@@ -151,6 +151,21 @@ __device__ __forceinline__ uint32_t tc_pack(float a, float b) {
   return *reinterpret_cast<const uint32_t *>(&h);
 }
 
+// Addition pairs (s, l), s <= l, in lexicographic order, as compile-time tables.
+template <int M>
+struct TcPairs {
+  int s[M * (M + 1) / 2], l[M * (M + 1) / 2];
+  __host__ __device__ constexpr TcPairs() : s(), l() {
+    int a = 0;
+    for (int i = 0; i < M; ++i)
+      for (int j = i; j < M; ++j) {
+        s[a] = i;
+        l[a] = j;
+        ++a;
+      }
+  }
+};
+
 // Addition pair (s, l), s <= l, of index a in lexicographic order.
 __host__ __device__ constexpr int tc_pair_s(int M, int a) {
   int s = 0;
@@ -185,38 +200,12 @@ __device__ __forceinline__ void tc_abort(volatile int *flag, int *status) {
 }
 
 // ---------------------------------------------------------------------------
-// Decode of a configuration index into prefix sums S_m (Algorithm 2 read as a
-// search): for m = M-2 .. 0 the largest x with C(x, m+1) <= remaining rank,
-// found by a branch-free binary search with power-of-two steps (top = largest
-// power of two <= xdim) instead of a linear walk over N + M table entries.
-// ---------------------------------------------------------------------------
-template <int M>
-__device__ __forceinline__ void tc_decode(uint32_t g, int N, uint32_t nc, const uint32_t *sat, int xdim, int top,
-                                          int (&S)[M]) {
-  uint32_t rem = nc - 1u - g;
-  int x = N + M - 1;
-#pragma unroll
-  for (int m = M - 2; m >= 0; --m) {
-    const uint32_t *row = sat + m * xdim;
-    int pos = m;                                          // C(m, m+1) = 0 <= rem
-    for (int step = top; step > 0; step >>= 1) {
-      const int c = pos + step;
-      if (c <= x - 1 && row[c] <= rem) pos = c;
-    }
-    rem -= row[pos];
-    S[m] = pos - m;
-    x = pos;
-  }
-  S[M - 1] = N;
-}
-
-// ---------------------------------------------------------------------------
 // Producer: digits of one column of X (all P additions) into the B operand
 // (K-major, 128 columns x KT), the column exponent at K position exp_pos().
 // The P gathers of C are issued together before any arithmetic.
 // ---------------------------------------------------------------------------
 template <int M>
-__device__ __forceinline__ void tc_produce(const TwoPhaseArgs &t, uint32_t tile, uint32_t total, int cl, int top,
+__device__ __forceinline__ void tc_produce(const TwoPhaseArgs &t, uint32_t tile, uint32_t total, int cl,
                                            unsigned char *bbuf, const uint32_t *s_mod, const uint32_t *s_sat,
                                            const float2 *s_sq) {
   constexpr TcShape sh(M);
@@ -231,28 +220,31 @@ __device__ __forceinline__ void tc_produce(const TwoPhaseArgs &t, uint32_t tile,
   const int jr = (int)(cc - np * nrhs);
 
   int S[M];
-  tc_decode<M>(np, a.N - 2, t.nc2, s_sat, a.xdim, top, S);
+  fock_decode_fast<M>(np, a.N - 2, t.nc2, s_sat, a.xdim, S);
   uint32_t U[M], V[M];
   const uint32_t base = twophase_targets<M>(S, s_mod, a.xdim, a.nc, U, V);
-  int occ[M];
+  float2 sq1[M], sq2[M];                                // sqrt(n'_m + 1), sqrt(n'_m + 2) as pairs
 #pragma unroll
-  for (int m = 0; m < M; ++m) occ[m] = S[m] - (m > 0 ? S[m - 1] : 0);
+  for (int m = 0; m < M; ++m) {
+    const int occ = S[m] - (m > 0 ? S[m - 1] : 0);
+    sq1[m] = s_sq[occ + 1];
+    sq2[m] = s_sq[occ + 2];
+  }
 
   // all P gathers first, then X = B_a(n') C[n' + a] as FP32 pairs in place
+  constexpr TcPairs<M> pr;
   const float4 *__restrict__ C = (const float4 *)a.C;
   float4 v[P];
 #pragma unroll
   for (int ai = 0; ai < P; ++ai) {
-    const int s = tc_pair_s(M, ai), l = tc_pair_l(M, ai);
+    const int s = pr.s[ai], l = pr.l[ai];
     v[ai] = __ldg(C + (size_t)(base - U[s] - V[l]) * nrhs + jr);
   }
   uint32_t ebits = 0;
 #pragma unroll
   for (int ai = 0; ai < P; ++ai) {
-    const int s = tc_pair_s(M, ai), l = tc_pair_l(M, ai);
-    const float2 b1 = s_sq[occ[s] + 1];
-    const float2 b2 = s == l ? s_sq[occ[s] + 2] : s_sq[occ[l] + 1];
-    const float2 amp = df_mul(b1, b2);
+    const int s = pr.s[ai], l = pr.l[ai];
+    const float2 amp = df_mul(sq1[s], s == l ? sq2[s] : sq1[l]);
     fp2_t Xh, Xl;
     fp2_dprod(fp2_make(v[ai].x, v[ai].y), fp2_make(v[ai].z, v[ai].w), fp2_make(amp.x, amp.x),
               fp2_make(amp.y, amp.y), Xh, Xl);
@@ -398,15 +390,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
     const uint32_t *s_mod = (const uint32_t *)(smem + L.off_mod);
     const uint32_t *s_sat = (const uint32_t *)(smem + L.off_sat);
     const float2 *s_sq = (const float2 *)(smem + L.off_sq);
-    int top = 1;
-    while (2 * top <= a.xdim) top *= 2;
     unsigned char *bbuf = smem + (g ? L.off_b1 : L.off_b0);
     for (uint32_t k = g; k < mytiles; k += 2) {
       if (k >= 2 && !tc_wait(&done[g], ((k - 2) >> 1) & 1u, flag)) {
         tc_abort(flag, t.status);
         break;
       }
-      tc_produce<M>(t, blockIdx.x + k * gridDim.x, total, cl, top, bbuf, s_mod, s_sat, s_sq);
+      tc_produce<M>(t, blockIdx.x + k * gridDim.x, total, cl, bbuf, s_mod, s_sat, s_sq);
       tc_fence_proxy_async();
       tc_arrive(&full[g]);
     }

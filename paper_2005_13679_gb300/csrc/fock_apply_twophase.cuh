@@ -120,7 +120,7 @@ __device__ __forceinline__ uint32_t twophase_slots(uint32_t gc, const ApplyArgs<
                                                    const uint32_t *s_mod, const uint32_t *s_sat, const SqT *s_sq,
                                                    TwoPhaseSlot *slot, int nt) {
   int S[M];
-  fock_decode_prefix<uint32_t, M>(gc, a.N - 2, M, nc2, s_sat, a.xdim, S);
+  fock_decode_fast<M>(gc, a.N - 2, nc2, s_sat, a.xdim, S);
   uint32_t U[M], V[M];
   const uint32_t base = twophase_targets<M>(S, s_mod, a.xdim, a.nc, U, V);
 #pragma unroll
@@ -305,7 +305,7 @@ fock_twophase_sigma_df(const TwoPhaseArgs t) {
     const uint32_t g = tile + tid;
     const bool live = g < nc;
     int S[M], n[M];
-    fock_decode_prefix<uint32_t, M>(live ? g : nc - 1u, a.N, M, nc, s_sat, a.xdim, S);
+    fock_decode_fast<M>(live ? g : nc - 1u, a.N, nc, s_sat, a.xdim, S);
 #pragma unroll
     for (int m = 0; m < M; ++m) n[m] = S[m] - (m > 0 ? S[m - 1] : 0);
     uint32_t P1[M], P2[M];
@@ -427,7 +427,7 @@ fock_twophase_sigma_mixed(const TwoPhaseArgs t) {
     const uint32_t g = tile + tid;
     const bool live = g < nc;
     int S[M], n[M];
-    fock_decode_prefix<uint32_t, M>(live ? g : nc - 1u, a.N, M, nc, s_sat, a.xdim, S);
+    fock_decode_fast<M>(live ? g : nc - 1u, a.N, nc, s_sat, a.xdim, S);
 #pragma unroll
     for (int m = 0; m < M; ++m) n[m] = S[m] - (m > 0 ? S[m - 1] : 0);
     uint32_t P1[M], P2[M];

@@ -36,6 +36,39 @@ __device__ __forceinline__ void fock_decode_prefix(Idx gamma, int N, int M, Idx 
     if (m >= M - 1) S[m] = N;
 }
 
+// Greedy decoding as fock_decode_prefix for a compile-time number of
+// orbitals and 32-bit indices, with each search started at the closed-form
+// estimate x ~ (k! r)^(1/k) + (k - 1)/2 of the largest x with C(x, k) <= r
+// (k = m + 1, r the remaining rank) and corrected by single steps.  The table
+// is non-decreasing in x, so the corrections end at the same x as the linear
+// walk; they take one or two table reads instead of up to N + M.
+template <int M>
+__device__ __forceinline__ void fock_decode_fast(uint32_t gamma, int N, uint32_t nc, const uint32_t *__restrict__ sat,
+                                                 int xdim, int (&S)[M]) {
+  uint32_t rem = nc - 1u - gamma;
+  int x = N + M - 1;
+#pragma unroll
+  for (int m = M - 2; m >= 0; --m) {
+    const uint32_t *row = sat + m * xdim;
+    int xx;
+    if (m == 0) {
+      xx = (int)min(rem, (uint32_t)(x - 1));            // C(x, 1) = x
+    } else {
+      float kf = 1.f;                                    // (m + 1)!
+#pragma unroll
+      for (int i = 2; i <= m + 1; ++i) kf *= (float)i;
+      const float est = exp2f(__log2f((float)rem * kf) * (1.f / (m + 1))) + 0.5f * m;
+      xx = min(max((int)est, m), x - 1);
+      while (xx < x - 1 && row[xx + 1] <= rem) ++xx;
+      while (row[xx] > rem) --xx;
+    }
+    rem -= row[xx];
+    S[m] = xx - m;
+    x = xx;
+  }
+  S[M - 1] = N;
+}
+
 // Index of the configuration with prefix sums S (S[M-1] = N).
 template <class Idx, int MAXM>
 __device__ __forceinline__ Idx fock_rank_prefix(const int (&S)[MAXM], int M, Idx nc,
