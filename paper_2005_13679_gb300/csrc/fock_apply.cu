@@ -454,7 +454,8 @@ static size_t twophase_y_offset(const fock_space *sp, const fock_ham *ham, int n
 static size_t twophase_y_bytes(const fock_space *sp, int nrhs, int precision) {
   const int64_t nc2 = count_nm(sp->N - 2, sp->M);
   const size_t elem = precision == FOCK_PREC_F32_MIXED ? sizeof(float2) : sizeof(float4);
-  return (size_t)fock_pair_count(sp->M) * (size_t)nc2 * (size_t)nrhs * elem;
+  const size_t cols = ((size_t)nc2 * (size_t)nrhs + kYBlock - 1) / kYBlock * kYBlock;
+  return (size_t)fock_pair_count(sp->M) * cols * elem;
 }
 
 // Phase 1 on the tensor cores: FP64-class precision, dense coefficients with

@@ -24,15 +24,16 @@
 // max|R~ row| * max|X~ column| * 2P; the five level sums are combined into an
 // FP32 pair (TwoSum) for phase 2.
 //
-// Tensor memory holds the level sums: an MMA of M = 128 rows computes 128
-// (real row, level) combinations at once.  Warp quarter q of tensor memory
-// (lanes 32q .. 32q+31) serves real rows q*RW .. q*RW + RW - 1 and their five
-// levels: slot s = (6 - l) * RW + i (i the row within the quarter) is lane s of
-// chain 1 for s < 32 and lane s - 32 of chain 2 otherwise.  Chain 1 holds
-// levels 6, 5 and part of 4 and contracts over all digits; chain 2 holds the
-// rest of 4, 3 and 2 and needs only digits 1..3.  K is ordered
-// [digits 1..3 of every real index, interleaved | digits 4, 5 interleaved] so
-// chain 2 reads the first part only.
+// The MMA computes the transposed product: its M = 128 rows are the tile's
+// (configuration, rhs) columns, so tensor-memory lane c holds everything of
+// column c, and its N columns are (real row, level) combinations.  Real rows
+// come in groups of three, 16 tensor-memory columns per group: column
+// 16 g + 5 i + (6 - l) holds level l of real row 3 g + i, and column 15 (the
+// spare of group 0) receives the column exponent, which the producer stores at
+// K position K1 - 1 and a unit row of the coefficient image copies.  An
+// epilogue thread reads its own lane: two groups (32 columns) hold three
+// complex rows (Re and Im), so no data crosses lanes.  K is ordered
+// [digits 1..3 of every real index, interleaved | digits 4, 5 interleaved].
 #pragma once
 
 #include <cuda_fp16.h>
@@ -40,26 +41,23 @@
 #include "fock_apply_twophase.cuh"
 #include "fock_tc.cuh"
 
-constexpr int kTcCols = 128;        // (configuration, rhs) columns per tile = MMA N
+constexpr int kTcCols = 128;        // (configuration, rhs) columns per tile = MMA M
 constexpr int kTcProducers = 128;   // producer group: 4 warps, one thread per column
 constexpr int kTcThreads = 416;     // two producer groups (warps 0-3 even tiles, 4-7 odd tiles),
-                                    // warps 8-11 epilogue (one per tensor-memory quarter), warp 12 MMA
-constexpr int kTcTmemCols = 512;    // two tiles x (chain 1 + chain 2) x 128 columns
+                                    // warps 8-11 epilogue (warp 8 + q: tile columns 32q .. 32q+31), warp 12 MMA
+constexpr int kTcTmemCols = 512;    // two tiles x NT (<= 224) columns, at 0 and 256
 constexpr uint32_t kTcPolls = 1u << 20;
-constexpr int kTcStageRow = 20;     // floats per staged row (16 columns + 4 of padding against bank conflicts)
-constexpr int kTcStageBytes = 4 * 64 * kTcStageRow * 4;
-constexpr int kTcExpSlot = 60;      // chain-2 lane 28 of every quarter carries the column exponents
+constexpr int kTcExpCol = 15;       // tensor-memory column of the column exponent
 
 // Shape of the real-form product for M orbitals (2 <= M <= 6).
 struct TcShape {
-  int P, R2, RW, K1, K2, KT;
+  int P, R2, NG, NT, K1, K2, KT;
   __host__ __device__ constexpr explicit TcShape(int m)
-      : P(m * (m + 1) / 2), R2(m * (m + 1)), RW(2 * ((m * (m + 1) + 7) / 8)),
+      : P(m * (m + 1) / 2), R2(m * (m + 1)), NG((m * (m + 1) + 2) / 3), NT(16 * ((m * (m + 1) + 2) / 3)),
         K1((3 * m * (m + 1) + 15) / 16 * 16), K2((2 * m * (m + 1) + 15) / 16 * 16),
         KT((3 * m * (m + 1) + 15) / 16 * 16 + (2 * m * (m + 1) + 15) / 16 * 16) {}
-  // bytes of the A image: chain 1 (128 x KT) then chain 2 (128 x K1), fp16
-  __host__ __device__ constexpr int a1_bytes() const { return 128 * KT * 2; }
-  __host__ __device__ constexpr int a_bytes() const { return 128 * (KT + K1) * 2; }
+  // bytes of the coefficient image (NT rows x KT, fp16) and of one digit tile
+  __host__ __device__ constexpr int r_bytes() const { return NT * KT * 2; }
   __host__ __device__ constexpr int b_bytes() const { return kTcCols * KT * 2; }
   // K position of the column exponent (the last of part 1, never a digit)
   __host__ __device__ constexpr int exp_pos() const { return K1 - 1; }
@@ -70,18 +68,19 @@ struct TcShape {
     const int m = P > c1 ? (P > c2 ? P : c2) : (c1 > c2 ? c1 : c2);
     return (m + 3) / 4 * 4;
   }
+  // tensor-memory column of level l of real row rho
+  __host__ __device__ constexpr int col(int rho, int l) const { return 16 * (rho / 3) + 5 * (rho % 3) + (6 - l); }
 };
 
 struct TcSmem {
-  size_t off_a, off_b0, off_b1, off_stg, off_er, off_mod, off_sat, off_sq, off_bar, total;
+  size_t off_r, off_b0, off_b1, off_er, off_mod, off_sat, off_sq, off_bar, total;
   __host__ __device__ TcSmem(int M, int xdim, int nsq) {
     const TcShape sh(M);
     const int rows = M > 1 ? M - 1 : 1;
     size_t o = 0;
-    off_a = o;    o += sh.a_bytes();
+    off_r = o;    o += sh.r_bytes();
     off_b0 = o;   o += sh.b_bytes();
     off_b1 = o;   o += sh.b_bytes();
-    off_stg = o;  o += kTcStageBytes;
     off_er = o;   o = fock_align16(o + 4 * (size_t)sh.R2);
     off_mod = o;  o = fock_align16(o + 4 * (size_t)rows * xdim);
     off_sat = o;  o = fock_align16(o + 4 * (size_t)rows * xdim);
@@ -337,8 +336,7 @@ __device__ __forceinline__ void tc_combine(float s2, float s3, float s4, float s
 template <int M>
 __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPhaseArgs t) {
   constexpr TcShape sh(M);
-  constexpr int RW = sh.RW, R2 = sh.R2, CH1 = sh.K1 / 8, CHT = sh.KT / 8;
-  constexpr int SROW = kTcStageRow;
+  constexpr int R2 = sh.R2, NT = sh.NT, CHT = sh.KT / 8;
   const ApplyArgs<uint32_t> &a = t.a;
   extern __shared__ __align__(16) unsigned char smem[];
   const TcSmem L(M, a.xdim, a.nsq);
@@ -348,8 +346,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
   // stage the A image, row exponents and tables
   {
     const uint4 *src = (const uint4 *)t.tc_a;
-    uint4 *dst = (uint4 *)(smem + L.off_a);
-    for (int i = tid; i < sh.a_bytes() / 16; i += kTcThreads) dst[i] = __ldg(src + i);
+    uint4 *dst = (uint4 *)(smem + L.off_r);
+    for (int i = tid; i < sh.r_bytes() / 16; i += kTcThreads) dst[i] = __ldg(src + i);
     int *s_er = (int *)(smem + L.off_er);
     for (int i = tid; i < R2; i += kTcThreads) s_er[i] = __ldg(t.tc_er + i);
     uint32_t *s_mod = (uint32_t *)(smem + L.off_mod), *s_sat = (uint32_t *)(smem + L.off_sat);
@@ -360,7 +358,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
     float2 *s_sq = (float2 *)(smem + L.off_sq);
     for (int i = tid; i < a.nsq; i += kTcThreads) s_sq[i] = ((const float2 *)a.sq)[i];
   }
-  tc_fence_proxy_async();                                // the A image is read by the tensor core
+  tc_fence_proxy_async();                                // the image is read by the tensor core
   uint64_t *full = (uint64_t *)(smem + L.off_bar), *done = full + 2, *empty = full + 4;
   uint32_t *tslot = (uint32_t *)(full + 6);
   volatile int *flag = (volatile int *)(tslot + 1);
@@ -403,8 +401,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
   } else if (warp == 12) {
     // ---------------- MMA issue ----------------
     if (lane == 0) {
-      const uint32_t idesc = tc_idesc_f16(128, kTcCols);
-      const uint32_t a1_addr = tc_smem_addr(smem + L.off_a), a2_addr = a1_addr + sh.a1_bytes();
+      const uint32_t idesc = tc_idesc_f16(kTcCols, NT);
+      const uint32_t r_addr = tc_smem_addr(smem + L.off_r);
       for (uint32_t k = 0; k < mytiles; ++k) {
         const int s = k & 1;
         if (!tc_wait(&full[s], (k >> 1) & 1u, flag) ||
@@ -413,41 +411,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
           break;
         }
         tc_fence_after_sync();
-        const uint32_t d1 = tbase + (uint32_t)s * 256u, d2 = d1 + 128u;
-        const uint32_t b_addr = tc_smem_addr(smem + (s ? L.off_b1 : L.off_b0));
+        const uint32_t d = tbase + (uint32_t)s * 256u;
+        const uint32_t x_addr = tc_smem_addr(smem + (s ? L.off_b1 : L.off_b0));
 #pragma unroll
         for (int kk = 0; kk < sh.KT / 16; ++kk)
-          tc_mma_f16(d1, tc_desc_kmajor(a1_addr + kk * 256, 128, CHT * 128),
-                     tc_desc_kmajor(b_addr + kk * 256, 128, CHT * 128), idesc, kk > 0);
-#pragma unroll
-        for (int kk = 0; kk < sh.K1 / 16; ++kk)
-          tc_mma_f16(d2, tc_desc_kmajor(a2_addr + kk * 256, 128, CH1 * 128),
-                     tc_desc_kmajor(b_addr + kk * 256, 128, CHT * 128), idesc, kk > 0);
+          tc_mma_f16(d, tc_desc_kmajor(x_addr + kk * 256, 128, CHT * 128),
+                     tc_desc_kmajor(r_addr + kk * 256, 128, CHT * 128), idesc, kk > 0);
         tc_commit(&done[s]);
         issued = k + 1;
       }
     }
   } else {
-    // ---------------- epilogue: quarter q, real rows q*RW .. ----------------
-    // Lane l works on column l & 15 of each 16-column group and on complex
-    // rows (l >> 4) + 2 it of the quarter; the load of the next group from
-    // tensor memory overlaps the combination of the current one.
-    constexpr int NIT = (RW + 2) / 4;
+    // ---------------- epilogue: tile columns 32q .. 32q+31, one per lane ----------------
+    // Each pass reads 32 tensor-memory columns (two row groups = three
+    // complex rows) of the thread's own lane; the next pass's load overlaps
+    // the combination of the current one.
+    constexpr int NPASS = (NT + 31) / 32;
     const int q = warp - 8;
     const int *s_er = (const int *)(smem + L.off_er);
-    float *stg = (float *)(smem + L.off_stg) + q * 64 * SROW;
-    const int nrow = min(RW, R2 - q * RW);               // real rows of this quarter (even, may be <= 0)
-    const int cx = lane & 15, r0 = lane >> 4;
-    int erow[NIT][2];                                    // e_rho - 16 of the rows of this lane
-#pragma unroll
-    for (int it = 0; it < NIT; ++it)
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const int i = 2 * (r0 + 2 * it) + c;
-        erow[it][c] = (i < nrow ? s_er[q * RW + i] : 0) - 16;
-      }
     float4 *__restrict__ Y = (float4 *)t.Y;
-    const size_t ldy = (size_t)total;
     for (uint32_t k = 0; k < mytiles; ++k) {
       const int s = k & 1;
       if (!tc_wait(&done[s], (k >> 1) & 1u, flag)) {
@@ -455,38 +437,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
         break;
       }
       tc_fence_after_sync();
-      const uint32_t tile = blockIdx.x + k * gridDim.x;
+      const uint32_t colg = (blockIdx.x + k * gridDim.x) * (uint32_t)kTcCols + (uint32_t)(32 * q + lane);
+      const bool live = colg < total;
       const uint32_t tq = tbase + (uint32_t)s * 256u + ((uint32_t)(32 * q) << 16);
-      float v1[16], v2[16];
-      tc_ld_x16(tq, v1);
-      tc_ld_x16(tq + 128u, v2);
-#pragma unroll 1
-      for (int g = 0; g < kTcCols / 16; ++g) {
+      float v[32];
+      tc_ld_x16(tq, *reinterpret_cast<float(*)[16]>(&v[0]));
+      tc_ld_x16(tq + 16u, *reinterpret_cast<float(*)[16]>(&v[16]));
+      int ec = 0;
+#pragma unroll
+      for (int pass = 0; pass < NPASS; ++pass) {
         tc_wait_ld();
+        float w[32];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          *(float4 *)(stg + lane * SROW + 4 * i) = make_float4(v1[4 * i], v1[4 * i + 1], v1[4 * i + 2], v1[4 * i + 3]);
-          *(float4 *)(stg + (32 + lane) * SROW + 4 * i) =
-              make_float4(v2[4 * i], v2[4 * i + 1], v2[4 * i + 2], v2[4 * i + 3]);
+        for (int i = 0; i < 32; ++i) w[i] = v[i];
+        if (pass + 1 < NPASS) {
+          tc_ld_x16(tq + (uint32_t)(32 * (pass + 1)), *reinterpret_cast<float(*)[16]>(&v[0]));
+          if (32 * (pass + 1) + 16 < NT) tc_ld_x16(tq + (uint32_t)(32 * (pass + 1) + 16), *reinterpret_cast<float(*)[16]>(&v[16]));
         }
-        if (g + 1 < kTcCols / 16) {
-          tc_ld_x16(tq + (uint32_t)(16 * (g + 1)), v1);
-          tc_ld_x16(tq + 128u + (uint32_t)(16 * (g + 1)), v2);
-        }
-        __syncwarp();
-        const int ec = (int)stg[kTcExpSlot * SROW + cx];
-        const uint32_t colg = tile * (uint32_t)kTcCols + (uint32_t)(16 * g + cx);
+        if (pass == 0) ec = (int)w[kTcExpCol] - 16;
 #pragma unroll
-        for (int it = 0; it < NIT; ++it) {
-          const int rl = r0 + 2 * it;                    // complex row within the quarter
-          if (2 * rl < nrow) {
+        for (int j = 0; j < 3; ++j) {
+          const int r = 3 * pass + j;                      // complex row
+          if (2 * r < R2) {
             float hv[2], lv[2];
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-              const int i = 2 * rl + c;
-              tc_combine(stg[(4 * RW + i) * SROW + cx], stg[(3 * RW + i) * SROW + cx], stg[(2 * RW + i) * SROW + cx],
-                         stg[(1 * RW + i) * SROW + cx], stg[(0 * RW + i) * SROW + cx], hv[c], lv[c]);
-              const int e = erow[it][c] + ec;
+              const int rho = 2 * r + c;
+              const int b = sh.col(rho, 6) - 32 * pass;    // levels 6..2 at b .. b+4
+              tc_combine(w[b + 4], w[b + 3], w[b + 2], w[b + 1], w[b], hv[c], lv[c]);
+              const int e = s_er[rho] + ec;
               if (e >= -126) {
                 const float sc = tc_pow2(e);
                 hv[c] = __fmul_rn(hv[c], sc);
@@ -495,11 +474,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
                 tc_scale(hv[c], lv[c], e);
               }
             }
-            if (colg < total)
-              Y[(size_t)((q * RW) / 2 + rl) * ldy + colg] = make_float4(hv[0], hv[1], lv[0], lv[1]);
+            if (live) Y[twophase_yidx(r, colg, sh.P)] = make_float4(hv[0], hv[1], lv[0], lv[1]);
           }
         }
-        __syncwarp();
       }
       tc_fence_before_sync();
       __syncwarp();

@@ -18,10 +18,19 @@
 
 #include "fock_apply_dense.cuh"
 
+// Y is stored in blocks of kYBlock consecutive (configuration, rhs) columns:
+// block b holds rows r = 0..P-1 of columns [b kYBlock, (b + 1) kYBlock), each
+// row contiguous.  A tile of phase 1 writes one contiguous block, and the P
+// entries that phase 2 reads for one configuration lie within one block.
+constexpr int kYBlock = 128;
+__host__ __device__ __forceinline__ size_t twophase_yidx(int r, size_t col, int P) {
+  return (col / kYBlock) * ((size_t)P * kYBlock) + (size_t)r * kYBlock + (col % kYBlock);
+}
+
 struct TwoPhaseArgs {
   ApplyArgs<uint32_t> a;          // N-space tables, coefficients (dense, r*P + a), C, sigma, nrhs, scales
   uint32_t nc2;                   // N_c(N - 2, M)
-  void *Y;                        // [P][nc2 * nrhs]
+  void *Y;                        // blocks of kYBlock columns x P rows (twophase_yidx)
   const float4 *g1, *g2;          // FP32-pair form: Gauss coefficients (see fock_apply.cu)
   const void *tc_a;               // tensor-core phase 1: digit image of R (fock_apply_tc.cuh), or NULL
   const int *tc_er;               // its row exponents
@@ -203,7 +212,6 @@ fock_twophase_x_df(const TwoPhaseArgs t) {
   const int nrhs = a.nrhs;
   const float4 *__restrict__ C = (const float4 *)a.C;
   float4 *__restrict__ Y = (float4 *)t.Y;
-  const size_t ldy = (size_t)nc2 * nrhs;
 
   for (uint32_t tile = blockIdx.x * (uint32_t)nt; tile < nc2; tile += gridDim.x * (uint32_t)nt) {
     const uint32_t g = tile + tid;
@@ -263,7 +271,7 @@ fock_twophase_x_df(const TwoPhaseArgs t) {
               df_add_acc(rh, rl, -fp2_y(K12h[q]), -fp2_y(K12l[q]));
               df_add_acc(ih, il, k1h, k1l);
               df_add_acc(ih, il, k3h, k3l);
-              Y[(size_t)(r0 + q) * ldy + (size_t)g * nrhs + j] = make_float4(rh, ih, rl, il);
+              Y[twophase_yidx(r0 + q, (size_t)g * nrhs + j, P)] = make_float4(rh, ih, rl, il);
             }
           }
         }
@@ -295,7 +303,6 @@ fock_twophase_sigma_df(const TwoPhaseArgs t) {
   const uint32_t nc = a.nc, nc2 = t.nc2;
   const int nrhs = a.nrhs;
   const float4 *__restrict__ Y = (const float4 *)t.Y;
-  const size_t ldy = (size_t)nc2 * nrhs;
   double out_scale = a.out_scale;
   if (a.in_exp) out_scale *= fock_pow2(__ldg(a.in_exp));
   // Y is incomplete if phase 1 gave up a wait: report NaN rather than a wrong sigma
@@ -321,7 +328,7 @@ fock_twophase_sigma_df(const TwoPhaseArgs t) {
           if (!__any_sync(0xffffffffu, valid)) continue;
           const uint32_t r2 = valid ? q0 - (P1[q] - P1[k]) - (P2[M - 1] - P2[q]) : 0u;
           const float2 A = df_mul(s_sq[valid ? n[k] : 0], s_sq[valid ? n[q] - (k == q) : 0]);
-          const float4 y = __ldg(Y + (size_t)r * ldy + (size_t)r2 * nrhs + j);
+          const float4 y = __ldg(Y + twophase_yidx(r, (size_t)r2 * nrhs + j, M * (M + 1) / 2));
           fp2_t p, e;
           fp2_dprod(fp2_make(y.x, y.y), fp2_make(y.z, y.w), fp2_make(A.x, A.x), fp2_make(A.y, A.y), p, e);
           fp2_dacc(Ah, Al, p, e);
@@ -361,7 +368,6 @@ fock_twophase_x_mixed(const TwoPhaseArgs t) {
   const int nrhs = a.nrhs;
   const float2 *__restrict__ C = (const float2 *)a.C;
   float2 *__restrict__ Y = (float2 *)t.Y;
-  const size_t ldy = (size_t)nc2 * nrhs;
 
   for (uint32_t tile = blockIdx.x * (uint32_t)nt; tile < nc2; tile += gridDim.x * (uint32_t)nt) {
     const uint32_t g = tile + tid;
@@ -393,7 +399,7 @@ fock_twophase_x_mixed(const TwoPhaseArgs t) {
 #pragma unroll
           for (int q = 0; q < RB; ++q)
             if (r0 + q < P)
-              Y[(size_t)(r0 + q) * ldy + (size_t)g * nrhs + j] =
+              Y[twophase_yidx(r0 + q, (size_t)g * nrhs + j, P)] =
                   make_float2(fp2_x(A1[q]) - fp2_y(A1[q]), fp2_x(A2[q]) + fp2_y(A2[q]));
         }
       }
@@ -420,7 +426,6 @@ fock_twophase_sigma_mixed(const TwoPhaseArgs t) {
   const uint32_t nc = a.nc, nc2 = t.nc2;
   const int nrhs = a.nrhs;
   const float2 *__restrict__ Y = (const float2 *)t.Y;
-  const size_t ldy = (size_t)nc2 * nrhs;
   const float out_scale = (float)a.out_scale;
 
   for (uint32_t tile = blockIdx.x * (uint32_t)nt; tile < nc; tile += gridDim.x * (uint32_t)nt) {
@@ -443,7 +448,7 @@ fock_twophase_sigma_mixed(const TwoPhaseArgs t) {
           if (!__any_sync(0xffffffffu, valid)) continue;
           const uint32_t r2 = valid ? q0 - (P1[q] - P1[k]) - (P2[M - 1] - P2[q]) : 0u;
           const float A = s_sq[valid ? n[k] : 0] * s_sq[valid ? n[q] - (k == q) : 0];
-          const float2 y = __ldg(Y + (size_t)r * ldy + (size_t)r2 * nrhs + j);
+          const float2 y = __ldg(Y + twophase_yidx(r, (size_t)r2 * nrhs + j, M * (M + 1) / 2));
           fp2_dacc(Sh, Sl, fp2_make(y.x * A, y.y * A), 0ull);
         }
       }

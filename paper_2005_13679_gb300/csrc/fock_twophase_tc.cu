@@ -15,7 +15,8 @@
 // rows 2r, 2r+1 are (Re, Im) of Y_r, columns 2a, 2a+1 multiply (Re, Im) of X_a.
 // Each real row rho gets e_rho with |R~[rho][k]| < 2^e_rho for all k and five
 // base-2^9 digits of R~ 2^(8 - e_rho), computed exactly in FP64.  The image is
-// the A operand of both chains in tensor-core shared-memory layout.
+// the MMA's B operand (N = (real row, level) combinations, K-major) in
+// tensor-core shared-memory layout.
 int fock_tc_image(int M, const std::complex<double> *R, std::vector<unsigned char> &img, std::vector<int> &er) {
   if (M < 2 || M > 6) return FOCK_ERR_UNSUPPORTED;
   const TcShape sh(M);
@@ -52,18 +53,14 @@ int fock_tc_image(int M, const std::complex<double> *R, std::vector<unsigned cha
       }
     }
   }
-  const int CH1 = sh.K1 / 8, CHT = sh.KT / 8;
-  img.assign(sh.a_bytes(), 0);
-  for (int chain = 0; chain < 2; ++chain) {
-    const int klen = chain == 0 ? sh.KT : sh.K1;
-    const int chunks = chain == 0 ? CHT : CH1;
-    unsigned char *base = img.data() + (chain == 0 ? 0 : sh.a1_bytes());
-    for (int lane = 0; lane < 128; ++lane) {
-      const int q = lane / 32, s = lane % 32 + 32 * chain;
-      if (s >= 5 * sh.RW) continue;
-      const int level = 6 - s / sh.RW, rho = q * sh.RW + s % sh.RW;
-      if (rho >= R2) continue;
-      for (int p = 0; p < klen; ++p) {
+  // rows of the image: level l of real row rho at sh.col(rho, l); row 15
+  // copies the column exponent stored at K position exp_pos()
+  const int CHT = sh.KT / 8;
+  img.assign(sh.r_bytes(), 0);
+  for (int rho = 0; rho < R2; ++rho)
+    for (int level = 2; level <= 6; ++level) {
+      const int row = sh.col(rho, level);
+      for (int p = 0; p < sh.KT; ++p) {
         int k, j;
         if (p < sh.K1) {
           k = p / 3;
@@ -75,15 +72,11 @@ int fock_tc_image(int M, const std::complex<double> *R, std::vector<unsigned cha
         const int i = level - j;
         if (k >= R2 || i < 1 || i > 5) continue;
         const __half h = __float2half(dig[((size_t)rho * R2 + k) * 5 + (i - 1)]);
-        memcpy(base + tc_kmajor_offset(lane, p, chunks), &h, 2);
+        memcpy(img.data() + tc_kmajor_offset(row, p, CHT), &h, 2);
       }
     }
-  }
-  // chain-2 lane 28 of each quarter copies the column exponent that the
-  // producer stores at K position exp_pos()
   const __half one = __float2half(1.f);
-  for (int q = 0; q < 4; ++q)
-    memcpy(img.data() + sh.a1_bytes() + tc_kmajor_offset(32 * q + (kTcExpSlot - 32), sh.exp_pos(), CH1), &one, 2);
+  memcpy(img.data() + tc_kmajor_offset(kTcExpCol, sh.exp_pos(), CHT), &one, 2);
   return FOCK_OK;
 }
 
