@@ -163,8 +163,9 @@ def run_reference(args, w):
 # * direct FP32-pair complex term: coefficient x amplitude (one packed pair
 #   product, 14), two packed pair products with C (28) and two packed TwoSum
 #   accumulations (28) = 70; real coefficients 35;
-# * two-phase FP32-pair (dense coefficients, 2 <= M <= 8): Gauss's three
-#   products, 1.5 packed pair products and accumulations = 42;
+# * two-phase FP32-pair phase 1 (dense coefficients, M = 7, 8, or N beyond the
+#   tensor-core layout): Gauss's three products, 1.5 packed pair products and
+#   accumulations = 42;
 # * FP32-mixed: direct 10 (real 6), two-phase 8 (two packed FMAs);
 # * native FP64: 10 (real 6) on the FP64 pipe.
 FLOPS_PER_TERM = {("f64", "direct"): 70, ("f64", "twophase"): 42, ("f32_mixed", "direct"): 10,
@@ -173,15 +174,52 @@ FLOPS_PER_TERM_REAL = {("f64", "direct"): 35, ("f32_mixed", "direct"): 6, ("f64_
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
 
 
+SMEM_OPTIN = 232448     # bytes of shared memory one block may opt into on this architecture
+
+
+def tc_shape(M):
+    """Real-form sizes of the tensor-core phase 1 (fock_apply_tc.cuh)."""
+    r2 = M * (M + 1)
+    k1, k2 = (3 * r2 + 15) // 16 * 16, (2 * r2 + 15) // 16 * 16
+    nt = 16 * ((r2 + 2) // 3)
+    return r2, nt, k1 + k2
+
+
+def tc_fits(N, M):
+    """Shared-memory layout of the tensor-core phase 1 within the per-block limit."""
+    al = lambda x: (x + 15) // 16 * 16
+    r2, nt, kt = tc_shape(M)
+    xdim, nsq = N + M + 3, N + 4
+    o = nt * kt * 2 + 2 * 128 * kt * 2
+    o = al(o + 4 * r2)
+    o = al(o + 4 * (M - 1) * xdim)
+    o = al(o + 4 * (M - 1) * xdim)
+    o = al(o + 8 * nsq)
+    o = al(o + 56)
+    return o <= SMEM_OPTIN
+
+
 def path_of(w, prec):
     """Which kernel family serves this workload (mirrors the library's dispatch)."""
-    return "twophase" if (w.kind == "generic" and 2 <= w.M <= 8 and prec in (0, 2)) else "direct"
+    if w.kind == "generic" and 2 <= w.M <= 8 and prec in (0, 2):
+        return "twophase_tc" if (prec == 0 and w.M <= 6 and tc_fits(w.N, w.M)) else "twophase"
+    return "direct"
+
+
+def tc_flops(w):
+    """Tensor-core work of phase 1 per apply: the 15 digit-pair products of the
+    error-free split (levels i + j <= 6) over the (2P)^2 real-form entries,
+    2 flop per product, for every (N-2)-space column; and the MMA work the
+    kernel executes (N = 16 ceil(2P / 3) level columns, K = KT digit positions)."""
+    r2, nt, kt = tc_shape(w.M)
+    cols = math.comb(w.N - 2 + w.M - 1, w.M - 1) * w.nrhs
+    return cols * 15 * r2 * r2 * 2, cols * 2 * nt * kt
 
 
 def launches_per_step(w, prec):
     """Kernels of one apply: the FP32-pair input preparation (2), then the
     two-phase pair (dense coefficients, 2 <= M <= 8) or one kernel."""
-    return (2 if prec == 0 else 0) + (2 if path_of(w, prec) == "twophase" else 1)
+    return (2 if prec == 0 else 0) + (2 if path_of(w, prec).startswith("twophase") else 1)
 
 
 def executed_terms(w, h, W):
@@ -431,10 +469,28 @@ def main():
     nbytes = w.nc * w.nrhs * elem
     hbm_gbs = 2 * nbytes / (ms * 1e-3) / 1e9
     executed = executed_terms(w, h, W) * w.nrhs
-    key = (args.precision, path_of(w, prec))
-    flops_term = FLOPS_PER_TERM_REAL[key] if (H.real and key in FLOPS_PER_TERM_REAL) else FLOPS_PER_TERM[key]
-    achieved = executed * flops_term / (kernel_ms * 1e-3) / 1e12
+    path = path_of(w, prec)
     traffic = load_traffic(w.name, args.precision)
+    if path == "twophase_tc":
+        # dominant kernel = phase 1 on the tensor cores (fp16 digits, FP32 accumulators)
+        alg, mma = tc_flops(w)
+        achieved = alg / (kernel_ms * 1e-3) / 1e12
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                    "frac": achieved / peaks["bf16_tflops"], "traffic": traffic, "kernel": "fock_twophase_x_tc",
+                    "kernel_ms": kernel_ms, "algorithmic_flops": alg, "executed_mma_flops": mma,
+                    "executed_tflops": mma / (kernel_ms * 1e-3) / 1e12, "path": path,
+                    "peak_note": "fp16 dense has the nominal bf16 rate on this part: measured bf16 burst "
+                                 f"({peak_src}); of measured"}
+    else:
+        key = (args.precision, "twophase" if path.startswith("twophase") else path)
+        flops_term = FLOPS_PER_TERM_REAL[key] if (H.real and key in FLOPS_PER_TERM_REAL) else FLOPS_PER_TERM[key]
+        achieved = executed * flops_term / (kernel_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                    "kernel": "phase 1" if path.startswith("twophase") else "main",
+                    "kernel_ms": kernel_ms, "executed_terms": executed, "flops_per_term": flops_term,
+                    "path": path,
+                    "pipe": "FP32 (fma.rn.f32x2 and scalar); peak = 152 SMs x 128 lanes x 2 flop x 2070 MHz"}
     out = {
         "metric": METRIC, "value": value, "unit": "config-terms/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all,
@@ -446,11 +502,7 @@ def main():
         "applies_per_s": applies,
         "config_terms_per_apply": terms,
         "gpu_launches": launches_per_step(w, prec) * args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                     "kernel_ms": kernel_ms, "executed_terms": executed, "flops_per_term": flops_term,
-                     "path": path_of(w, prec),
-                     "pipe": "FP32 (fma.rn.f32x2 and scalar); peak = 152 SMs x 128 lanes x 2 flop x 2070 MHz"},
+        "roofline": roofline,
         "hbm": {"compulsory_bytes": 2 * nbytes, "achieved_gbs": hbm_gbs, "peak_gbs": peaks["hbm_gbs"],
                 "frac": hbm_gbs / peaks["hbm_gbs"], "peak_source": peak_src},
         "e2e": {"value": terms / (e2e_ms * 1e-3), "unit": "config-terms/s",

@@ -181,9 +181,12 @@ int fock_hamiltonian_is_real(const fock_ham *ham, int *is_real);
 /* Profiling hook: when set, every apply with this Hamiltonian records
  * start_event immediately before and stop_event immediately after its main
  * H C kernel, on the apply's stream (the input preparation of FOCK_PREC_F64 is
- * outside the pair).  Events are cudaEvent_t passed as void*, owned by the
- * caller; NULL, NULL clears the hook.  Not thread-safe with concurrent applies
- * on the same Hamiltonian. */
+ * outside the pair).  For the two-phase evaluation of dense coefficients the
+ * main kernel is the first phase (the product with the reduced coefficients
+ * over the (N-2)-particle space); the second phase follows the stop event.
+ * Events are cudaEvent_t passed as void*, owned by the caller; NULL, NULL
+ * clears the hook.  Not thread-safe with concurrent applies on the same
+ * Hamiltonian. */
 int fock_apply_set_events(fock_ham *ham, void *start_event, void *stop_event);
 
 /* Device workspace (bytes) an apply with these options needs; 0 if none. */

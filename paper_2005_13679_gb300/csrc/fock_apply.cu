@@ -537,7 +537,7 @@ static void fill_args(ApplyArgs<Idx> &a, const fock_space *sp, const fock_ham *h
 
 static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Cin, void *sigma, int nrhs,
                        int precision, const int32_t *map, const int *in_exp, bool maps, bool nrhs16, int maxm,
-                       void *ws, size_t ws_bytes, cudaStream_t stream);
+                       void *ws, size_t ws_bytes, cudaStream_t stream, bool *stop_recorded);
 
 int fock_apply_internal(const fock_space *sp, const fock_ham *ham, const void *C, void *sigma,
                         int nrhs, int precision, int arm, void *ws, size_t ws_bytes,
@@ -571,15 +571,18 @@ int fock_apply_internal(const fock_space *sp, const fock_ham *ham, const void *C
   }
   const bool maps = map != nullptr;
   if (ham->ev_start) FOCK_CUDA_TRY(cudaEventRecord(ham->ev_start, stream));
+  bool stop_recorded = false;
   const int st = launch_main(sp, ham, Cin, sigma, nrhs, precision, map, in_exp, maps, nrhs16, maxm, ws, ws_bytes,
-                             stream);
-  if (st == FOCK_OK && ham->ev_stop) FOCK_CUDA_TRY(cudaEventRecord(ham->ev_stop, stream));
+                             stream, &stop_recorded);
+  if (st == FOCK_OK && ham->ev_stop && !stop_recorded) FOCK_CUDA_TRY(cudaEventRecord(ham->ev_stop, stream));
   return st;
 }
 
+// For the two-phase paths the caller's stop event (fock_apply_set_events) is
+// recorded after phase 1, the dominant kernel; *stop_recorded tells the caller.
 static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Cin, void *sigma, int nrhs,
                        int precision, const int32_t *map, const int *in_exp, bool maps, bool nrhs16, int maxm,
-                       void *ws, size_t ws_bytes, cudaStream_t stream) {
+                       void *ws, size_t ws_bytes, cudaStream_t stream, bool *stop_recorded) {
   if (sp->idx32) {
     ApplyArgs<uint32_t> a;
     fill_args(a, sp, ham, Cin, sigma, nrhs, precision, map, in_exp);
@@ -595,6 +598,8 @@ static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Ci
       t.tc_a = nullptr;
       t.tc_er = nullptr;
       t.status = nullptr;
+      t.phase1_done = ham->ev_stop;
+      *stop_recorded = ham->ev_stop != nullptr;
       if (tc_eligible(sp, ham, a, nrhs, precision)) {
         t.tc_a = ham->d_tc_a;
         t.tc_er = ham->d_tc_er;

@@ -35,6 +35,7 @@ struct TwoPhaseArgs {
   const void *tc_a;               // tensor-core phase 1: digit image of R (fock_apply_tc.cuh), or NULL
   const int *tc_er;               // its row exponents
   int *status;                    // nonzero after a bounded wait of phase 1 expired, or NULL
+  cudaEvent_t phase1_done;        // recorded between the two phases when non-null (profiling hook)
 };
 
 template <int M>

@@ -8,6 +8,7 @@ static int launch_df(const TwoPhaseArgs &t, int dev, cudaStream_t s) {
   const TwoPhaseSmem<M> L(a.xdim, a.nsq, 2 * sizeof(float4), sizeof(TwoPhaseSlot) * M, FOCK_APPLY_THREADS);
   int st = fock_launch_grid(fock_twophase_x_df<M>, t, t.nc2, L.total, dev, s);
   if (st) return st;
+  if (t.phase1_done) FOCK_CUDA_TRY(cudaEventRecord(t.phase1_done, s));
   return fock_launch_grid(fock_twophase_sigma_df<M>, t, a.nc, twophase_sigma_smem(a.rows, a.xdim, a.nsq), dev, s);
 }
 
@@ -17,6 +18,7 @@ static int launch_mixed(const TwoPhaseArgs &t, int dev, cudaStream_t s) {
   const TwoPhaseSmem<M> L(a.xdim, a.nsq, sizeof(float2), sizeof(TwoPhaseSlot) * M, FOCK_APPLY_THREADS);
   int st = fock_launch_grid(fock_twophase_x_mixed<M>, t, t.nc2, L.total, dev, s);
   if (st) return st;
+  if (t.phase1_done) FOCK_CUDA_TRY(cudaEventRecord(t.phase1_done, s));
   return fock_launch_grid(fock_twophase_sigma_mixed<M>, t, a.nc, twophase_sigma_smem(a.rows, a.xdim, a.nsq), dev, s);
 }
 

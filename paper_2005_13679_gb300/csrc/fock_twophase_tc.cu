@@ -96,6 +96,7 @@ static int launch_tc(const TwoPhaseArgs &t, int dev, cudaStream_t s) {
   fock_twophase_x_tc<M><<<(unsigned)grid, kTcThreads, smem, s>>>(t);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fock_cuda_status(e);
+  if (t.phase1_done) FOCK_CUDA_TRY(cudaEventRecord(t.phase1_done, s));
   return fock_launch_grid(fock_twophase_sigma_df<M>, t, a.nc, twophase_sigma_smem(a.rows, a.xdim, a.nsq), dev, s);
 }
 
