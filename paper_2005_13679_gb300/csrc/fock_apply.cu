@@ -404,11 +404,8 @@ __global__ void fock_split_kernel(const double2 *__restrict__ x, int64_t n, cons
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double2 v = __ldg(x + i);
-    const double f = fock_pow2(sh);
-    const double re = v.x * f, im = v.y * f;
-    const float rh = __double2float_rn(re), ih = __double2float_rn(im);
-    const float rl = __double2float_rn(re - (double)rh), il = __double2float_rn(im - (double)ih);
-    y[i] = make_float4(rh, ih, rl, il);
+    const float2 re = df_split_bits(v.x, sh), im = df_split_bits(v.y, sh);
+    y[i] = make_float4(re.x, im.x, re.y, im.y);
   }
 }
 

@@ -304,10 +304,11 @@ fock_twophase_sigma_df(const TwoPhaseArgs t) {
   const uint32_t nc = a.nc, nc2 = t.nc2;
   const int nrhs = a.nrhs;
   const float4 *__restrict__ Y = (const float4 *)t.Y;
-  double out_scale = a.out_scale;
-  if (a.in_exp) out_scale *= fock_pow2(__ldg(a.in_exp));
+  // output scale 2^e_out: the coefficient scale (a power of two) and the input scale
+  int e_out = (int)(((unsigned long long)__double_as_longlong(a.out_scale) >> 52) & 0x7ff) - 1023;
+  if (a.in_exp) e_out += __ldg(a.in_exp);
   // Y is incomplete if phase 1 gave up a wait: report NaN rather than a wrong sigma
-  if (t.status && *(volatile const int *)t.status) out_scale = __longlong_as_double(0x7ff8000000000000ll);
+  const bool failed = t.status && *(volatile const int *)t.status;
 
   for (uint32_t tile = blockIdx.x * (uint32_t)nt; tile < nc; tile += gridDim.x * (uint32_t)nt) {
     const uint32_t g = tile + tid;
@@ -316,19 +317,26 @@ fock_twophase_sigma_df(const TwoPhaseArgs t) {
     fock_decode_fast<M>(live ? g : nc - 1u, a.N, nc, s_sat, a.xdim, S);
 #pragma unroll
     for (int m = 0; m < M; ++m) n[m] = S[m] - (m > 0 ? S[m - 1] : 0);
+    float2 sq0[M], sq1[M];                                  // sqrt(n_m), sqrt(n_m - 1) as pairs
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      sq0[m] = s_sq[n[m]];
+      sq1[m] = s_sq[max(n[m] - 1, 0)];
+    }
     uint32_t P1[M], P2[M];
     const uint32_t q0 = twophase_prefix2<M>(S, s_mod, a.xdim, nc2, P1, P2);
     for (int j = 0; j < nrhs; ++j) {
       fp2_t Ah = 0ull, Al = 0ull;
+      // every removal is evaluated: an impossible one has amplitude 0
+      // (sqrt(0) or sqrt(n - 1) = 0 for n = 1) and reads the block start
 #pragma unroll
       for (int k = 0; k < M; ++k) {
 #pragma unroll
         for (int q = k; q < M; ++q) {
           const int r = k * M - (k * (k - 1)) / 2 + (q - k);
-          const bool valid = live && (k == q ? n[k] >= 2 : (n[k] >= 1 && n[q] >= 1));
-          if (!__any_sync(0xffffffffu, valid)) continue;
+          const bool valid = k == q ? n[k] >= 2 : (n[k] >= 1 && n[q] >= 1);
           const uint32_t r2 = valid ? q0 - (P1[q] - P1[k]) - (P2[M - 1] - P2[q]) : 0u;
-          const float2 A = df_mul(s_sq[valid ? n[k] : 0], s_sq[valid ? n[q] - (k == q) : 0]);
+          const float2 A = df_mul(sq0[k], k == q ? sq1[k] : sq0[q]);
           const float4 y = __ldg(Y + twophase_yidx(r, (size_t)r2 * nrhs + j, M * (M + 1) / 2));
           fp2_t p, e;
           fp2_dprod(fp2_make(y.x, y.y), fp2_make(y.z, y.w), fp2_make(A.x, A.x), fp2_make(A.y, A.y), p, e);
@@ -339,8 +347,10 @@ fock_twophase_sigma_df(const TwoPhaseArgs t) {
         float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
         df_add_acc(rh, rl, fp2_x(Ah), fp2_x(Al));
         df_add_acc(ih, il, fp2_y(Ah), fp2_y(Al));
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
         ((double2 *)a.sigma)[(size_t)g * nrhs + j] =
-            make_double2(((double)rh + (double)rl) * out_scale, ((double)ih + (double)il) * out_scale);
+            failed ? make_double2(nan, nan)
+                   : make_double2(df_to_double_bits(rh, rl, e_out), df_to_double_bits(ih, il, e_out));
       }
     }
   }

@@ -53,6 +53,77 @@ __device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
   return make_float2(s, __fsub_rn(e, __fsub_rn(s, p)));
 }
 
+// ---- conversions between FP64 and FP32 pairs with integer operations -------
+// This part runs FP64 instructions at about 1/74 of the FP32 rate, so the
+// conversions at the ends of the FP32-pair path work on the bit patterns.
+
+// x 2^sh as an FP32 pair: hi = x 2^sh rounded to nearest-even, lo = the exact
+// remainder rounded to nearest.  Requires |x 2^sh| < 2^127; values below
+// 2^-125 (after scaling) become (0, 0), as do zeros and FP64 subnormals.
+__device__ __forceinline__ float2 df_split_bits(double x, int sh) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  const int e0 = ex - 1075 + sh;                       // |x| 2^sh = m 2^e0, m the 53-bit significand
+  if (ex == 0 || e0 + 52 < -125) return make_float2(0.f, 0.f);
+  const uint64_t m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  uint64_t mh = m >> 29;
+  const uint64_t r = m & 0x1FFFFFFFull;
+  if (r > 0x10000000ull || (r == 0x10000000ull && (mh & 1))) ++mh;   // round to 24 bits, ties to even
+  const int lo_i = (int)((int64_t)m - (int64_t)(mh << 29));          // |lo_i| <= 2^28
+  // 2^(e0 + 29) and 2^e0 as two float factors each (e0 + 29 <= 98 here)
+  const int a1 = max(e0 + 29, -126), a2 = e0 + 29 - a1;
+  const int c1 = max(e0, -126), c2 = e0 - c1;
+  float hi = __fmul_rn(__fmul_rn((float)(int)mh, __int_as_float((a1 + 127) << 23)), __int_as_float((max(a2, -126) + 127) << 23));
+  float lo = __fmul_rn(__fmul_rn(__int2float_rn(lo_i), __int_as_float((c1 + 127) << 23)), __int_as_float((max(c2, -126) + 127) << 23));
+  if (b >> 63) {
+    hi = -hi;
+    lo = -lo;
+  }
+  return make_float2(hi, lo);
+}
+
+// (hi + lo) 2^e as a double.  The pair is first renormalised by TwoSum (an
+// accumulated low word may exceed the high word's ulp after cancellation),
+// then the sum is formed exactly on the 2^-52 grid of the high significand
+// (bits of the low word below it are dropped, a relative error below 2^-52)
+// and rounded to 53 bits.
+__device__ __forceinline__ double df_to_double_bits(float h0, float l0, int e) {
+  const float hi = __fadd_rn(h0, l0);
+  const float bb = __fsub_rn(hi, h0);
+  const float lo = __fadd_rn(__fsub_rn(h0, __fsub_rn(hi, bb)), __fsub_rn(l0, bb));
+  const uint32_t bh = __float_as_uint(hi), bl = __float_as_uint(lo);
+  if ((bh & 0x7fffffffu) == 0u) return 0.0;
+  const int fh = (int)((bh >> 23) & 0xff), fl = (int)((bl >> 23) & 0xff);
+  int64_t mh = (int64_t)((bh & 0x7fffffu) | (fh ? 0x800000u : 0u));
+  int64_t ml = (int64_t)((bl & 0x7fffffu) | (fl ? 0x800000u : 0u));
+  const int eh = (fh ? fh : 1) - 150, el = (fl ? fl : 1) - 150;   // value = m 2^e
+  if (bh >> 31) mh = -mh;
+  if (bl >> 31) ml = -ml;
+  int64_t S = mh * (1ll << 29);                         // units of 2^(eh - 29)
+  const int d = el - (eh - 29);
+  if (ml != 0 && d > -40) S += d >= 0 ? ml * (1ll << d) : (ml >> -d);
+  if (S == 0) return 0.0;
+  const uint64_t sgn = S < 0 ? 0x8000000000000000ull : 0ull;
+  uint64_t u = (uint64_t)(S < 0 ? -S : S);
+  int shift = 63 - __clzll((long long)u) - 52;          // bring the leading 1 to bit 52
+  uint64_t mant;
+  if (shift > 0) {
+    const uint64_t rem = u & ((1ull << shift) - 1), half = 1ull << (shift - 1);
+    mant = u >> shift;
+    if (rem > half || (rem == half && (mant & 1))) {
+      ++mant;
+      if (mant >> 53) {
+        mant >>= 1;
+        ++shift;
+      }
+    }
+  } else {
+    mant = u << -shift;
+  }
+  const int ex = eh - 29 + e + shift + 52 + 1023;
+  return __longlong_as_double((long long)(sgn | ((uint64_t)ex << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
 // ---- native FP64 -----------------------------------------------------------
 struct PolF64 {
   using vec_t = double2;   // one complex element of C / sigma

@@ -228,3 +228,22 @@ def test_full_size_block_rhs_n20_m8(torch):
         assert rel(got, ref) <= 1e-12
         one = H.apply(Bd[:, j].contiguous(), precision=fock.FOCK_PREC_F64)
         assert torch.allclose(one, blk[:, j], rtol=0, atol=1e-13)
+
+
+def test_full_vector_fp32_pair_against_native(torch):
+    """All 8,259,888 rows of the generic N = 60, M = 6 workload: the FP64-class
+    path (tensor-core phase 1, FP32-pair phase 2, integer conversions at both
+    ends) against the native FP64 arm, which the small cases pin to the oracle.
+    Every row is checked, so a rare failure (a cancellation, a rounding carry,
+    an extreme exponent) cannot hide between sampled rows."""
+    w = inputs.WORKLOADS["generic_n60_m6"]
+    h, W = w.hamiltonian()
+    sp = fock.Space(w.N, w.M)
+    H = fock.Hamiltonian(sp, h, W)
+    Cd = torch.from_numpy(w.state()).cuda()
+    a = H.apply(Cd, precision=fock.FOCK_PREC_F64)
+    b = H.apply(Cd, precision=fock.FOCK_PREC_F64_NATIVE)
+    scale = b.abs().max().item()
+    assert (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item() <= 1e-12
+    assert (a - b).abs().max().item() <= 1e-11 * scale
+
