@@ -29,9 +29,10 @@ int fock_launch_sparse_f64(const SparseArgs &, bool, bool, int, cudaStream_t);
 int fock_launch_sparse_df(const SparseArgs &, bool, bool, int, cudaStream_t);
 int fock_launch_sparse_mixed(const SparseArgs &, bool, bool, int, cudaStream_t);
 int fock_launch_twophase(const TwoPhaseArgs &, bool, int, cudaStream_t);
-int fock_launch_twophase_tc(const TwoPhaseArgs &, int, cudaStream_t);
+int fock_launch_twophase_tc(const TwoPhaseArgs &, bool, int, cudaStream_t);
 int fock_tc_image(int M, const std::complex<double> *R, std::vector<unsigned char> &img, std::vector<int> &er);
-size_t fock_tc_smem(int M, int xdim, int nsq);
+int fock_tc_image_mixed(int M, const std::complex<double> *R, std::vector<unsigned char> &img, std::vector<int> &er);
+size_t fock_tc_smem(int M, int xdim, int nsq, bool mixed);
 
 // Segment form of one term (see fock_apply_sparse.cuh): the removal (k, q)
 // (q = -1 for one particle) and the addition (s, l) (s = -1 for one particle)
@@ -109,6 +110,8 @@ static void free_ham(fock_ham *h) {
   cudaFree(h->d_gauss2);
   cudaFree(h->d_tc_a);
   cudaFree(h->d_tc_er);
+  cudaFree(h->d_tc_ma);
+  cudaFree(h->d_tc_mer);
   cudaFree(h->d_slots);
   cudaFree(h->ws);
   cudaFree(h->hb_in);
@@ -333,6 +336,9 @@ extern "C" int fock_hamiltonian_create(const fock_space *sp, const double *h_hos
     st = fock_tc_image(M, Rs.data(), img, er);
     if (!st) st = upload(&H->d_tc_a, img.data(), img.size());
     if (!st) st = upload(&H->d_tc_er, er.data(), er.size());
+    if (!st) st = fock_tc_image_mixed(M, coef.data(), img, er);
+    if (!st) st = upload(&H->d_tc_ma, img.data(), img.size());
+    if (!st) st = upload(&H->d_tc_mer, er.data(), er.size());
   }
   if (!st) st = upload(&H->d_terms, terms.data(), nadd);
   if (!st) st = upload(&H->d_slots, slots.data(), nadd);
@@ -444,8 +450,12 @@ static bool twophase_eligible(const fock_space *sp, const fock_ham *ham, int pre
          (precision == FOCK_PREC_F64 || precision == FOCK_PREC_F32_MIXED);
 }
 
+// Y follows the FP64-class split copy of C, or a 256-byte header of status
+// words for the mixed form.
 static size_t twophase_y_offset(const fock_space *sp, const fock_ham *ham, int nrhs, int precision) {
-  return (fock_apply_ws_bytes(sp, ham, nrhs, precision) + 255) & ~(size_t)255;
+  size_t base = fock_apply_ws_bytes(sp, ham, nrhs, precision);
+  if (base < kWsHeader) base = kWsHeader;
+  return (base + 255) & ~(size_t)255;
 }
 
 static size_t twophase_y_bytes(const fock_space *sp, int nrhs, int precision) {
@@ -455,16 +465,19 @@ static size_t twophase_y_bytes(const fock_space *sp, int nrhs, int precision) {
   return (size_t)fock_pair_count(sp->M) * cols * elem;
 }
 
-// Phase 1 on the tensor cores: FP64-class precision, dense coefficients with
-// 2 <= M <= 6 (their digit image exists), its shared-memory layout within the
-// device's per-block limit and fewer than 2^31 (configuration, rhs) columns.
+// Phase 1 on the tensor cores: FP64-class or FP32-mixed precision, dense
+// coefficients with 2 <= M <= 6 (their images exist), the shared-memory
+// layout within the device's per-block limit and fewer than 2^31
+// (configuration, rhs) columns.
 static bool tc_eligible(const fock_space *sp, const fock_ham *ham, const ApplyArgs<uint32_t> &a, int nrhs,
                         int precision) {
-  if (precision != FOCK_PREC_F64 || !ham->d_tc_a || sp->M < 2 || sp->M > 6) return false;
+  const bool mixed = precision == FOCK_PREC_F32_MIXED;
+  if (!(precision == FOCK_PREC_F64 || mixed) || sp->M < 2 || sp->M > 6) return false;
+  if (!(mixed ? ham->d_tc_ma : ham->d_tc_a)) return false;
   if ((uint64_t)count_nm(sp->N - 2, sp->M) * (uint64_t)nrhs >= (1ull << 31)) return false;
   int optin = 0;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, sp->device) != cudaSuccess) return false;
-  return fock_tc_smem(sp->M, a.xdim, a.nsq) <= (size_t)optin;
+  return fock_tc_smem(sp->M, a.xdim, a.nsq, mixed) <= (size_t)optin;
 }
 
 // Workspace that selects the fastest path (the minimum is fock_apply_ws_bytes).
@@ -598,10 +611,12 @@ static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Ci
       t.phase1_done = ham->ev_stop;
       *stop_recorded = ham->ev_stop != nullptr;
       if (tc_eligible(sp, ham, a, nrhs, precision)) {
-        t.tc_a = ham->d_tc_a;
-        t.tc_er = ham->d_tc_er;
+        const bool mixed = precision == FOCK_PREC_F32_MIXED;
+        t.tc_a = mixed ? ham->d_tc_ma : ham->d_tc_a;
+        t.tc_er = mixed ? ham->d_tc_mer : ham->d_tc_er;
         t.status = (int *)ws + 2;
-        return fock_launch_twophase_tc(t, sp->device, stream);
+        if (mixed) FOCK_CUDA_TRY(cudaMemsetAsync(t.status, 0, sizeof(int), stream));
+        return fock_launch_twophase_tc(t, mixed, sp->device, stream);
       }
       return fock_launch_twophase(t, precision == FOCK_PREC_F32_MIXED, sp->device, stream);
     }

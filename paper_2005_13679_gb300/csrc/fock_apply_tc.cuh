@@ -72,22 +72,35 @@ struct TcShape {
   __host__ __device__ constexpr int col(int rho, int l) const { return 16 * (rho / 3) + 5 * (rho % 3) + (6 - l); }
 };
 
+// Shared-memory layout of the kernel for a policy with an nt x kt coefficient
+// image, kt-deep digit tiles, r2 row exponents and a square-root table of
+// sq_bytes per entry.
 struct TcSmem {
   size_t off_r, off_b0, off_b1, off_er, off_mod, off_sat, off_sq, off_bar, total;
-  __host__ __device__ TcSmem(int M, int xdim, int nsq) {
-    const TcShape sh(M);
+  __host__ __device__ TcSmem(int nt, int kt, int r2, int M, int xdim, int nsq, int sq_bytes) {
     const int rows = M > 1 ? M - 1 : 1;
     size_t o = 0;
-    off_r = o;    o += sh.r_bytes();
-    off_b0 = o;   o += sh.b_bytes();
-    off_b1 = o;   o += sh.b_bytes();
-    off_er = o;   o = fock_align16(o + 4 * (size_t)sh.R2);
+    off_r = o;    o += (size_t)nt * kt * 2;
+    off_b0 = o;   o += (size_t)kTcCols * kt * 2;
+    off_b1 = o;   o += (size_t)kTcCols * kt * 2;
+    off_er = o;   o = fock_align16(o + 4 * (size_t)r2);
     off_mod = o;  o = fock_align16(o + 4 * (size_t)rows * xdim);
     off_sat = o;  o = fock_align16(o + 4 * (size_t)rows * xdim);
-    off_sq = o;   o = fock_align16(o + 8 * (size_t)nsq);
+    off_sq = o;   o = fock_align16(o + (size_t)sq_bytes * nsq);
     off_bar = o;  o = fock_align16(o + 6 * 8 + 8);
     total = o;
   }
+};
+
+// Shape of the FP32-mixed product: one accumulator per real row, K holds
+// [X_h | 2^11 X_l | X_h] of the 2P real indices and the column exponent.
+struct TcMixedShape {
+  int P, R2, NT, KT;
+  __host__ __device__ constexpr explicit TcMixedShape(int m)
+      : P(m * (m + 1) / 2), R2(m * (m + 1)), NT((m * (m + 1) + 1 + 15) / 16 * 16),
+        KT((3 * m * (m + 1) + 1 + 15) / 16 * 16) {}
+  __host__ __device__ constexpr int r_bytes() const { return NT * KT * 2; }
+  __host__ __device__ constexpr int exp_pos() const { return 3 * R2; }
 };
 
 // 2^e as a float for -126 <= e <= 127.
@@ -195,7 +208,7 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile
 
 __device__ __forceinline__ void tc_abort(volatile int *flag, int *status) {
   *flag = 1;
-  atomicExch(status, 1);
+  if (status) atomicExch(status, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -325,38 +338,218 @@ __device__ __forceinline__ void tc_combine(float s2, float s3, float s4, float s
 }
 
 // ---------------------------------------------------------------------------
+// FP32-mixed producer: X = B_a(n') C[n' + a] in FP32 from complex64 C, the
+// column scaled by 2^E so that |X 2^E| < 2^15, and each real value split into
+// fp16 x_h = RN(X 2^E) and x_l = RN(2^11 (X 2^E - x_h)).
+// ---------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ void tc_produce_mixed(const TwoPhaseArgs &t, uint32_t tile, uint32_t total, int cl,
+                                                 unsigned char *bbuf, const uint32_t *s_mod, const uint32_t *s_sat,
+                                                 const float *s_sq) {
+  constexpr TcMixedShape sh(M);
+  constexpr int P = sh.P, R2 = sh.R2, CHT = sh.KT / 8;
+  const ApplyArgs<uint32_t> &a = t.a;
+  const uint32_t col = tile * (uint32_t)kTcCols + cl;
+  const uint32_t cc = col < total ? col : total - 1u;
+  const uint32_t nrhs = (uint32_t)a.nrhs;
+  const uint32_t np = nrhs == 1u ? cc : cc / nrhs;
+  const int jr = (int)(cc - np * nrhs);
+  int S[M];
+  fock_decode_fast<M>(np, a.N - 2, t.nc2, s_sat, a.xdim, S);
+  uint32_t U[M], V[M];
+  const uint32_t base = twophase_targets<M>(S, s_mod, a.xdim, a.nc, U, V);
+  float sq1[M], sq2[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int occ = S[m] - (m > 0 ? S[m - 1] : 0);
+    sq1[m] = s_sq[occ + 1];
+    sq2[m] = s_sq[occ + 2];
+  }
+  constexpr TcPairs<M> pr;
+  const float2 *__restrict__ C = (const float2 *)a.C;
+  float x[R2];
+#pragma unroll
+  for (int ai = 0; ai < P; ++ai) {
+    const float2 v = __ldg(C + (size_t)(base - U[pr.s[ai]] - V[pr.l[ai]]) * nrhs + jr);
+    x[2 * ai] = v.x;
+    x[2 * ai + 1] = v.y;
+  }
+  uint32_t ebits = 0;
+#pragma unroll
+  for (int ai = 0; ai < P; ++ai) {
+    const int s = pr.s[ai], l = pr.l[ai];
+    const float amp = sq1[s] * (s == l ? sq2[s] : sq1[l]);
+    x[2 * ai] *= amp;
+    x[2 * ai + 1] *= amp;
+    ebits = max(ebits, max(__float_as_uint(x[2 * ai]) & 0x7f800000u, __float_as_uint(x[2 * ai + 1]) & 0x7f800000u));
+  }
+  const int field = (int)(ebits >> 23);
+  const int e_c = field > 0 ? field - 126 : 0;          // |X| < 2^e_c
+  int E = 15 - e_c;
+  if (E > 127) {                                         // columns ~2^-112 below the largest amplitude
+#pragma unroll
+    for (int k = 0; k < R2; ++k) x[k] = __fmul_rn(x[k], 0x1p64f);
+    E -= 64;
+  }
+  const float f = tc_pow2(E);
+  __half xh[R2], xl[R2];
+#pragma unroll
+  for (int k = 0; k < R2; ++k) {
+    const float v = __fmul_rn(x[k], f);
+    xh[k] = __float2half_rn(v);
+    xl[k] = __float2half_rn(__fmul_rn(__fsub_rn(v, __half2float(xh[k])), 2048.f));
+  }
+  const __half hexp = __float2half_rn((float)e_c);
+  const __half hz = __float2half_rn(0.f);
+  unsigned char *colbase = bbuf + (size_t)(cl >> 3) * (CHT * 128) + (cl & 7) * 16;
+#pragma unroll
+  for (int ch = 0; ch < CHT; ++ch) {
+    uint32_t w[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      __half hv[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int p = 8 * ch + 2 * e + u;
+        hv[u] = p < R2 ? xh[p] : p < 2 * R2 ? xl[p - R2] : p < 3 * R2 ? xh[p - 2 * R2] : p == 3 * R2 ? hexp : hz;
+      }
+      w[e] = (uint32_t)__half_as_ushort(hv[0]) | ((uint32_t)__half_as_ushort(hv[1]) << 16);
+    }
+    *(uint4 *)(colbase + ch * 128) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Policies: shapes, producer, square-root table and epilogue of the two forms.
+// ---------------------------------------------------------------------------
+template <int M>
+struct TcPolDF {                                         // FP64-class: exact digits, level sums
+  static constexpr TcShape sh{M};
+  static constexpr int NT = sh.NT, KT = sh.KT, R2 = sh.R2, R_BYTES = sh.r_bytes();
+  using sq_t = float2;
+  __device__ static void produce(const TwoPhaseArgs &t, uint32_t tile, uint32_t total, int cl, unsigned char *bbuf,
+                                 const uint32_t *s_mod, const uint32_t *s_sat, const void *s_sq) {
+    tc_produce<M>(t, tile, total, cl, bbuf, s_mod, s_sat, (const float2 *)s_sq);
+  }
+  // Lane-local epilogue: 32 tensor-memory columns (three complex rows) per
+  // pass; the next pass's load overlaps the combination of the current one.
+  __device__ static void drain(const TwoPhaseArgs &t, uint32_t tq, uint32_t colg, bool live, const int *s_er) {
+    constexpr int NPASS = (NT + 31) / 32;
+    constexpr TcShape shp(M);
+    float4 *__restrict__ Y = (float4 *)t.Y;
+    float v[32];
+    tc_ld_x16(tq, *reinterpret_cast<float(*)[16]>(&v[0]));
+    tc_ld_x16(tq + 16u, *reinterpret_cast<float(*)[16]>(&v[16]));
+    int ec = 0;
+#pragma unroll
+    for (int pass = 0; pass < NPASS; ++pass) {
+      tc_wait_ld();
+      float w[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) w[i] = v[i];
+      if (pass + 1 < NPASS) {
+        tc_ld_x16(tq + (uint32_t)(32 * (pass + 1)), *reinterpret_cast<float(*)[16]>(&v[0]));
+        if (32 * (pass + 1) + 16 < NT)
+          tc_ld_x16(tq + (uint32_t)(32 * (pass + 1) + 16), *reinterpret_cast<float(*)[16]>(&v[16]));
+      }
+      if (pass == 0) ec = (int)w[kTcExpCol] - 16;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int r = 3 * pass + j;                      // complex row
+        if (2 * r < R2) {
+          float hv[2], lv[2];
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const int rho = 2 * r + c;
+            const int b = shp.col(rho, 6) - 32 * pass;   // levels 6..2 at b .. b+4
+            tc_combine(w[b + 4], w[b + 3], w[b + 2], w[b + 1], w[b], hv[c], lv[c]);
+            const int e = s_er[rho] + ec;
+            if (e >= -126) {
+              const float sc = tc_pow2(e);
+              hv[c] = __fmul_rn(hv[c], sc);
+              lv[c] = __fmul_rn(lv[c], sc);
+            } else {
+              tc_scale(hv[c], lv[c], e);
+            }
+          }
+          if (live) Y[twophase_yidx(r, colg, shp.P)] = make_float4(hv[0], hv[1], lv[0], lv[1]);
+        }
+      }
+    }
+  }
+};
+
+template <int M>
+struct TcPolMixed {                                      // FP32-mixed: fp16 hi/lo split, one accumulator per row
+  static constexpr TcMixedShape sh{M};
+  static constexpr int NT = sh.NT, KT = sh.KT, R2 = sh.R2, R_BYTES = sh.r_bytes();
+  using sq_t = float;
+  __device__ static void produce(const TwoPhaseArgs &t, uint32_t tile, uint32_t total, int cl, unsigned char *bbuf,
+                                 const uint32_t *s_mod, const uint32_t *s_sat, const void *s_sq) {
+    tc_produce_mixed<M>(t, tile, total, cl, bbuf, s_mod, s_sat, (const float *)s_sq);
+  }
+  // Y = D 2^(e_rho + e_c - 30): the row scale 2^(15 - e_rho) of the image and
+  // the column scale 2^(15 - e_c) of the digits taken out.
+  __device__ static void drain(const TwoPhaseArgs &t, uint32_t tq, uint32_t colg, bool live, const int *s_er) {
+    constexpr int P = M * (M + 1) / 2;
+    float2 *__restrict__ Y = (float2 *)t.Y;
+    float d[NT];
+#pragma unroll
+    for (int i = 0; i < NT / 16; ++i) tc_ld_x16(tq + (uint32_t)(16 * i), *reinterpret_cast<float(*)[16]>(&d[16 * i]));
+    tc_wait_ld();
+    const int ec = (int)d[R2] - 30;
+#pragma unroll
+    for (int r = 0; r < P; ++r) {
+      float v[2];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int e = s_er[2 * r + c] + ec;
+        v[c] = e >= -126 ? __fmul_rn(d[2 * r + c], tc_pow2(e))
+                         : __fmul_rn(__fmul_rn(d[2 * r + c], tc_pow2(-126)), tc_pow2(max(e + 126, -126)));
+      }
+      if (live) Y[twophase_yidx(r, colg, P)] = make_float2(v[0], v[1]);
+    }
+  }
+};
+
+template <class Pol, int M>
+__host__ __device__ inline TcSmem tc_smem_of(int xdim, int nsq) {
+  return TcSmem(Pol::NT, Pol::KT, Pol::R2, M, xdim, nsq, (int)sizeof(typename Pol::sq_t));
+}
+
+// ---------------------------------------------------------------------------
 // The kernel: persistent, one CTA per SM, tiles of 128 columns, three roles
-// joined by mbarriers (slot s = tile & 1 for the B buffer and the tensor
+// joined by mbarriers (slot s = tile & 1 for the digit tile and the tensor
 // memory of a tile):
 //   producers (warps 0-3 for even k, warps 4-7 for odd k)
 //                           wait done[s] of tile k-2, write B[s], arrive full[s]
 //   MMA (warp 12, one lane) wait full[s] and empty[s] of tile k-2, issue, commit done[s]
 //   epilogue (warps 8-11)   wait done[s], drain tensor memory, write Y, arrive empty[s]
 // ---------------------------------------------------------------------------
-template <int M>
+template <int M, class Pol>
 __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPhaseArgs t) {
-  constexpr TcShape sh(M);
-  constexpr int R2 = sh.R2, NT = sh.NT, CHT = sh.KT / 8;
+  constexpr int NT = Pol::NT, CHT = Pol::KT / 8;
   const ApplyArgs<uint32_t> &a = t.a;
   extern __shared__ __align__(16) unsigned char smem[];
-  const TcSmem L(M, a.xdim, a.nsq);
+  const TcSmem L = tc_smem_of<Pol, M>(a.xdim, a.nsq);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int rows = M > 1 ? M - 1 : 1;
 
-  // stage the A image, row exponents and tables
+  // stage the coefficient image, row exponents and tables
   {
     const uint4 *src = (const uint4 *)t.tc_a;
     uint4 *dst = (uint4 *)(smem + L.off_r);
-    for (int i = tid; i < sh.r_bytes() / 16; i += kTcThreads) dst[i] = __ldg(src + i);
+    for (int i = tid; i < Pol::R_BYTES / 16; i += kTcThreads) dst[i] = __ldg(src + i);
     int *s_er = (int *)(smem + L.off_er);
-    for (int i = tid; i < R2; i += kTcThreads) s_er[i] = __ldg(t.tc_er + i);
+    for (int i = tid; i < Pol::R2; i += kTcThreads) s_er[i] = __ldg(t.tc_er + i);
     uint32_t *s_mod = (uint32_t *)(smem + L.off_mod), *s_sat = (uint32_t *)(smem + L.off_sat);
     for (int i = tid; i < rows * a.xdim; i += kTcThreads) {
       s_mod[i] = a.mod[i];
       s_sat[i] = a.sat[i];
     }
-    float2 *s_sq = (float2 *)(smem + L.off_sq);
-    for (int i = tid; i < a.nsq; i += kTcThreads) s_sq[i] = ((const float2 *)a.sq)[i];
+    using sq_t = typename Pol::sq_t;
+    sq_t *s_sq = (sq_t *)(smem + L.off_sq);
+    for (int i = tid; i < a.nsq; i += kTcThreads) s_sq[i] = ((const sq_t *)a.sq)[i];
   }
   tc_fence_proxy_async();                                // the image is read by the tensor core
   uint64_t *full = (uint64_t *)(smem + L.off_bar), *done = full + 2, *empty = full + 4;
@@ -387,14 +580,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
     const int g = warp >> 2, cl = tid & (kTcProducers - 1);
     const uint32_t *s_mod = (const uint32_t *)(smem + L.off_mod);
     const uint32_t *s_sat = (const uint32_t *)(smem + L.off_sat);
-    const float2 *s_sq = (const float2 *)(smem + L.off_sq);
+    const void *s_sq = smem + L.off_sq;
     unsigned char *bbuf = smem + (g ? L.off_b1 : L.off_b0);
     for (uint32_t k = g; k < mytiles; k += 2) {
       if (k >= 2 && !tc_wait(&done[g], ((k - 2) >> 1) & 1u, flag)) {
         tc_abort(flag, t.status);
         break;
       }
-      tc_produce<M>(t, blockIdx.x + k * gridDim.x, total, cl, bbuf, s_mod, s_sat, s_sq);
+      Pol::produce(t, blockIdx.x + k * gridDim.x, total, cl, bbuf, s_mod, s_sat, s_sq);
       tc_fence_proxy_async();
       tc_arrive(&full[g]);
     }
@@ -414,7 +607,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
         const uint32_t d = tbase + (uint32_t)s * 256u;
         const uint32_t x_addr = tc_smem_addr(smem + (s ? L.off_b1 : L.off_b0));
 #pragma unroll
-        for (int kk = 0; kk < sh.KT / 16; ++kk)
+        for (int kk = 0; kk < Pol::KT / 16; ++kk)
           tc_mma_f16(d, tc_desc_kmajor(x_addr + kk * 256, 128, CHT * 128),
                      tc_desc_kmajor(r_addr + kk * 256, 128, CHT * 128), idesc, kk > 0);
         tc_commit(&done[s]);
@@ -423,13 +616,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
     }
   } else {
     // ---------------- epilogue: tile columns 32q .. 32q+31, one per lane ----------------
-    // Each pass reads 32 tensor-memory columns (two row groups = three
-    // complex rows) of the thread's own lane; the next pass's load overlaps
-    // the combination of the current one.
-    constexpr int NPASS = (NT + 31) / 32;
     const int q = warp - 8;
     const int *s_er = (const int *)(smem + L.off_er);
-    float4 *__restrict__ Y = (float4 *)t.Y;
     for (uint32_t k = 0; k < mytiles; ++k) {
       const int s = k & 1;
       if (!tc_wait(&done[s], (k >> 1) & 1u, flag)) {
@@ -438,46 +626,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
       }
       tc_fence_after_sync();
       const uint32_t colg = (blockIdx.x + k * gridDim.x) * (uint32_t)kTcCols + (uint32_t)(32 * q + lane);
-      const bool live = colg < total;
-      const uint32_t tq = tbase + (uint32_t)s * 256u + ((uint32_t)(32 * q) << 16);
-      float v[32];
-      tc_ld_x16(tq, *reinterpret_cast<float(*)[16]>(&v[0]));
-      tc_ld_x16(tq + 16u, *reinterpret_cast<float(*)[16]>(&v[16]));
-      int ec = 0;
-#pragma unroll
-      for (int pass = 0; pass < NPASS; ++pass) {
-        tc_wait_ld();
-        float w[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) w[i] = v[i];
-        if (pass + 1 < NPASS) {
-          tc_ld_x16(tq + (uint32_t)(32 * (pass + 1)), *reinterpret_cast<float(*)[16]>(&v[0]));
-          if (32 * (pass + 1) + 16 < NT) tc_ld_x16(tq + (uint32_t)(32 * (pass + 1) + 16), *reinterpret_cast<float(*)[16]>(&v[16]));
-        }
-        if (pass == 0) ec = (int)w[kTcExpCol] - 16;
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const int r = 3 * pass + j;                      // complex row
-          if (2 * r < R2) {
-            float hv[2], lv[2];
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              const int rho = 2 * r + c;
-              const int b = sh.col(rho, 6) - 32 * pass;    // levels 6..2 at b .. b+4
-              tc_combine(w[b + 4], w[b + 3], w[b + 2], w[b + 1], w[b], hv[c], lv[c]);
-              const int e = s_er[rho] + ec;
-              if (e >= -126) {
-                const float sc = tc_pow2(e);
-                hv[c] = __fmul_rn(hv[c], sc);
-                lv[c] = __fmul_rn(lv[c], sc);
-              } else {
-                tc_scale(hv[c], lv[c], e);
-              }
-            }
-            if (live) Y[twophase_yidx(r, colg, sh.P)] = make_float4(hv[0], hv[1], lv[0], lv[1]);
-          }
-        }
-      }
+      Pol::drain(t, tbase + (uint32_t)s * 256u + ((uint32_t)(32 * q) << 16), colg, colg < total, s_er);
       tc_fence_before_sync();
       __syncwarp();
       if (lane == 0) tc_arrive(&empty[s]);

@@ -437,7 +437,9 @@ fock_twophase_sigma_mixed(const TwoPhaseArgs t) {
   const uint32_t nc = a.nc, nc2 = t.nc2;
   const int nrhs = a.nrhs;
   const float2 *__restrict__ Y = (const float2 *)t.Y;
-  const float out_scale = (float)a.out_scale;
+  // Y is incomplete if the tensor-core phase 1 gave up a wait: report NaN
+  const float out_scale = (t.status && *(volatile const int *)t.status) ? __int_as_float(0x7fc00000)
+                                                                        : (float)a.out_scale;
 
   for (uint32_t tile = blockIdx.x * (uint32_t)nt; tile < nc; tile += gridDim.x * (uint32_t)nt) {
     const uint32_t g = tile + tid;

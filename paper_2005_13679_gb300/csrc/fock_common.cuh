@@ -114,6 +114,8 @@ struct fock_ham {
   float4 *d_gauss2;         // dense only: [ceil(P/2)*P] (Im R - Re R) of rows 2i, 2i+1, scaled
   unsigned char *d_tc_a;    // dense, 2 <= M <= 6: digit image of R for the tensor-core phase 1
   int *d_tc_er;             // its row exponents
+  unsigned char *d_tc_ma;   // the same for the FP32-mixed form (fp16 hi/lo split of R)
+  int *d_tc_mer;
   int32_t *d_slots;         // [nadd] jump-map slot of each term
   // workspace owned by the Hamiltonian (used when the caller passes none)
   void *ws;
