@@ -185,16 +185,22 @@ def tc_shape(M):
     return r2, nt, k1 + k2
 
 
-def tc_fits(N, M):
+def tc_shape_mixed(M):
+    """Real-form sizes of the FP32-mixed tensor-core phase 1."""
+    r2 = M * (M + 1)
+    return r2, (r2 + 1 + 15) // 16 * 16, (3 * r2 + 1 + 15) // 16 * 16
+
+
+def tc_fits(N, M, mixed=False):
     """Shared-memory layout of the tensor-core phase 1 within the per-block limit."""
     al = lambda x: (x + 15) // 16 * 16
-    r2, nt, kt = tc_shape(M)
+    r2, nt, kt = tc_shape_mixed(M) if mixed else tc_shape(M)
     xdim, nsq = N + M + 3, N + 4
     o = nt * kt * 2 + 2 * 128 * kt * 2
     o = al(o + 4 * r2)
     o = al(o + 4 * (M - 1) * xdim)
     o = al(o + 4 * (M - 1) * xdim)
-    o = al(o + 8 * nsq)
+    o = al(o + (4 if mixed else 8) * nsq)
     o = al(o + 56)
     return o <= SMEM_OPTIN
 
@@ -202,18 +208,20 @@ def tc_fits(N, M):
 def path_of(w, prec):
     """Which kernel family serves this workload (mirrors the library's dispatch)."""
     if w.kind == "generic" and 2 <= w.M <= 8 and prec in (0, 2):
-        return "twophase_tc" if (prec == 0 and w.M <= 6 and tc_fits(w.N, w.M)) else "twophase"
+        return "twophase_tc" if (w.M <= 6 and tc_fits(w.N, w.M, prec == 2)) else "twophase"
     return "direct"
 
 
-def tc_flops(w):
-    """Tensor-core work of phase 1 per apply: the 15 digit-pair products of the
-    error-free split (levels i + j <= 6) over the (2P)^2 real-form entries,
-    2 flop per product, for every (N-2)-space column; and the MMA work the
-    kernel executes (N = 16 ceil(2P / 3) level columns, K = KT digit positions)."""
-    r2, nt, kt = tc_shape(w.M)
+def tc_flops(w, mixed=False):
+    """Tensor-core work of phase 1 per apply and the MMA work executed, for
+    every (N-2)-space column: FP64-class, the 15 digit-pair products of the
+    error-free split (levels i + j <= 6) over the (2P)^2 real-form entries;
+    FP32-mixed, the 3 products of the fp16 hi/lo split (R_h X_h, R_h X_l,
+    R_l X_h); 2 flop per product.  Executed: 2 N K per column with the MMA's
+    N (level or row columns) and K (digit positions)."""
+    r2, nt, kt = tc_shape_mixed(w.M) if mixed else tc_shape(w.M)
     cols = math.comb(w.N - 2 + w.M - 1, w.M - 1) * w.nrhs
-    return cols * 15 * r2 * r2 * 2, cols * 2 * nt * kt
+    return cols * (3 if mixed else 15) * r2 * r2 * 2, cols * 2 * nt * kt
 
 
 def launches_per_step(w, prec):
@@ -473,7 +481,7 @@ def main():
     traffic = load_traffic(w.name, args.precision)
     if path == "twophase_tc":
         # dominant kernel = phase 1 on the tensor cores (fp16 digits, FP32 accumulators)
-        alg, mma = tc_flops(w)
+        alg, mma = tc_flops(w, prec == 2)
         achieved = alg / (kernel_ms * 1e-3) / 1e12
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                     "frac": achieved / peaks["bf16_tflops"], "traffic": traffic, "kernel": "fock_twophase_x_tc",
