@@ -526,6 +526,9 @@ def main():
             if p == 2:
                 X = X.to(torch.complex64)
             Y = torch.empty_like(X)
+            del wsb                                  # each precision gets its own preferred workspace
+            wsb = torch.empty(max(fock.fock_apply_workspace_size(sp.handle, H.handle, w.nrhs, p), 16),
+                              dtype=torch.uint8, device="cuda")
             steps = 2 if p == 1 else max(3, args.steps // 2)
             t = time_steps(torch, lambda: fock.fock_apply_H(sp.handle, H.handle, X, Y, w.nrhs, p,
                                                               fock.FOCK_ARM_AUTO, wsb), steps, 1, lambda: None)

@@ -14,6 +14,9 @@ Contents (Andriati & Gammal, arXiv:2005.13679):
   definition (unrank, move particles, rank);
 * ``apply_push``, ``apply_rows``, ``dense_hamiltonian`` -- sigma = H C of
   Eq. Haction from the operator strings of Eqs. noninteracting/interacting;
+* ``rho1``, ``rho2`` -- the one- and two-body density matrices of Eqs. rho1
+  and rho2, each element by its definition <C| O C> with O the unit one- or
+  two-body operator applied by ``apply_push``;
 * ``lanczos_ground`` -- Lanczos with complete re-orthogonalisation and a
   tridiagonal eigen-solve, as in Sec. 5;
 * ``bethe_ground_energy`` -- the Lieb-Liniger ground state from the Bethe
@@ -193,6 +196,39 @@ def column_terms(N: int, M: int, h, W, gamma: int) -> int:
     hh = _cplx(h, (M, M))
     WW = None if W is None else _cplx(W, (M, M, M, M))
     return int(_load().oracle_column_terms(N, M, _ptr(hh), None if WW is None else _ptr(WW), int(gamma)))
+
+
+# --------------------------------------------------------------------------
+# Density matrices (Eqs. rho1, rho2)
+# --------------------------------------------------------------------------
+def rho1(N: int, M: int, C) -> np.ndarray:
+    """rho1[k, l] = <C| a^dag_k a_l |C> (Eq. rho1): the expectation of the unit
+    one-body operator h = E_kl, applied by the push form."""
+    CC = _cplx(C, (nc(N, M),))
+    out = np.empty((M, M), dtype=np.complex128)
+    for k in range(M):
+        for l in range(M):
+            h = np.zeros((M, M), dtype=np.complex128)
+            h[k, l] = 1.0
+            out[k, l] = np.vdot(CC, apply_push(N, M, h, None, CC))
+    return out
+
+
+def rho2(N: int, M: int, C) -> np.ndarray:
+    """rho2[k, l, q, s] = <C| a^dag_k a^dag_l a_q a_s |C> (Eq. rho2): the
+    expectation of the two-body operator with W[k, l, q, s] = 2 (W multiplies
+    1/2 a^dag_k a^dag_l a_q a_s), applied by the push form."""
+    CC = _cplx(C, (nc(N, M),))
+    zero_h = np.zeros((M, M), dtype=np.complex128)
+    out = np.empty((M, M, M, M), dtype=np.complex128)
+    for k in range(M):
+        for l in range(M):
+            for q in range(M):
+                for s in range(M):
+                    W = np.zeros((M, M, M, M), dtype=np.complex128)
+                    W[k, l, q, s] = 2.0
+                    out[k, l, q, s] = np.vdot(CC, apply_push(N, M, zero_h, W, CC))
+    return out
 
 
 # --------------------------------------------------------------------------
