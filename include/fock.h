@@ -260,6 +260,25 @@ int fock_lanczos_ground(const fock_space *sp, const fock_ham *ham, int32_t max_i
                         void *vec_dev, int32_t *iters, void *stream);
 
 /* ------------------------------------------------------------------------- */
+/* Density matrices                                                          */
+/* ------------------------------------------------------------------------- */
+/* One- and two-body density matrices of the state C (Eqs. rho1 and rho2):
+ *     rho1_host[2 (k M + l) + {0,1}]             = <C| a^dag_k a_l |C>,
+ *     rho2_host[2 (((k M + l) M + q) M + s) + {0,1}] = <C| a^dag_k a^dag_l a_q a_s |C>,
+ * complex128 interleaved, host memory of M^2 and M^4 complex values; either
+ * may be NULL (not both).  C_dev holds N_c complex128 values on the space's
+ * device (not required to be normalised).  Computed as Gram matrices of the
+ * vectors a_l C over the (N-1)-particle and a_q a_s C over the (N-2)-particle
+ * configurations: FP32-pair products within tiles of 128 configurations, FP64
+ * sums across tiles, block partials added in a fixed order (deterministic).
+ * rho2 is zero for N < 2.  Allocates and frees its own device workspace
+ * (16 B per configuration plus the partial sums).  Synchronous on `stream`.
+ * FOCK_ERR_UNSUPPORTED for M > 12 or N_c >= 2^32 - 1; FOCK_ERR_DEVICE when
+ * the current device is not the space's. */
+int fock_density_matrices(const fock_space *sp, const void *C_dev, double *rho1_host, double *rho2_host,
+                          void *stream);
+
+/* ------------------------------------------------------------------------- */
 /* Uneven batches of independent problems                                    */
 /* ------------------------------------------------------------------------- */
 typedef struct fock_batch fock_batch;

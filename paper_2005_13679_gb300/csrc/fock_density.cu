@@ -1,0 +1,334 @@
+// fock_density.cu -- one- and two-body density matrices (Eqs. rho1, rho2):
+//
+//     rho1[k][l]       = <Psi| a^dag_k a_l |Psi>           = sum_{m'} conj(Z_k[m']) Z_l[m'],
+//     rho2[k][l][q][s] = <Psi| a^dag_k a^dag_l a_q a_s |Psi> = sum_{n'} conj(X_{kl}[n']) X_{qs}[n'],
+//
+// with Z_l[m'] = <m'| a_l |Psi> = sqrt(m'_l + 1) C[m' + e_l] over the
+// (N-1)-particle configurations and X_{qs}[n'] = <n'| a_q a_s |Psi> =
+// sqrt(n'_q + 1) sqrt(n'_s + 1 + delta_qs) C[n' + e_q + e_s] over the
+// (N-2)-particle configurations (a_q a_s = a_s a_q, so one vector per unordered
+// pair).  Both are Hermitian Gram matrices of small vectors over a large
+// space: one thread builds the vector of one configuration in a shared tile,
+// the block accumulates the upper triangle over the tile's 128 columns in
+// FP32 pairs, the per-tile sums are added in FP64, and the per-block partials
+// are summed in a fixed order (deterministic).  This replaces the paper's
+// element-by-element sums over beta with a reduction that reads each C
+// gather once per configuration of the smaller space.
+#include <math.h>
+
+#include <vector>
+
+#include "fock_apply_twophase.cuh"
+
+namespace {
+
+constexpr int kGramCols = 128;
+
+template <int M, bool TWO>
+struct GramShape {
+  static constexpr int K = TWO ? M * (M + 1) / 2 : M;     // vectors per configuration
+  static constexpr int E = K * (K + 1) / 2;               // upper-triangle entries
+};
+
+struct GramArgs {
+  int N, M, xdim, nsq;
+  uint32_t nc, ncol;                // N-space size; columns (configurations of the smaller space)
+  const uint32_t *mod, *sat;        // binomial tables of the N-space (wrapping and saturated)
+  const float4 *C;                  // FP32-pair split of C (re_hi, im_hi, re_lo, im_lo), scaled
+  double2 *partial;                 // [gridDim.x][E]
+};
+
+// sqrt(i) as an FP32 pair: the correctly rounded root and the residual
+// (i - hi^2, exact by FMA) divided by 2 hi.
+__device__ __forceinline__ float2 gram_sqrt_pair(int i) {
+  const float x = (float)i;
+  const float hi = __fsqrt_rn(x);
+  const float lo = hi > 0.f ? __fdiv_rn(__fmaf_rn(-hi, hi, x), 2.f * hi) : 0.f;
+  return make_float2(hi, lo);
+}
+
+// (re, im) of conj(a) b accumulated into the packed pair (h, l), a and b as
+// float4 (re_hi, im_hi, re_lo, im_lo):
+//   Re = ar br + ai bi,  Im = ar bi - ai br.
+__device__ __forceinline__ void gram_mac(fp2_t &h, fp2_t &l, float4 a, float4 b) {
+  fp2_t p, e;
+  fp2_dprod(fp2_make(a.x, a.x), fp2_make(a.z, a.z), fp2_make(b.x, b.y), fp2_make(b.z, b.w), p, e);
+  fp2_dacc(h, l, p, e);
+  fp2_dprod(fp2_make(a.y, a.y), fp2_make(a.w, a.w), fp2_make(b.y, -b.x), fp2_make(b.w, -b.z), p, e);
+  fp2_dacc(h, l, p, e);
+}
+
+template <int M, bool TWO>
+__global__ void __launch_bounds__(kGramCols) fock_gram_kernel(const GramArgs g) {
+  constexpr int K = GramShape<M, TWO>::K, E = GramShape<M, TWO>::E;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int rows = M > 1 ? M - 1 : 1;
+  float4 *Xt = (float4 *)smem;                                        // [kGramCols][K]
+  double2 *acc = (double2 *)(Xt + kGramCols * K);                     // [E]
+  uint32_t *s_mod = (uint32_t *)(acc + E);
+  uint32_t *s_sat = s_mod + rows * g.xdim;
+  float2 *s_sq = (float2 *)(s_sat + rows * g.xdim + 2);
+  uint8_t *emap = (uint8_t *)(s_sq + g.nsq);                          // [E][2]
+  const int tid = threadIdx.x;
+  for (int i = tid; i < rows * g.xdim; i += kGramCols) {
+    s_mod[i] = g.mod[i];
+    s_sat[i] = g.sat[i];
+  }
+  for (int i = tid; i < g.nsq; i += kGramCols) s_sq[i] = gram_sqrt_pair(i);
+  for (int e = tid; e < E; e += kGramCols) {
+    int a = 0, r = e;                                                 // row-major upper triangle
+    while (r >= K - a) {
+      r -= K - a;
+      ++a;
+    }
+    emap[2 * e] = (uint8_t)a;
+    emap[2 * e + 1] = (uint8_t)(a + r);
+    acc[e] = make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+
+  for (uint32_t tile = blockIdx.x * (uint32_t)kGramCols; tile < g.ncol; tile += gridDim.x * (uint32_t)kGramCols) {
+    // ---- this thread's column vector into the tile ----
+    const uint32_t col = tile + tid;
+    float4 *xrow = Xt + tid * K;
+    if (col < g.ncol) {
+      int S[M];
+      if (TWO) {
+        fock_decode_fast<M>(col, g.N - 2, g.ncol, s_sat, g.xdim, S);
+        uint32_t U[M], V[M];
+        const uint32_t base = twophase_targets<M>(S, s_mod, g.xdim, g.nc, U, V);
+        float2 sq1[M], sq2[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const int occ = S[m] - (m > 0 ? S[m - 1] : 0);
+          sq1[m] = s_sq[occ + 1];
+          sq2[m] = s_sq[occ + 2];
+        }
+        int a = 0;
+#pragma unroll
+        for (int s = 0; s < M; ++s)
+#pragma unroll
+          for (int l = s; l < M; ++l, ++a) {
+            const float4 v = __ldg(g.C + (base - U[s] - V[l]));
+            const float2 amp = df_mul(sq1[s], s == l ? sq2[s] : sq1[l]);
+            fp2_t Xh, Xl;
+            fp2_dprod(fp2_make(v.x, v.y), fp2_make(v.z, v.w), fp2_make(amp.x, amp.x), fp2_make(amp.y, amp.y),
+                      Xh, Xl);
+            xrow[a] = make_float4(fp2_x(Xh), fp2_y(Xh), fp2_x(Xl), fp2_y(Xl));
+          }
+      } else {
+        fock_decode_fast<M>(col, g.N - 1, g.ncol, s_sat, g.xdim, S);
+        // rank(m' + e_l) = (nc - 1 - F1[M-1]) - (F0[l] - F1[l]) with F_d[j] the
+        // prefix sums of C(S_m + m + d, m + 1) over m < j
+        uint32_t F0 = 0, F1 = 0, D[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          D[m] = F0 - F1;
+          if (m < M - 1) {
+            const uint32_t *row = s_mod + m * g.xdim + (S[m] + m);
+            F0 += row[0];
+            F1 += row[1];
+          }
+        }
+        const uint32_t base = g.nc - 1u - F1;
+#pragma unroll
+        for (int l = 0; l < M; ++l) {
+          const float4 v = __ldg(g.C + (base - D[l]));
+          const int occ = S[l] - (l > 0 ? S[l - 1] : 0);
+          const float2 amp = s_sq[occ + 1];
+          fp2_t Xh, Xl;
+          fp2_dprod(fp2_make(v.x, v.y), fp2_make(v.z, v.w), fp2_make(amp.x, amp.x), fp2_make(amp.y, amp.y), Xh,
+                    Xl);
+          xrow[l] = make_float4(fp2_x(Xh), fp2_y(Xh), fp2_x(Xl), fp2_y(Xl));
+        }
+      }
+    } else {
+      for (int a = 0; a < K; ++a) xrow[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    // ---- Gram entries of the tile ----
+    for (int e = tid; e < E; e += kGramCols) {
+      const int a = emap[2 * e], b = emap[2 * e + 1];
+      fp2_t h = 0ull, l = 0ull;
+#pragma unroll 4
+      for (int c = 0; c < kGramCols; ++c) gram_mac(h, l, Xt[c * K + a], Xt[c * K + b]);
+      double2 s = acc[e];
+      s.x += (double)fp2_x(h) + (double)fp2_x(l);
+      s.y += (double)fp2_y(h) + (double)fp2_y(l);
+      acc[e] = s;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < E; e += kGramCols) g.partial[(size_t)blockIdx.x * E + e] = acc[e];
+}
+
+// out[e] = sum over blocks of partial[b][e], in block order.
+__global__ void fock_gram_reduce(const double2 *__restrict__ partial, int blocks, int E, double2 *__restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  double2 s = make_double2(0.0, 0.0);
+  for (int b = 0; b < blocks; ++b) {
+    const double2 v = partial[(size_t)b * E + e];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  out[e] = s;
+}
+
+template <int M, bool TWO>
+size_t gram_smem(int xdim, int nsq) {
+  constexpr int K = GramShape<M, TWO>::K, E = GramShape<M, TWO>::E;
+  const int rows = M > 1 ? M - 1 : 1;
+  return (size_t)kGramCols * K * 16 + (size_t)E * 16 + 8 * (size_t)rows * xdim + 8 + 8 * (size_t)nsq + 2 * (size_t)E;
+}
+
+// Runs one Gram reduction; G receives the upper triangle (E entries).
+template <int M, bool TWO>
+int gram_run(const GramArgs &g0, int device, cudaStream_t s, std::vector<double> &G) {
+  constexpr int E = GramShape<M, TWO>::E;
+  GramArgs g = g0;
+  const size_t smem = gram_smem<M, TWO>(g.xdim, g.nsq);
+  auto kern = fock_gram_kernel<M, TWO>;
+  if (smem > 48 * 1024) FOCK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  FOCK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGramCols, smem));
+  if (per_sm < 1) return FOCK_ERR_UNSUPPORTED;
+  int64_t tiles = ((int64_t)g.ncol + kGramCols - 1) / kGramCols;
+  int64_t grid = (int64_t)per_sm * fock_get_sm_count(device);
+  if (grid > tiles) grid = tiles;
+  if (grid < 1) grid = 1;
+  double2 *buf = nullptr;
+  FOCK_CUDA_TRY(cudaMalloc(&buf, sizeof(double2) * (size_t)E * (grid + 1)));
+  g.partial = buf;
+  kern<<<(unsigned)grid, kGramCols, smem, s>>>(g);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    fock_gram_reduce<<<(E + 127) / 128, 128, 0, s>>>(buf, (int)grid, E, buf + (size_t)E * grid);
+    e = cudaGetLastError();
+  }
+  G.assign(2 * (size_t)E, 0.0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(G.data(), buf + (size_t)E * grid, sizeof(double2) * E, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(buf);
+  return e == cudaSuccess ? FOCK_OK : fock_cuda_status(e);
+}
+
+template <bool TWO>
+int gram_dispatch(int M, const GramArgs &g, int device, cudaStream_t s, std::vector<double> &G) {
+  switch (M) {
+#define FOCK_GRAM_CASE(MM) \
+    case MM: return gram_run<MM, TWO>(g, device, s, G);
+    FOCK_GRAM_CASE(1)
+    FOCK_GRAM_CASE(2)
+    FOCK_GRAM_CASE(3)
+    FOCK_GRAM_CASE(4)
+    FOCK_GRAM_CASE(5)
+    FOCK_GRAM_CASE(6)
+    FOCK_GRAM_CASE(7)
+    FOCK_GRAM_CASE(8)
+    FOCK_GRAM_CASE(9)
+    FOCK_GRAM_CASE(10)
+    FOCK_GRAM_CASE(11)
+    FOCK_GRAM_CASE(12)
+#undef FOCK_GRAM_CASE
+  }
+  return FOCK_ERR_UNSUPPORTED;
+}
+
+int64_t nc_of(int n, int m) {
+  if (n < 0 || m < 1) return 0;
+  // C(n + m - 1, m - 1) by the multiplicative formula (fits: the caller's
+  // space is 32-bit)
+  uint64_t r = 1;
+  for (int i = 1; i <= m - 1; ++i) r = r * (uint64_t)(n + i) / (uint64_t)i;
+  return (int64_t)r;
+}
+
+}  // namespace
+
+int fock_prepare_df(const void *C, int64_t n, void *ws, int device, cudaStream_t stream);
+
+extern "C" int fock_density_matrices(const fock_space *sp, const void *C_dev, double *rho1_host, double *rho2_host,
+                                     void *stream) {
+  if (!sp || !C_dev || (!rho1_host && !rho2_host)) return FOCK_ERR_ARG;
+  if (!sp->idx32 || sp->M > 12) return FOCK_ERR_UNSUPPORTED;
+  int dev = -1;
+  FOCK_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != sp->device) return FOCK_ERR_DEVICE;
+  const int N = sp->N, M = sp->M;
+  cudaStream_t s = (cudaStream_t)stream;
+  // FP32-pair split of C, scaled by a power of two (the apply's preparation)
+  void *ws = nullptr;
+  FOCK_CUDA_TRY(cudaMalloc(&ws, 256 + 16 * (size_t)sp->nc));
+  int st = fock_prepare_df(C_dev, sp->nc, ws, sp->device, s);
+  int words[2] = {0, 0};
+  if (!st) {
+    cudaError_t e = cudaMemcpyAsync(words, ws, sizeof(words), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = fock_cuda_status(e);
+  }
+  GramArgs g;
+  g.N = N;
+  g.M = M;
+  g.xdim = sp->tab.xdim;
+  g.nsq = N + 4;
+  g.nc = (uint32_t)sp->nc;
+  g.mod = sp->tab.mod32;
+  g.sat = sp->tab.sat32;
+  g.C = (const float4 *)((const char *)ws + 256);
+  g.partial = nullptr;
+  const double scale2 = ldexp(1.0, 2 * words[1]);       // |C|^2 units of the split
+  auto pair_index = [M](int k, int l) {                  // unordered pair {k, l} in the kernel's order
+    const int s = k < l ? k : l, t = k < l ? l : k;
+    return s * M - s * (s - 1) / 2 + (t - s);
+  };
+  if (!st && rho1_host) {
+    g.ncol = (uint32_t)nc_of(N - 1, M);
+    std::vector<double> G;
+    st = gram_dispatch<false>(M, g, sp->device, s, G);
+    if (!st) {
+      int e = 0;
+      for (int a = 0; a < M; ++a)
+        for (int b = a; b < M; ++b, ++e) {
+          const double re = G[2 * e] * scale2, im = G[2 * e + 1] * scale2;
+          rho1_host[2 * (a * M + b)] = re;
+          rho1_host[2 * (a * M + b) + 1] = im;
+          rho1_host[2 * (b * M + a)] = re;
+          rho1_host[2 * (b * M + a) + 1] = -im;
+        }
+    }
+  }
+  if (!st && rho2_host) {
+    const size_t m4 = (size_t)M * M * M * M;
+    if (N < 2) {
+      for (size_t i = 0; i < 2 * m4; ++i) rho2_host[i] = 0.0;
+    } else {
+      g.ncol = (uint32_t)nc_of(N - 2, M);
+      std::vector<double> G;
+      st = gram_dispatch<true>(M, g, sp->device, s, G);
+      if (!st) {
+        const int P = M * (M + 1) / 2;
+        std::vector<double> full(2 * (size_t)P * P);
+        int e = 0;
+        for (int a = 0; a < P; ++a)
+          for (int b = a; b < P; ++b, ++e) {
+            full[2 * ((size_t)a * P + b)] = G[2 * e] * scale2;
+            full[2 * ((size_t)a * P + b) + 1] = G[2 * e + 1] * scale2;
+            full[2 * ((size_t)b * P + a)] = G[2 * e] * scale2;
+            full[2 * ((size_t)b * P + a) + 1] = -G[2 * e + 1] * scale2;
+          }
+        for (int k = 0; k < M; ++k)
+          for (int l = 0; l < M; ++l)
+            for (int q = 0; q < M; ++q)
+              for (int r = 0; r < M; ++r) {
+                const size_t o = ((((size_t)k * M + l) * M + q) * M + r);
+                const size_t src = (size_t)pair_index(k, l) * P + pair_index(q, r);
+                rho2_host[2 * o] = full[2 * src];
+                rho2_host[2 * o + 1] = full[2 * src + 1];
+              }
+      }
+    }
+  }
+  cudaFree(ws);
+  return st;
+}

@@ -50,7 +50,7 @@ EXPORTS = (
     "fock_hamiltonian_create", "fock_hamiltonian_destroy", "fock_hamiltonian_terms",
     "fock_hamiltonian_is_real",
     "fock_apply_set_events", "fock_apply_workspace_size", "fock_apply_H", "fock_apply_H_host", "fock_apply_H_noalloc",
-    "fock_lanczos_ground",
+    "fock_lanczos_ground", "fock_density_matrices",
     "fock_batch_create", "fock_batch_destroy", "fock_batch_offsets", "fock_batch_terms", "fock_batch_apply",
     "fock_batch_autotune", "fock_batch_lanczos_ground",
 )
@@ -103,6 +103,7 @@ def load(path: str | None = None):
         "fock_apply_H_noalloc": [vp, vp, vp, vp, i32, ctypes.c_int, vp],
         "fock_lanczos_ground": [vp, vp, i32, i32, dbl, ctypes.c_uint64, ctypes.c_int, vp,
                                 P(dbl), P(dbl), vp, P(i32), vp],
+        "fock_density_matrices": [vp, vp, vp, vp, vp],
     }
     sigs.update({
         "fock_batch_create": [i32, vp, vp, vp, vp, dbl, P(vp)],
@@ -321,6 +322,19 @@ def fock_lanczos_ground(sp, ham, max_iter: int = 300, restart_len: int = 30, tol
                                     _stream(stream))
     _check(st, "fock_lanczos_ground", allow=(FOCK_ERR_NOCONV,))
     return E0.value, res.value, it.value, vec, st
+
+
+def fock_density_matrices(sp, C, M: int, want_rho2: bool = True, stream=None):
+    """(rho1 [M, M], rho2 [M, M, M, M] or None) of the complex128 CUDA vector C
+    as numpy complex128 arrays: rho1[k, l] = <C|a^dag_k a_l|C>,
+    rho2[k, l, q, s] = <C|a^dag_k a^dag_l a_q a_s|C>."""
+    import numpy as np
+    r1 = np.zeros((M, M), dtype=np.complex128)
+    r2 = np.zeros((M, M, M, M), dtype=np.complex128) if want_rho2 else None
+    _check(load().fock_density_matrices(sp, _dptr(C), r1.ctypes.data,
+                                        None if r2 is None else r2.ctypes.data, _stream(stream)),
+           "fock_density_matrices")
+    return r1, r2
 
 
 # --------------------------------------------------------------------------
