@@ -535,6 +535,24 @@ def main():
             extras[name] = {"ms_per_step": t, "config_terms_per_s": terms / (t * 1e-3)}
             del X, Y
         out["other_precisions"] = extras
+        if w.nrhs == 1 and w.M <= 12:
+            # one- and two-body density matrices of the same state (Eqs. rho1, rho2)
+            X = torch.from_numpy(Cn).cuda()
+            fock.fock_density_matrices(sp.handle, X, w.M)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            reps = 3
+            for _ in range(reps):
+                fock.fock_density_matrices(sp.handle, X, w.M)
+            t = (time.perf_counter() - t0) / reps * 1e3
+            P = w.M * (w.M + 1) // 2
+            out["density_matrices"] = {
+                "ms_per_call": t, "rho1_columns": math.comb(w.N - 1 + w.M - 1, w.M - 1),
+                "rho2_columns": math.comb(w.N - 2 + w.M - 1, w.M - 1) if w.N >= 2 else 0,
+                "rho2_gram_entries": P * (P + 1) // 2,
+                "note": "host-synchronous call incl. its workspace allocation and the input split; "
+                        "Gram matrices over the (N-1)- and (N-2)-particle spaces"}
+            del X
         n, dt = oracle_rate(w, h, W, Cn if w.nrhs == 1 else Cn[:, 0].copy(), args.cpu_seconds)
         per_cfg = H.terms / w.nc
         out["cpu_baseline"] = {"value": per_cfg * n / dt, "unit": "config-terms/s", "cores": 1,
