@@ -17,6 +17,8 @@ Contents (Andriati & Gammal, arXiv:2005.13679):
 * ``rho1``, ``rho2`` -- the one- and two-body density matrices of Eqs. rho1
   and rho2, each element by its definition <C| O C> with O the unit one- or
   two-body operator applied by ``apply_push``;
+* ``evolve`` -- exp(-i H dt) C through the eigen-decomposition of the dense H
+  (the exact propagator that a short-iterative-Lanczos step approximates);
 * ``lanczos_ground`` -- Lanczos with complete re-orthogonalisation and a
   tridiagonal eigen-solve, as in Sec. 5;
 * ``bethe_ground_energy`` -- the Lieb-Liniger ground state from the Bethe
@@ -229,6 +231,19 @@ def rho2(N: int, M: int, C) -> np.ndarray:
                     W[k, l, q, s] = 2.0
                     out[k, l, q, s] = np.vdot(CC, apply_push(N, M, zero_h, W, CC))
     return out
+
+
+# --------------------------------------------------------------------------
+# Time evolution (the propagator of the SIL integrator named in Sec. 1)
+# --------------------------------------------------------------------------
+def evolve(N: int, M: int, h, W, C, dt: float) -> np.ndarray:
+    """exp(-i H dt) C for a tiny space: H = U diag(E) U^H from the dense
+    Hamiltonian (numpy's Hermitian eigen-solver as a step), then
+    U diag(exp(-i E dt)) U^H C."""
+    H = dense_hamiltonian(N, M, h, W)
+    E, U = np.linalg.eigh(H)
+    CC = _cplx(C, (nc(N, M),))
+    return U @ (np.exp(-1j * E * dt) * (U.conj().T @ CC))
 
 
 # --------------------------------------------------------------------------
