@@ -259,6 +259,22 @@ int fock_lanczos_ground(const fock_space *sp, const fock_ham *ham, int32_t max_i
                         const void *start_dev, double *E0, double *residual,
                         void *vec_dev, int32_t *iters, void *stream);
 
+/* Short-iterative-Lanczos time step C <- exp(-i H dt) C (the SIL integrator
+ * the paper names as a consumer of H C, Sec. 1).  C_dev: N_c complex128 on
+ * the space's device, overwritten.  The Krylov space of C (Lanczos vectors
+ * orthogonalised twice against all previous ones) grows until the weight of
+ * the next vector in exp(-i T dt) e_0 is below tol (relative to ||C||), the
+ * space is invariant, or max_krylov (1..128) vectors are used; T is the
+ * tridiagonal projection of H, exponentiated by its eigen-decomposition on
+ * the host.  Products use `precision` (FOCK_PREC_F64, _F64_NATIVE or
+ * _F32_MIXED).  *krylov_used and *err_est (may be NULL) receive the Krylov
+ * dimension and the final weight.  Allocates max_krylov + 1 vectors and the
+ * apply workspace.  Synchronous.  Returns FOCK_ERR_NOCONV (C still updated
+ * with the best estimate) when max_krylov vectors were not enough. */
+int fock_sil_step(const fock_space *sp, const fock_ham *ham, void *C_dev, double dt,
+                  int32_t max_krylov, double tol, int precision, int32_t *krylov_used,
+                  double *err_est, void *stream);
+
 /* ------------------------------------------------------------------------- */
 /* Density matrices                                                          */
 /* ------------------------------------------------------------------------- */

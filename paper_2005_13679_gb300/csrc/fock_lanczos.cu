@@ -435,3 +435,129 @@ extern "C" int fock_lanczos_ground(const fock_space *sp, const fock_ham *ham, in
 #undef TRY
   return converged ? FOCK_OK : FOCK_ERR_NOCONV;
 }
+
+// ---------------------------------------------------------------------------
+// Short-iterative-Lanczos time step (the consumer of H C named in Sec. 1):
+// C <- exp(-i H dt) C by the Krylov space of C.  With v_0 = C / ||C|| and the
+// Lanczos vectors v_0 .. v_{m-1} (every new vector orthogonalised twice
+// against all previous ones), T = V^H H V is tridiagonal and
+//     exp(-i H dt) C ~ ||C|| V exp(-i T dt) e_0.
+// exp(-i T dt) e_0 comes from the Jacobi eigen-decomposition of T.  The
+// Krylov space grows until the weight of the next vector, beta_{m-1} times
+// the last component of exp(-i T dt) e_0, falls below tol (relative to
+// ||C||), the space is invariant, or max_krylov vectors are used.
+// ---------------------------------------------------------------------------
+extern "C" int fock_sil_step(const fock_space *sp, const fock_ham *ham, void *C_dev, double dt,
+                             int32_t max_krylov, double tol, int precision, int32_t *krylov_used,
+                             double *err_est, void *stream) {
+  if (!sp || !ham || !C_dev || max_krylov < 1 || max_krylov > 128 || !(tol > 0.0) || !isfinite(dt))
+    return FOCK_ERR_ARG;
+  if (precision < FOCK_PREC_F64 || precision > FOCK_PREC_F32_MIXED) return FOCK_ERR_ARG;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return FOCK_ERR_CUDA;
+  if (cur != sp->device) return FOCK_ERR_DEVICE;
+  Ctx c;
+  c.n = sp->nc;
+  c.real = false;                 // exp(-i H dt) makes any vector complex
+  c.sms = fock_get_sm_count(sp->device);
+  c.s = (cudaStream_t)stream;
+  c.partial_h.resize((size_t)kDotBlocks * kChunk);
+  const int64_t n = c.n;
+  int K = max_krylov;
+  if ((int64_t)K > n) K = (int)n;
+
+  double2 *V = nullptr, *w = nullptr;
+  float2 *c64a = nullptr, *c64b = nullptr;
+  void *ws = nullptr;
+  const size_t ws_bytes = fock_apply_ws_pref(sp, ham, 1, precision);
+  int st = FOCK_OK;
+  auto cleanup = [&]() {
+    cudaFree(V);
+    cudaFree(w);
+    cudaFree(c64a);
+    cudaFree(c64b);
+    cudaFree(ws);
+    cudaFree(c.partial_d);
+  };
+#define TRY(x)                  \
+  do {                          \
+    st = (x);                   \
+    if (st) { cleanup(); return st; } \
+  } while (0)
+  TRY(cudaMalloc(&V, sizeof(double2) * (size_t)n * K) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
+  TRY(cudaMalloc(&w, sizeof(double2) * (size_t)n) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
+  TRY(cudaMalloc(&c.partial_d, sizeof(double2) * kDotBlocks * kChunk) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
+  if (ws_bytes) TRY(cudaMalloc(&ws, ws_bytes) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
+  if (precision == FOCK_PREC_F32_MIXED) {
+    TRY(cudaMalloc(&c64a, sizeof(float2) * (size_t)n) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
+    TRY(cudaMalloc(&c64b, sizeof(float2) * (size_t)n) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
+  }
+  auto apply = [&](const double2 *x, double2 *y) -> int {
+    if (precision == FOCK_PREC_F32_MIXED) {
+      to_c64_kernel<<<c.grid(), 256, 0, c.s>>>(x, n, c64a);
+      int r = fock_apply_internal(sp, ham, c64a, c64b, 1, precision, FOCK_ARM_HASH, ws, ws_bytes, c.s);
+      if (r) return r;
+      to_c128_kernel<<<c.grid(), 256, 0, c.s>>>(c64b, n, y);
+      return cudaGetLastError() == cudaSuccess ? FOCK_OK : FOCK_ERR_CUDA;
+    }
+    return fock_apply_internal(sp, ham, x, y, 1, precision, FOCK_ARM_HASH, ws, ws_bytes, c.s);
+  };
+
+  const double beta0 = norm(c, (const double2 *)C_dev, &st);
+  if (st) { cleanup(); return st; }
+  if (krylov_used) *krylov_used = 0;
+  if (err_est) *err_est = 0.0;
+  if (beta0 == 0.0) {
+    cleanup();
+    return FOCK_OK;
+  }
+  scale_copy_kernel<<<c.grid(), 256, 0, c.s>>>((const double2 *)C_dev, 1.0 / beta0, n, V);
+  TRY(cudaGetLastError() == cudaSuccess ? FOCK_OK : FOCK_ERR_CUDA);
+  std::vector<double> alpha, beta;
+  std::vector<double> cre, cim;                       // exp(-i T dt) e_0
+  std::vector<double2> h, h2;
+  double err = 0.0;
+  int m = 0;
+  for (int j = 0; j < K; ++j) {
+    double2 *vj = V + (size_t)j * n;
+    TRY(apply(vj, w));
+    TRY(dots(c, V, n, j + 1, w, h));
+    TRY(combine(c, V, n, j + 1, h, 1.0, w));
+    TRY(dots(c, V, n, j + 1, w, h2));                  // second Gram-Schmidt pass
+    TRY(combine(c, V, n, j + 1, h2, 1.0, w));
+    alpha.push_back(h[j].x + h2[j].x);
+    const double b = norm(c, w, &st);
+    if (st) { cleanup(); return st; }
+    m = j + 1;
+    // exp(-i T dt) e_0 for the current m x m tridiagonal T
+    std::vector<double> T((size_t)m * m, 0.0), evals, evecs;
+    for (int i = 0; i < m; ++i) T[(size_t)i * m + i] = alpha[i];
+    for (int i = 0; i + 1 < m; ++i) T[(size_t)i * m + i + 1] = T[(size_t)(i + 1) * m + i] = beta[i];
+    jacobi_eigen(T, m, evals, evecs);
+    cre.assign(m, 0.0);
+    cim.assign(m, 0.0);
+    for (int i = 0; i < m; ++i) {
+      const double ph = -evals[i] * dt, w0 = evecs[(size_t)i * m + 0];
+      for (int k = 0; k < m; ++k) {
+        const double q = evecs[(size_t)i * m + k] * w0;
+        cre[k] += q * cos(ph);
+        cim[k] += q * sin(ph);
+      }
+    }
+    err = b * hypot(cre[m - 1], cim[m - 1]);
+    if (err < tol || b <= 1e-14 * fabs(alpha[0]) || b == 0.0 || m == K) break;
+    beta.push_back(b);
+    scale_copy_kernel<<<c.grid(), 256, 0, c.s>>>(w, 1.0 / b, n, V + (size_t)(j + 1) * n);
+    TRY(cudaGetLastError() == cudaSuccess ? FOCK_OK : FOCK_ERR_CUDA);
+  }
+  // C = beta0 sum_k c_k v_k  (combine computes w = 0 w - sum h_k v_k)
+  std::vector<double2> coef(m);
+  for (int k = 0; k < m; ++k) coef[k] = make_double2(-beta0 * cre[k], -beta0 * cim[k]);
+  TRY(combine(c, V, n, m, coef, 0.0, (double2 *)C_dev));
+  TRY(cudaStreamSynchronize(c.s) == cudaSuccess ? FOCK_OK : FOCK_ERR_CUDA);
+  if (krylov_used) *krylov_used = m;
+  if (err_est) *err_est = err;
+  cleanup();
+#undef TRY
+  return err < tol ? FOCK_OK : FOCK_ERR_NOCONV;
+}

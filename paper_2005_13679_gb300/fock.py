@@ -50,7 +50,7 @@ EXPORTS = (
     "fock_hamiltonian_create", "fock_hamiltonian_destroy", "fock_hamiltonian_terms",
     "fock_hamiltonian_is_real",
     "fock_apply_set_events", "fock_apply_workspace_size", "fock_apply_H", "fock_apply_H_host", "fock_apply_H_noalloc",
-    "fock_lanczos_ground", "fock_density_matrices",
+    "fock_lanczos_ground", "fock_sil_step", "fock_density_matrices",
     "fock_batch_create", "fock_batch_destroy", "fock_batch_offsets", "fock_batch_terms", "fock_batch_apply",
     "fock_batch_autotune", "fock_batch_lanczos_ground",
 )
@@ -104,6 +104,7 @@ def load(path: str | None = None):
         "fock_lanczos_ground": [vp, vp, i32, i32, dbl, ctypes.c_uint64, ctypes.c_int, vp,
                                 P(dbl), P(dbl), vp, P(i32), vp],
         "fock_density_matrices": [vp, vp, vp, vp, vp],
+        "fock_sil_step": [vp, vp, vp, dbl, i32, dbl, ctypes.c_int, P(i32), P(dbl), vp],
     }
     sigs.update({
         "fock_batch_create": [i32, vp, vp, vp, vp, dbl, P(vp)],
@@ -322,6 +323,17 @@ def fock_lanczos_ground(sp, ham, max_iter: int = 300, restart_len: int = 30, tol
                                     _stream(stream))
     _check(st, "fock_lanczos_ground", allow=(FOCK_ERR_NOCONV,))
     return E0.value, res.value, it.value, vec, st
+
+
+def fock_sil_step(sp, ham, C, dt: float, max_krylov: int = 30, tol: float = 1e-12,
+                  precision: int = FOCK_PREC_F64, stream=None):
+    """C <- exp(-i H dt) C in place (complex128 CUDA vector); returns
+    (krylov dimension, error estimate, status)."""
+    m, err = ctypes.c_int32(), ctypes.c_double()
+    st = load().fock_sil_step(sp, ham, _dptr(C), float(dt), int(max_krylov), float(tol), int(precision),
+                              ctypes.byref(m), ctypes.byref(err), _stream(stream))
+    _check(st, "fock_sil_step", allow=(FOCK_ERR_NOCONV,))
+    return m.value, err.value, st
 
 
 def fock_density_matrices(sp, C, M: int, want_rho2: bool = True, stream=None):
