@@ -59,6 +59,22 @@ def lieb_liniger_hw(M: int, g: float, L: float = 1.0):
     return h, W
 
 
+def bose_hubbard_hw(M: int, J: float = 1.0, U: float = 1.0, mu: float = 0.0, periodic: bool = True):
+    """Bose-Hubbard chain of M sites: hopping -J between neighbouring sites
+    (a ring when periodic), on-site energy -mu, and on-site repulsion U as the
+    two-body coefficient W[k, k, k, k] = U (multiplying 1/2 a^dag_k a^dag_k a_k a_k)."""
+    h = np.zeros((M, M), dtype=np.complex128)
+    for k in range(M):
+        h[k, k] = -mu
+        for l in ((k + 1) % M if periodic else k + 1,):
+            if l < M and l != k:
+                h[k, l] += -J
+                h[l, k] += -J
+    W = np.zeros((M, M, M, M), dtype=np.complex128)
+    W[np.arange(M), np.arange(M), np.arange(M), np.arange(M)] = U
+    return h, W
+
+
 def random_hermitian_hw(M: int, seed: int, sigma_h: float = 1.0, sigma_w: float = 0.1):
     """Random Hermitian h and boson-symmetric Hermitian W (see module notes)."""
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -121,7 +137,7 @@ class Workload:
     name: str
     N: int
     M: int
-    kind: str                 # "ll" or "generic"
+    kind: str                 # "ll", "generic" or "bh"
     seed: int
     g: float = 1.0
     L: float = 1.0
@@ -136,6 +152,8 @@ class Workload:
     def hamiltonian(self):
         if self.kind == "ll":
             return lieb_liniger_hw(self.M, self.g, self.L)
+        if self.kind == "bh":
+            return bose_hubbard_hw(self.M, 1.0, self.g)
         return random_hermitian_hw(self.M, self.seed)
 
     def state(self) -> np.ndarray:
@@ -161,6 +179,8 @@ WORKLOADS = {
     # Profiling size of the Lieb-Liniger M = 10 workload: 20,160,075
     # configurations (complex128 C of 323 MB, larger than L2).
     "ll_n22_m10": Workload("ll_n22_m10", N=22, M=10, kind="ll", g=0.5, seed=3),
+    # Bose-Hubbard ring, 20 bosons on 12 sites, J = 1, U = 4: 84,672,315 configurations.
+    "bh_n20_m12": Workload("bh_n20_m12", N=20, M=12, kind="bh", g=4.0, seed=6),
     # Generic Hermitian h/W, 20 bosons in 8 orbitals, a block of 16 vectors.
     "generic_n20_m8_rhs16": Workload("generic_n20_m8_rhs16", N=20, M=8, kind="generic", seed=4,
                                      nrhs=16, rhs_seeds=list(range(4000, 4016))),

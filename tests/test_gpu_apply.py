@@ -129,6 +129,18 @@ def test_maps_arm_equals_hash_arm(torch, N, M, kind, prec):
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N,M", [(6, 4), (4, 7), (9, 3), (3, 12)])
+def test_bose_hubbard_against_oracle(torch, N, M, prec):
+    h, W = inputs.bose_hubbard_hw(M, J=1.0, U=3.5, mu=0.2)
+    sp = fock.Space(N, M)
+    H = fock.Hamiltonian(sp, h, W)
+    C = inputs.random_state(sp.nc, 23)
+    ref = oracle.apply_push(N, M, h, W, C)
+    out = H.apply(dev_vec(torch, C, prec), precision=prec)
+    assert rel(out.cpu().numpy().astype(np.complex128), ref) <= TOL[prec]
+
+
 def test_alias_and_argument_errors(torch):
     sp = fock.Space(5, 5)
     h, W = hw("ll", 5)
@@ -190,7 +202,7 @@ def sampled_rows(nc, seed, count):
     return np.unique(np.concatenate([edge, rng.integers(0, nc, count)])).astype(np.int64)
 
 
-@pytest.mark.parametrize("name", ["generic_n100_m6", "ll_n30_m10", "ll_n5_m5"])
+@pytest.mark.parametrize("name", ["generic_n100_m6", "ll_n30_m10", "ll_n5_m5", "bh_n20_m12"])
 def test_full_size_sampled_rows(torch, name):
     w = inputs.WORKLOADS[name]
     h, W = w.hamiltonian()

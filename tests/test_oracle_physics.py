@@ -64,3 +64,19 @@ def test_ll_exact_diagonalisation_converges_to_bethe():
     assert energies[-1] > E_bethe
     # Tonks-Girardeau energy bounds every finite-g ground state from above
     assert energies[0] < 0.5 * (2 * np.pi) ** 2 * 10
+
+
+def test_bose_hubbard_limits():
+    """Bose-Hubbard ring (inputs.bose_hubbard_hw) through the oracle: with U = 0
+    the ground energy is N times the lowest ring mode, -2J; with J = 0 the
+    Hamiltonian is diagonal with (U/2) sum_k n_k (n_k - 1)."""
+    N, M = 4, 5
+    h, W = inputs.bose_hubbard_hw(M, J=0.7, U=0.0)
+    E = np.linalg.eigvalsh(oracle.dense_hamiltonian(N, M, h, W))
+    assert abs(E[0] - N * (-2 * 0.7)) < 1e-12
+    h, W = inputs.bose_hubbard_hw(M, J=0.0, U=1.7)
+    H = oracle.dense_hamiltonian(N, M, h, W)
+    assert np.allclose(H, np.diag(np.diag(H)), atol=1e-14)
+    for i in range(oracle.nc(N, M)):
+        n = oracle.unrank(N, M, i)
+        assert abs(H[i, i] - 0.5 * 1.7 * np.sum(n * (n - 1))) < 1e-12
