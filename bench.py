@@ -209,7 +209,16 @@ def path_of(w, prec):
     """Which kernel family serves this workload (mirrors the library's dispatch)."""
     if w.kind == "generic" and 2 <= w.M <= 8 and prec in (0, 2):
         return "twophase_tc" if (w.M <= 6 and tc_fits(w.N, w.M, prec == 2)) else "twophase"
+    if w.kind == "bh" and 2 <= w.M <= 12:
+        return "nn"
     return "direct"
+
+
+def nn_terms(w):
+    """Terms the nearest-neighbour kernel evaluates: per configuration the
+    diagonal and two hops per bond (M bonds on a ring, M = 2 has one)."""
+    nb = w.M if w.M > 2 else 1
+    return w.nc * (1 + 2 * nb)
 
 
 def tc_flops(w, mixed=False):
@@ -489,6 +498,26 @@ def main():
                     "executed_tflops": mma / (kernel_ms * 1e-3) / 1e12, "path": path,
                     "peak_note": "fp16 dense has the nominal bf16 rate on this part: measured bf16 burst "
                                  f"({peak_src}); of measured"}
+    elif path == "nn":
+        # one pass: C read once (neighbour reads hit L2), sigma written once;
+        # the binding roof is the larger of the FP32-pipe and HBM fractions
+        executed = nn_terms(w) * w.nrhs
+        key = (args.precision, "direct")
+        flops_term = FLOPS_PER_TERM_REAL[key] if H.real else FLOPS_PER_TERM[key]
+        alu = executed * flops_term / (kernel_ms * 1e-3) / 1e12
+        gbs = 2 * nbytes / (kernel_ms * 1e-3) / 1e9
+        alu_frac, hbm_frac = alu / FP32_PEAK_TFLOPS, gbs / peaks["hbm_gbs"]
+        if hbm_frac >= alu_frac:
+            roofline = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": hbm_frac, "traffic": traffic}
+        else:
+            roofline = {"bound": "alu", "achieved": alu, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": alu_frac, "traffic": traffic}
+        roofline.update({"kernel": "fock_apply_nn", "kernel_ms": kernel_ms, "executed_terms": executed,
+                         "flops_per_term": flops_term, "alu_frac": alu_frac, "hbm_frac": hbm_frac,
+                         "algorithmic_bytes": 2 * nbytes, "path": path,
+                         "peak_note": f"HBM: measured copy bandwidth ({peak_src}); FP32 pipe: 152 SMs x 128 "
+                                      "lanes x 2 flop x 2070 MHz"})
     else:
         key = (args.precision, "twophase" if path.startswith("twophase") else path)
         flops_term = FLOPS_PER_TERM_REAL[key] if (H.real and key in FLOPS_PER_TERM_REAL) else FLOPS_PER_TERM[key]

@@ -30,6 +30,7 @@ int fock_launch_sparse_df(const SparseArgs &, bool, bool, int, cudaStream_t);
 int fock_launch_sparse_mixed(const SparseArgs &, bool, bool, int, cudaStream_t);
 int fock_launch_twophase(const TwoPhaseArgs &, bool, int, cudaStream_t);
 int fock_launch_twophase_tc(const TwoPhaseArgs &, bool, int, cudaStream_t);
+int fock_launch_nn(const ApplyArgs<uint32_t> &, const void *, const void *, int, int, int, cudaStream_t);
 int fock_tc_image(int M, const std::complex<double> *R, std::vector<unsigned char> &img, std::vector<int> &er);
 int fock_tc_image_mixed(int M, const std::complex<double> *R, std::vector<unsigned char> &img, std::vector<int> &er);
 size_t fock_tc_smem(int M, int xdim, int nsq, bool mixed);
@@ -112,6 +113,10 @@ static void free_ham(fock_ham *h) {
   cudaFree(h->d_tc_er);
   cudaFree(h->d_tc_ma);
   cudaFree(h->d_tc_mer);
+  for (int i = 0; i < 3; ++i) {
+    cudaFree(h->d_nn_bond[i]);
+    cudaFree(h->d_nn_diag[i]);
+  }
   cudaFree(h->d_slots);
   cudaFree(h->ws);
   cudaFree(h->hb_in);
@@ -130,6 +135,89 @@ static int upload(T **dst, const T *src, size_t n) {
   FOCK_CUDA_TRY(cudaMalloc(dst, n * sizeof(T)));
   FOCK_CUDA_TRY(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
   return FOCK_OK;
+}
+
+// Nearest-neighbour structure: 2 <= M <= 12, h_kl = 0 unless l = k or
+// l = k +- 1 (mod M for a ring, M > 2), W_kqsl = 0 unless k = q = s = l, and
+// the diagonal entries real.  Then every configuration has one diagonal term
+// and two hops per bond, evaluated by fock_launch_nn.
+static int build_nn(fock_ham *H, const double *h_host, const double *W_host) {
+  const int M = H->sp->M;
+  H->nn = false;
+  if (M < 2 || M > 12) return FOCK_OK;
+  auto hre = [&](int k, int l) { return h_host[2 * (k * M + l)]; };
+  auto him = [&](int k, int l) { return h_host[2 * (k * M + l) + 1]; };
+  bool ring = false;
+  for (int k = 0; k < M; ++k) {
+    if (him(k, k) != 0.0) return FOCK_OK;
+    for (int l = 0; l < M; ++l) {
+      if (hre(k, l) == 0.0 && him(k, l) == 0.0) continue;
+      const int d = k > l ? k - l : l - k;
+      if (d <= 1) continue;
+      if (d == M - 1) {
+        ring = true;
+        continue;
+      }
+      return FOCK_OK;
+    }
+  }
+  std::vector<double> Wd(M, 0.0);
+  if (W_host) {
+    const size_t n = (size_t)M * M * M * M;
+    for (size_t w = 0; w < n; ++w) {
+      const size_t l = w % M, s = (w / M) % M, q = (w / M / M) % M, k = w / M / M / M;
+      const bool onsite = k == q && q == s && s == l;
+      if (!onsite && (W_host[2 * w] != 0.0 || W_host[2 * w + 1] != 0.0)) return FOCK_OK;
+      if (onsite) {
+        if (W_host[2 * w + 1] != 0.0) return FOCK_OK;
+        Wd[k] = W_host[2 * w];
+      }
+    }
+  }
+  const int nb = ring && M > 2 ? M : M - 1;
+  double amax = 0.0;
+  std::vector<cplx> bond(2 * nb);
+  for (int b = 0; b < nb; ++b) {
+    const int k = b, l = (b + 1) % M;
+    bond[2 * b] = cplx(hre(k, l), him(k, l));
+    bond[2 * b + 1] = cplx(hre(l, k), him(l, k));
+    amax = fmax(amax, fmax(std::abs(bond[2 * b]), std::abs(bond[2 * b + 1])));
+  }
+  std::vector<double> diag(2 * M);
+  for (int k = 0; k < M; ++k) {
+    diag[k] = hre(k, k);
+    diag[M + k] = Wd[k];
+    amax = fmax(amax, fmax(fabs(diag[k]), fabs(diag[M + k])));
+  }
+  H->nn_nb = nb;
+  H->nn_scale = amax > 0.0 ? ldexp(1.0, ilogb(amax) + 1) : 1.0;
+  std::vector<float4> bdf(2 * nb);
+  std::vector<double2> b64(2 * nb);
+  std::vector<float2> b32(2 * nb);
+  for (int i = 0; i < 2 * nb; ++i) {
+    float rh, rl, ih, il;
+    split_float(bond[i].real() / H->nn_scale, rh, rl);
+    split_float(bond[i].imag() / H->nn_scale, ih, il);
+    bdf[i] = make_float4(rh, ih, rl, il);
+    b64[i] = make_double2(bond[i].real(), bond[i].imag());
+    b32[i] = make_float2((float)bond[i].real(), (float)bond[i].imag());
+  }
+  std::vector<float2> ddf(2 * M);
+  std::vector<float> d32(2 * M);
+  for (int i = 0; i < 2 * M; ++i) {
+    float hi, lo;
+    split_float(diag[i] / H->nn_scale, hi, lo);
+    ddf[i] = make_float2(hi, lo);
+    d32[i] = (float)diag[i];
+  }
+  int st = upload((float4 **)&H->d_nn_bond[FOCK_PREC_F64], bdf.data(), bdf.size());
+  if (!st) st = upload((double2 **)&H->d_nn_bond[FOCK_PREC_F64_NATIVE], b64.data(), b64.size());
+  if (!st) st = upload((float2 **)&H->d_nn_bond[FOCK_PREC_F32_MIXED], b32.data(), b32.size());
+  if (!st) st = upload((float2 **)&H->d_nn_diag[FOCK_PREC_F64], ddf.data(), ddf.size());
+  if (!st) st = upload((double **)&H->d_nn_diag[FOCK_PREC_F64_NATIVE], diag.data(), diag.size());
+  if (!st) st = upload((float **)&H->d_nn_diag[FOCK_PREC_F32_MIXED], d32.data(), d32.size());
+  if (!st) H->nn = true;
+  return st;
 }
 
 extern "C" int fock_hamiltonian_create(const fock_space *sp, const double *h_host,
@@ -340,6 +428,7 @@ extern "C" int fock_hamiltonian_create(const fock_space *sp, const double *h_hos
     if (!st) st = upload(&H->d_tc_ma, img.data(), img.size());
     if (!st) st = upload(&H->d_tc_mer, er.data(), er.size());
   }
+  if (!st) st = build_nn(H, h_host, W_host);
   if (!st) st = upload(&H->d_terms, terms.data(), nadd);
   if (!st) st = upload(&H->d_slots, slots.data(), nadd);
   if (!st) st = upload(&H->d_rem, rem.data(), rem.size());
@@ -619,6 +708,12 @@ static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Ci
         return fock_launch_twophase_tc(t, mixed, sp->device, stream);
       }
       return fock_launch_twophase(t, precision == FOCK_PREC_F32_MIXED, sp->device, stream);
+    }
+    // Nearest-neighbour operators: one diagonal term and two hops per bond.
+    if (!maps && ham->nn) {
+      if (precision == FOCK_PREC_F64) a.out_scale = ham->nn_scale;
+      return fock_launch_nn(a, ham->d_nn_bond[precision], ham->d_nn_diag[precision], ham->nn_nb, precision,
+                            sp->device, stream);
     }
     // Every reduced coefficient present and M <= 10: the register-resident
     // kernel with the addition loop unrolled at compile time.

@@ -116,6 +116,13 @@ struct fock_ham {
   int *d_tc_er;             // its row exponents
   unsigned char *d_tc_ma;   // the same for the FP32-mixed form (fp16 hi/lo split of R)
   int *d_tc_mer;
+  // nearest-neighbour operators (h on sites and bonds k, k + 1 mod M, W only
+  // on-site): per-bond and per-site coefficients, indexed by the precision
+  bool nn;
+  int nn_nb;                // bonds: M - 1, or M for a ring
+  double nn_scale;          // FOCK_PREC_F64 arrays stored divided by this power of two
+  void *d_nn_bond[3];       // [2 nb] h_kl, h_lk of bond (k, k + 1 mod M)
+  void *d_nn_diag[3];       // [2 M] h_kk, then W_kkkk (real)
   int32_t *d_slots;         // [nadd] jump-map slot of each term
   // workspace owned by the Hamiltonian (used when the caller passes none)
   void *ws;

@@ -75,6 +75,27 @@ def bose_hubbard_hw(M: int, J: float = 1.0, U: float = 1.0, mu: float = 0.0, per
     return h, W
 
 
+def nearest_neighbour_hw(M: int, seed: int, ring: bool = True, complex_hops: bool = True):
+    """Random operator of the Bose-Hubbard class: site energies h[k, k] and
+    on-site repulsions W[k, k, k, k] drawn uniformly, hops h[k, k + 1] (and
+    h[M - 1, 0] on a ring) of random size and, when complex_hops, random
+    phase; h[l, k] = conj(h[k, l])."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h = np.zeros((M, M), dtype=np.complex128)
+    h[np.arange(M), np.arange(M)] = rng.uniform(-1.0, 1.0, M)
+    nb = M if (ring and M > 2) else M - 1
+    for b in range(nb):
+        k, l = b, (b + 1) % M
+        t = -rng.uniform(0.5, 1.5)
+        if complex_hops:
+            t *= np.exp(1j * rng.uniform(-np.pi, np.pi))
+        h[k, l] += t
+        h[l, k] += np.conj(t)
+    W = np.zeros((M, M, M, M), dtype=np.complex128)
+    W[np.arange(M), np.arange(M), np.arange(M), np.arange(M)] = rng.uniform(0.0, 8.0, M)
+    return h, W
+
+
 def random_hermitian_hw(M: int, seed: int, sigma_h: float = 1.0, sigma_w: float = 0.1):
     """Random Hermitian h and boson-symmetric Hermitian W (see module notes)."""
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -181,6 +202,9 @@ WORKLOADS = {
     "ll_n22_m10": Workload("ll_n22_m10", N=22, M=10, kind="ll", g=0.5, seed=3),
     # Bose-Hubbard ring, 20 bosons on 12 sites, J = 1, U = 4: 84,672,315 configurations.
     "bh_n20_m12": Workload("bh_n20_m12", N=20, M=12, kind="bh", g=4.0, seed=6),
+    # Profiling size of the Bose-Hubbard ring: 16 bosons on 12 sites,
+    # 13,037,895 configurations (complex128 C of 209 MB, larger than L2).
+    "bh_n16_m12": Workload("bh_n16_m12", N=16, M=12, kind="bh", g=4.0, seed=6),
     # Generic Hermitian h/W, 20 bosons in 8 orbitals, a block of 16 vectors.
     "generic_n20_m8_rhs16": Workload("generic_n20_m8_rhs16", N=20, M=8, kind="generic", seed=4,
                                      nrhs=16, rhs_seeds=list(range(4000, 4016))),

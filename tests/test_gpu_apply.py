@@ -124,8 +124,10 @@ def test_maps_arm_equals_hash_arm(torch, N, M, kind, prec):
     ref = oracle.apply_push(N, M, h, W, C.cpu().numpy().astype(np.complex128))
     for out in (a, b):
         assert rel(out.cpu().numpy().astype(np.complex128), ref) <= TOL[prec]
-    if kind != "generic":
+    if kind == "ll":
         # same kernel and same arithmetic order on both arms: bit-identical sums
+        # (the one-body M = 3 case takes the nearest-neighbour kernel on the
+        # hash arm: every pair of three sites neighbours on a ring)
         assert torch.equal(a, b)
 
 
@@ -139,6 +141,56 @@ def test_bose_hubbard_against_oracle(torch, N, M, prec):
     ref = oracle.apply_push(N, M, h, W, C)
     out = H.apply(dev_vec(torch, C, prec), precision=prec)
     assert rel(out.cpu().numpy().astype(np.complex128), ref) <= TOL[prec]
+
+
+# Nearest-neighbour operators take their own kernel (one diagonal term and two
+# hops per bond); chains and rings, real and complex hops, M = 2 (one bond),
+# M = 3 (every pair neighbouring), several tiles with a ragged tail.
+NN_CASES = [
+    (9, 6, True, True),     # 2002 configurations
+    (9, 6, False, False),
+    (10, 8, True, False),   # 19448
+    (5, 2, False, True),
+    (7, 3, True, True),
+    (3, 12, True, True),
+    (1, 5, True, True),
+    (6, 1, False, False),   # one site: no bond, generic path
+]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N,M,ring,cplx", NN_CASES)
+def test_nearest_neighbour_against_oracle(torch, N, M, ring, cplx, prec):
+    h, W = inputs.nearest_neighbour_hw(M, 11 + N + M, ring, cplx)
+    sp = fock.Space(N, M)
+    H = fock.Hamiltonian(sp, h, W)
+    C = inputs.random_state(sp.nc, 29)
+    ref = oracle.apply_push(N, M, h, W, C)
+    out = H.apply(dev_vec(torch, C, prec), precision=prec)
+    assert rel(out.cpu().numpy().astype(np.complex128), ref) <= TOL[prec]
+    # without W: one-body hops and site energies only
+    H1 = fock.Hamiltonian(sp, h, None)
+    ref1 = oracle.apply_push(N, M, h, None, C)
+    out1 = H1.apply(dev_vec(torch, C, prec), precision=prec)
+    assert rel(out1.cpu().numpy().astype(np.complex128), ref1) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_nearest_neighbour_block_and_maps(torch, prec):
+    """Block right-hand sides against single applies, and the hash arm (the
+    nearest-neighbour kernel) against the jump-map arm (the generic kernels)."""
+    N, M, nrhs = 8, 7, 3
+    h, W = inputs.nearest_neighbour_hw(M, 5, True, True)
+    sp = fock.Space(N, M)
+    fock.fock_build_jump_maps(sp.handle, fock.FOCK_MAP_SINGLE | fock.FOCK_MAP_DOUBLE)
+    H = fock.Hamiltonian(sp, h, W)
+    Cb = np.stack([inputs.random_state(sp.nc, 40 + j) for j in range(nrhs)], axis=1)
+    out = H.apply(dev_vec(torch, Cb, prec), nrhs=nrhs, precision=prec).cpu().numpy().astype(np.complex128)
+    for j in range(nrhs):
+        one = H.apply(dev_vec(torch, Cb[:, j], prec), precision=prec).cpu().numpy().astype(np.complex128)
+        assert rel(out[:, j], one) <= TOL[prec]
+        maps = H.apply(dev_vec(torch, Cb[:, j], prec), precision=prec, arm=fock.FOCK_ARM_MAPS)
+        assert rel(one, maps.cpu().numpy().astype(np.complex128)) <= TOL[prec]
 
 
 def test_alias_and_argument_errors(torch):
