@@ -30,7 +30,8 @@ int fock_launch_sparse_df(const SparseArgs &, bool, bool, int, cudaStream_t);
 int fock_launch_sparse_mixed(const SparseArgs &, bool, bool, int, cudaStream_t);
 int fock_launch_twophase(const TwoPhaseArgs &, bool, int, cudaStream_t);
 int fock_launch_twophase_tc(const TwoPhaseArgs &, bool, int, cudaStream_t);
-int fock_launch_nn(const ApplyArgs<uint32_t> &, const void *, const void *, int, int, int, cudaStream_t);
+int fock_launch_nn(const ApplyArgs<uint32_t> &, const void *, const void *, const void *, int, int, int,
+                   cudaStream_t);
 int fock_tc_image(int M, const std::complex<double> *R, std::vector<unsigned char> &img, std::vector<int> &er);
 int fock_tc_image_mixed(int M, const std::complex<double> *R, std::vector<unsigned char> &img, std::vector<int> &er);
 size_t fock_tc_smem(int M, int xdim, int nsq, bool mixed);
@@ -115,7 +116,8 @@ static void free_ham(fock_ham *h) {
   cudaFree(h->d_tc_mer);
   for (int i = 0; i < 3; ++i) {
     cudaFree(h->d_nn_bond[i]);
-    cudaFree(h->d_nn_diag[i]);
+    cudaFree(h->d_nn_e[i]);
+    cudaFree(h->d_nn_t[i]);
   }
   cudaFree(h->d_slots);
   cudaFree(h->ws);
@@ -183,12 +185,25 @@ static int build_nn(fock_ham *H, const double *h_host, const double *W_host) {
     bond[2 * b + 1] = cplx(hre(l, k), him(l, k));
     amax = fmax(amax, fmax(std::abs(bond[2 * b]), std::abs(bond[2 * b + 1])));
   }
-  std::vector<double> diag(2 * M);
-  for (int k = 0; k < M; ++k) {
-    diag[k] = hre(k, k);
-    diag[M + k] = Wd[k];
-    amax = fmax(amax, fmax(fabs(diag[k]), fabs(diag[M + k])));
-  }
+  // site energies E_k(n) for n = 0..N and, for N + 1 <= 32, the hop amplitudes
+  // sqrt(a (b + 1)) for a, b = 0..N (each one correctly rounded square root;
+  // used by the native FP64 form)
+  const int N = H->sp->N, np1 = N + 1;
+  std::vector<double> E((size_t)M * np1);
+  for (int k = 0; k < M; ++k)
+    for (int n = 0; n <= N; ++n) {
+      E[(size_t)k * np1 + n] = hre(k, k) * n + 0.5 * Wd[k] * n * (n - 1.0);
+      amax = fmax(amax, fmax(fabs(hre(k, k)), fabs(Wd[k])));
+    }
+  const bool tt = np1 <= 32;
+  // the kernel stages these tables and the hash tables in shared memory; beyond
+  // about 24 KB per block (8 blocks per SM) the generic kernels serve instead
+  const size_t smem = 32 * (size_t)M + 8 * ((size_t)M * np1 + (tt ? (size_t)np1 * np1 : (size_t)N + 4) + 1) +
+                      8 * (size_t)(M - 1) * (N + M + 5);
+  if (smem > 24 * 1024) return FOCK_OK;
+  std::vector<double> T(tt ? (size_t)np1 * np1 : 0);
+  for (int a = 0; tt && a <= N; ++a)
+    for (int b = 0; b <= N; ++b) T[(size_t)a * np1 + b] = sqrt((double)a * (b + 1));
   H->nn_nb = nb;
   H->nn_scale = amax > 0.0 ? ldexp(1.0, ilogb(amax) + 1) : 1.0;
   std::vector<float4> bdf(2 * nb);
@@ -202,20 +217,31 @@ static int build_nn(fock_ham *H, const double *h_host, const double *W_host) {
     b64[i] = make_double2(bond[i].real(), bond[i].imag());
     b32[i] = make_float2((float)bond[i].real(), (float)bond[i].imag());
   }
-  std::vector<float2> ddf(2 * M);
-  std::vector<float> d32(2 * M);
-  for (int i = 0; i < 2 * M; ++i) {
-    float hi, lo;
-    split_float(diag[i] / H->nn_scale, hi, lo);
-    ddf[i] = make_float2(hi, lo);
-    d32[i] = (float)diag[i];
-  }
+  // FP32-pair and float copies; the energies of the FP32-pair form are scaled
+  // like the coefficients
+  auto pairs = [](const std::vector<double> &v, double sc) {
+    std::vector<float2> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+      float hi, lo;
+      split_float(v[i] / sc, hi, lo);
+      o[i] = make_float2(hi, lo);
+    }
+    return o;
+  };
+  auto floats = [](const std::vector<double> &v) {
+    std::vector<float> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = (float)v[i];
+    return o;
+  };
+  const std::vector<float2> edf = pairs(E, H->nn_scale);
+  const std::vector<float> e32 = floats(E);
   int st = upload((float4 **)&H->d_nn_bond[FOCK_PREC_F64], bdf.data(), bdf.size());
   if (!st) st = upload((double2 **)&H->d_nn_bond[FOCK_PREC_F64_NATIVE], b64.data(), b64.size());
   if (!st) st = upload((float2 **)&H->d_nn_bond[FOCK_PREC_F32_MIXED], b32.data(), b32.size());
-  if (!st) st = upload((float2 **)&H->d_nn_diag[FOCK_PREC_F64], ddf.data(), ddf.size());
-  if (!st) st = upload((double **)&H->d_nn_diag[FOCK_PREC_F64_NATIVE], diag.data(), diag.size());
-  if (!st) st = upload((float **)&H->d_nn_diag[FOCK_PREC_F32_MIXED], d32.data(), d32.size());
+  if (!st) st = upload((float2 **)&H->d_nn_e[FOCK_PREC_F64], edf.data(), edf.size());
+  if (!st) st = upload((double **)&H->d_nn_e[FOCK_PREC_F64_NATIVE], E.data(), E.size());
+  if (!st) st = upload((float **)&H->d_nn_e[FOCK_PREC_F32_MIXED], e32.data(), e32.size());
+  if (!st && tt) st = upload((double **)&H->d_nn_t[FOCK_PREC_F64_NATIVE], T.data(), T.size());
   if (!st) H->nn = true;
   return st;
 }
@@ -712,8 +738,8 @@ static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Ci
     // Nearest-neighbour operators: one diagonal term and two hops per bond.
     if (!maps && ham->nn) {
       if (precision == FOCK_PREC_F64) a.out_scale = ham->nn_scale;
-      return fock_launch_nn(a, ham->d_nn_bond[precision], ham->d_nn_diag[precision], ham->nn_nb, precision,
-                            sp->device, stream);
+      return fock_launch_nn(a, ham->d_nn_bond[precision], ham->d_nn_e[precision], ham->d_nn_t[precision],
+                            ham->nn_nb, precision, sp->device, stream);
     }
     // Every reduced coefficient present and M <= 10: the register-resident
     // kernel with the addition loop unrolled at compile time.

@@ -122,7 +122,8 @@ struct fock_ham {
   int nn_nb;                // bonds: M - 1, or M for a ring
   double nn_scale;          // FOCK_PREC_F64 arrays stored divided by this power of two
   void *d_nn_bond[3];       // [2 nb] h_kl, h_lk of bond (k, k + 1 mod M)
-  void *d_nn_diag[3];       // [2 M] h_kk, then W_kkkk (real)
+  void *d_nn_e[3];          // [M][N + 1] site energies E_k(n) = h_kk n + W_kkkk n (n - 1) / 2
+  void *d_nn_t[3];          // [N + 1][N + 1] hop amplitudes sqrt(a (b + 1)) (native FP64 only; null for large N)
   int32_t *d_slots;         // [nadd] jump-map slot of each term
   // workspace owned by the Hamiltonian (used when the caller passes none)
   void *ws;
