@@ -19,6 +19,9 @@ Contents (Andriati & Gammal, arXiv:2005.13679):
   two-body operator applied by ``apply_push``;
 * ``evolve`` -- exp(-i H dt) C through the eigen-decomposition of the dense H
   (the exact propagator that a short-iterative-Lanczos step approximates);
+* ``sector_indices``, ``sector_apply`` -- the configurations of one total
+  orbital weight sum_i i n_i (total momentum for plane waves) in the order of
+  the full space, and sigma = H C restricted to them (embed, push, restrict);
 * ``lanczos_ground`` -- Lanczos with complete re-orthogonalisation and a
   tridiagonal eigen-solve, as in Sec. 5;
 * ``bethe_ground_energy`` -- the Lieb-Liniger ground state from the Bethe
@@ -244,6 +247,30 @@ def evolve(N: int, M: int, h, W, C, dt: float) -> np.ndarray:
     E, U = np.linalg.eigh(H)
     CC = _cplx(C, (nc(N, M),))
     return U @ (np.exp(-1j * E * dt) * (U.conj().T @ CC))
+
+
+# --------------------------------------------------------------------------
+# Sectors of fixed total orbital weight (total momentum for plane waves)
+# --------------------------------------------------------------------------
+def sector_indices(N: int, M: int, Q: int) -> np.ndarray:
+    """Full-space indices, ascending, of the configurations with
+    sum_i i n_i = Q.  For the plane-wave orbitals of Sec. 5 (orbital i has
+    momentum (i - floor(M/2)) 2 pi / L) this is the sector of total momentum
+    (Q - N floor(M/2)) 2 pi / L, which H preserves when h is diagonal and
+    W_kqsl = 0 unless k + q = s + l.  The sector's basis is ordered as the
+    full space orders it (Algorithm 1), so the rank of a sector configuration
+    is its position in this list."""
+    occ = unrank_batch(N, M, np.arange(nc(N, M), dtype=np.int64))
+    return np.nonzero(occ.astype(np.int64) @ np.arange(M, dtype=np.int64) == Q)[0]
+
+
+def sector_apply(N: int, M: int, Q: int, h, W, Cs) -> np.ndarray:
+    """sigma = H C on a sector: C embedded in the full space (zero outside
+    the sector), sigma = H C by the push form, and the sector's rows kept."""
+    idx = sector_indices(N, M, Q)
+    C = np.zeros(nc(N, M), dtype=np.complex128)
+    C[idx] = _cplx(Cs, (idx.shape[0],))
+    return apply_push(N, M, h, W, C)[idx]
 
 
 # --------------------------------------------------------------------------

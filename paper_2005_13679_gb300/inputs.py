@@ -96,6 +96,19 @@ def nearest_neighbour_hw(M: int, seed: int, ring: bool = True, complex_hops: boo
     return h, W
 
 
+def weight_conserving_hw(M: int, seed: int):
+    """Random operator that preserves the total orbital weight sum_i i n_i:
+    real diagonal h, and the random symmetrised W of ``random_hermitian_hw``
+    kept only where k + q = s + l (the Lieb-Liniger selection rule, with
+    complex coefficients)."""
+    h0, W0 = random_hermitian_hw(M, seed)
+    h = np.diag(np.real(np.diag(h0))).astype(np.complex128)
+    i = np.arange(M)
+    tot = i[:, None] + i[None, :]
+    W = np.where(tot[:, :, None, None] == tot[None, None, :, :], W0, 0.0)
+    return np.ascontiguousarray(h), np.ascontiguousarray(W)
+
+
 def random_hermitian_hw(M: int, seed: int, sigma_h: float = 1.0, sigma_w: float = 0.1):
     """Random Hermitian h and boson-symmetric Hermitian W (see module notes)."""
     rng = np.random.Generator(np.random.PCG64(seed))
