@@ -63,6 +63,7 @@ extern "C" {
 #define FOCK_ERR_NOT_BUILT     -12   /* jump maps requested but not built        */
 #define FOCK_ERR_DEVICE        -13   /* object used on another device            */
 #define FOCK_ERR_SCRATCH_LIMIT -14   /* request exceeds the fixed no-alloc scratch */
+#define FOCK_ERR_NOT_CONSERVING -15  /* operator changes a sector's total weight  */
 
 /* Human-readable name of a status code (static storage, never NULL). */
 const char *fock_strerror(int status);
@@ -293,6 +294,70 @@ int fock_sil_step(const fock_space *sp, const fock_ham *ham, void *C_dev, double
  * the current device is not the space's. */
 int fock_density_matrices(const fock_space *sp, const void *C_dev, double *rho1_host, double *rho2_host,
                           void *stream);
+
+/* ------------------------------------------------------------------------- */
+/* Sectors of fixed total orbital weight Q = sum_i i n_i                     */
+/* ------------------------------------------------------------------------- */
+/* With the plane-wave orbitals of Sec. 5 (orbital i of momentum
+ * (i - floor(M/2)) 2 pi / L) a sector is a total-momentum sector,
+ * P = (Q - N floor(M/2)) 2 pi / L.  An operator with diagonal h and
+ * W_kqsl = 0 unless k + q = s + l (Lieb-Liniger, Sec. 5) maps each sector into
+ * itself (total momentum is conserved), so its eigenproblem and its dynamics
+ * restrict to one sector, about N (M - 1) + 1 times smaller than H(N, M).
+ * This restriction is not in the paper; it follows from the conservation law.
+ * Sector vectors are ordered as H(N, M) orders its configurations (Algorithm
+ * 1), restricted to the sector, and stored [N_sec][nrhs] like full vectors. */
+typedef struct fock_sector fock_sector;
+
+/* The sector of weight Q of the space (0 <= Q <= N (M - 1), FOCK_ERR_ARG
+ * otherwise).  Builds the counting tables D_m(s, q) (configurations of s
+ * particles in orbitals 0..m-1 of weight q; host uint64 and device mod 2^32,
+ * (2M - 3)(N + 1)(Q + 1) words on the device).  FOCK_ERR_OVERFLOW when the
+ * sector holds 2^31 configurations or more.  The sector refers to `sp`, which
+ * must outlive it. */
+int fock_sector_create(const fock_space *sp, int64_t Q, fock_sector **out);
+int fock_sector_destroy(fock_sector *sec);
+int fock_sector_size(const fock_sector *sec, int64_t *n_sector);
+
+/* Sector indices of `count` occupation vectors (int32 [count][M], device).
+ * Vectors that are not configurations of the sector (negative entries, sum
+ * != N, weight != Q) get -1 and the call returns FOCK_ERR_INVALID_CONFIG
+ * after the whole batch ran.  Synchronous on `stream`. */
+int fock_sector_rank(const fock_sector *sec, const int32_t *occ_dev, int64_t count, int64_t *idx_dev,
+                     void *stream);
+
+/* Occupation vectors of `count` sector indices; indices outside [0, N_sec)
+ * give rows of -1 and FOCK_ERR_RANGE.  Synchronous on `stream`. */
+int fock_sector_unrank(const fock_sector *sec, const int64_t *idx_dev, int64_t count, int32_t *occ_dev,
+                       void *stream);
+
+/* Terms one sector apply evaluates: sum over the operator's removal lists of
+ * (additions) x (sector configurations in which the removal is possible).
+ * FOCK_ERR_NOT_CONSERVING if a term changes the weight; FOCK_ERR_ARG if `ham`
+ * was built on another space. */
+int fock_sector_terms(const fock_sector *sec, const fock_ham *ham, int64_t *terms);
+
+/* Device workspace fock_sector_apply_H wants (FOCK_PREC_F64: 256 B + 16 B per
+ * configuration per right-hand side; 0 otherwise). */
+int fock_sector_workspace_size(const fock_sector *sec, int32_t nrhs, int precision, size_t *bytes);
+
+/* sigma = H C within the sector (Eq. Haction restricted), precisions and
+ * buffer rules as fock_apply_H (complex128 or complex64, [N_sec][nrhs],
+ * 1 <= nrhs <= 16, no aliasing).  `ham` must have been created on the
+ * sector's space and conserve the weight (FOCK_ERR_NOT_CONSERVING otherwise,
+ * checked on the host before any launch).  A NULL or short workspace makes
+ * the sector allocate and keep its own.  Asynchronous on `stream`. */
+int fock_sector_apply_H(const fock_sector *sec, const fock_ham *ham, const void *C_dev, void *sigma_dev,
+                        int32_t nrhs, int precision, void *workspace_dev, size_t workspace_bytes,
+                        void *stream);
+
+/* Lanczos ground state within the sector: fock_lanczos_ground's algorithm,
+ * arguments and statuses, over vectors of N_sec entries (vec_dev, if not
+ * NULL, receives N_sec complex128 entries). */
+int fock_sector_lanczos_ground(const fock_sector *sec, const fock_ham *ham, int32_t max_iter,
+                               int32_t restart_len, double tol, uint64_t seed, int precision,
+                               const void *start_dev, double *E0, double *residual, void *vec_dev,
+                               int32_t *iters, void *stream);
 
 /* ------------------------------------------------------------------------- */
 /* Uneven batches of independent problems                                    */

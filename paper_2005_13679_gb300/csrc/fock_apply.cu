@@ -530,7 +530,7 @@ __global__ void fock_split_kernel(const double2 *__restrict__ x, int64_t n, cons
   }
 }
 
-static const size_t kWsHeader = 256;
+static const size_t kWsHeader = FOCK_WS_HEADER;
 
 
 // FP32-pair preparation of n complex128 values: max exponent, then the scaled

@@ -17,10 +17,13 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <functional>
+
 #include "../../include/fock.h"
 
 #define FOCK_MAXM 12
 #define FOCK_MAX_NRHS 16
+#define FOCK_WS_HEADER 256   // bytes before the FP32-pair copy of C in an apply workspace
 
 // Device-side status word bits (written with atomicOr by kernels that validate
 // their inputs; read back by the host after the launch).
@@ -143,3 +146,10 @@ size_t fock_apply_ws_bytes(const fock_space *sp, const fock_ham *ham, int nrhs, 
 size_t fock_apply_ws_pref(const fock_space *sp, const fock_ham *ham, int nrhs, int precision);
 int fock_prepare_df(const void *C, int64_t n, void *ws, int device, cudaStream_t stream);
 int fock_get_sm_count(int device);
+
+// H x -> y for the Lanczos driver: (precision, x, y, workspace, its bytes, stream).
+typedef std::function<int(int, const void *, void *, void *, size_t, cudaStream_t)> FockApplyFn;
+int fock_lanczos_run(int64_t n_vec, bool ham_real, int device, const FockApplyFn &apply_fn, size_t ws_bytes,
+                     int32_t max_iter, int32_t restart_len, double tol, uint64_t seed, int precision,
+                     const void *start_dev, double *E0, double *residual, void *vec_dev, int32_t *iters,
+                     cudaStream_t stream);

@@ -273,23 +273,23 @@ void jacobi_eigen(std::vector<double> A, int n, std::vector<double> &evals, std:
 
 }  // namespace
 
-extern "C" int fock_lanczos_ground(const fock_space *sp, const fock_ham *ham, int32_t max_iter,
-                                   int32_t restart_len, double tol, uint64_t seed, int precision,
-                                   const void *start_dev, double *E0, double *residual,
-                                   void *vec_dev, int32_t *iters, void *stream) {
-  if (!sp || !ham || !E0 || max_iter < 1 || restart_len < 2 || restart_len > 256 || !(tol > 0.0))
+// Thick-restart Lanczos over vectors of n complex128 entries; `apply` computes
+// H x -> y in the requested precision on the stream (x, y device vectors of
+// the precision's storage type, ws a workspace of ws_bytes).
+int fock_lanczos_run(int64_t n_vec, bool ham_real, int device, const FockApplyFn &apply_fn, size_t ws_bytes,
+                     int32_t max_iter, int32_t restart_len, double tol, uint64_t seed, int precision,
+                     const void *start_dev, double *E0, double *residual, void *vec_dev, int32_t *iters,
+                     cudaStream_t stream) {
+  if (!E0 || max_iter < 1 || restart_len < 2 || restart_len > 256 || !(tol > 0.0) || n_vec < 1)
     return FOCK_ERR_ARG;
   if (precision < FOCK_PREC_F64 || precision > FOCK_PREC_F32_MIXED) return FOCK_ERR_ARG;
-  int cur = -1;
-  if (cudaGetDevice(&cur) != cudaSuccess) return FOCK_ERR_CUDA;
-  if (cur != sp->device) return FOCK_ERR_DEVICE;
   Ctx c;
-  c.n = sp->nc;
+  c.n = n_vec;
   // A real Hamiltonian keeps a real start vector real: every product and every
   // Gram-Schmidt step then has zero imaginary parts, which are skipped.
-  c.real = ham->real && start_dev == nullptr;
-  c.sms = fock_get_sm_count(sp->device);
-  c.s = (cudaStream_t)stream;
+  c.real = ham_real && start_dev == nullptr;
+  c.sms = fock_get_sm_count(device);
+  c.s = stream;
   c.partial_h.resize((size_t)kDotBlocks * kChunk);
   const int64_t n = c.n;
   int m = restart_len;
@@ -299,7 +299,6 @@ extern "C" int fock_lanczos_ground(const fock_space *sp, const fock_ham *ham, in
   double2 *V = nullptr, *w = nullptr;
   float2 *c64a = nullptr, *c64b = nullptr;
   void *ws = nullptr;
-  size_t ws_bytes = fock_apply_ws_pref(sp, ham, 1, FOCK_PREC_F64);
   int st = FOCK_OK;
   auto cleanup = [&]() {
     cudaFree(V);
@@ -327,12 +326,12 @@ extern "C" int fock_lanczos_ground(const fock_space *sp, const fock_ham *ham, in
   auto apply = [&](int prec, const double2 *x, double2 *y) -> int {
     if (prec == FOCK_PREC_F32_MIXED) {
       to_c64_kernel<<<c.grid(), 256, 0, c.s>>>(x, n, c64a);
-      int r = fock_apply_internal(sp, ham, c64a, c64b, 1, prec, FOCK_ARM_HASH, ws, ws_bytes, c.s);
+      int r = apply_fn(prec, c64a, c64b, ws, ws_bytes, c.s);
       if (r) return r;
       to_c128_kernel<<<c.grid(), 256, 0, c.s>>>(c64b, n, y);
       return cudaGetLastError() == cudaSuccess ? FOCK_OK : FOCK_ERR_CUDA;
     }
-    return fock_apply_internal(sp, ham, x, y, 1, prec, FOCK_ARM_HASH, ws, ws_bytes, c.s);
+    return apply_fn(prec, x, y, ws, ws_bytes, c.s);
   };
 
   // start vector
@@ -434,6 +433,22 @@ extern "C" int fock_lanczos_ground(const fock_space *sp, const fock_ham *ham, in
   cleanup();
 #undef TRY
   return converged ? FOCK_OK : FOCK_ERR_NOCONV;
+}
+
+extern "C" int fock_lanczos_ground(const fock_space *sp, const fock_ham *ham, int32_t max_iter,
+                                   int32_t restart_len, double tol, uint64_t seed, int precision,
+                                   const void *start_dev, double *E0, double *residual,
+                                   void *vec_dev, int32_t *iters, void *stream) {
+  if (!sp || !ham || ham->sp != sp) return FOCK_ERR_ARG;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return FOCK_ERR_CUDA;
+  if (cur != sp->device) return FOCK_ERR_DEVICE;
+  FockApplyFn apply = [sp, ham](int prec, const void *x, void *y, void *ws, size_t ws_bytes, cudaStream_t s) {
+    return fock_apply_internal(sp, ham, x, y, 1, prec, FOCK_ARM_HASH, ws, ws_bytes, s);
+  };
+  return fock_lanczos_run(sp->nc, ham->real, sp->device, apply, fock_apply_ws_pref(sp, ham, 1, FOCK_PREC_F64),
+                          max_iter, restart_len, tol, seed, precision, start_dev, E0, residual, vec_dev, iters,
+                          (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -29,6 +29,7 @@ extern "C" const char *fock_strerror(int status) {
     case FOCK_ERR_NOT_BUILT: return "jump maps not built";
     case FOCK_ERR_DEVICE: return "object belongs to another device";
     case FOCK_ERR_SCRATCH_LIMIT: return "request exceeds the fixed scratch of the no-allocation entry point";
+    case FOCK_ERR_NOT_CONSERVING: return "operator changes the total orbital weight of the sector";
     default: return "unknown status";
   }
 }

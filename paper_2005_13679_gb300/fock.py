@@ -29,6 +29,7 @@ FOCK_ERR_TIMEOUT = -11
 FOCK_ERR_NOT_BUILT = -12
 FOCK_ERR_DEVICE = -13
 FOCK_ERR_SCRATCH_LIMIT = -14
+FOCK_ERR_NOT_CONSERVING = -15
 FOCK_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 FOCK_MAP_SINGLE = 1
@@ -51,6 +52,8 @@ EXPORTS = (
     "fock_hamiltonian_is_real",
     "fock_apply_set_events", "fock_apply_workspace_size", "fock_apply_H", "fock_apply_H_host", "fock_apply_H_noalloc",
     "fock_lanczos_ground", "fock_sil_step", "fock_density_matrices",
+    "fock_sector_create", "fock_sector_destroy", "fock_sector_size", "fock_sector_rank", "fock_sector_unrank",
+    "fock_sector_terms", "fock_sector_workspace_size", "fock_sector_apply_H", "fock_sector_lanczos_ground",
     "fock_batch_create", "fock_batch_destroy", "fock_batch_offsets", "fock_batch_terms", "fock_batch_apply",
     "fock_batch_autotune", "fock_batch_lanczos_ground",
 )
@@ -106,6 +109,18 @@ def load(path: str | None = None):
         "fock_density_matrices": [vp, vp, vp, vp, vp],
         "fock_sil_step": [vp, vp, vp, dbl, i32, dbl, ctypes.c_int, P(i32), P(dbl), vp],
     }
+    sigs.update({
+        "fock_sector_create": [vp, i64, P(vp)],
+        "fock_sector_destroy": [vp],
+        "fock_sector_size": [vp, P(i64)],
+        "fock_sector_rank": [vp, vp, i64, vp, vp],
+        "fock_sector_unrank": [vp, vp, i64, vp, vp],
+        "fock_sector_terms": [vp, vp, P(i64)],
+        "fock_sector_workspace_size": [vp, i32, ctypes.c_int, P(sz)],
+        "fock_sector_apply_H": [vp, vp, vp, vp, i32, ctypes.c_int, vp, sz, vp],
+        "fock_sector_lanczos_ground": [vp, vp, i32, i32, dbl, ctypes.c_uint64, ctypes.c_int, vp,
+                                       P(dbl), P(dbl), vp, P(i32), vp],
+    })
     sigs.update({
         "fock_batch_create": [i32, vp, vp, vp, vp, dbl, P(vp)],
         "fock_batch_destroy": [vp],
@@ -383,6 +398,112 @@ class Hamiltonian:
     def close(self):
         if self.handle:
             fock_hamiltonian_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------------
+# sectors of fixed total orbital weight (total momentum)
+# --------------------------------------------------------------------------
+def fock_sector_create(sp, Q: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().fock_sector_create(sp, int(Q), ctypes.byref(h)), "fock_sector_create")
+    return h
+
+
+def fock_sector_destroy(sec) -> None:
+    load().fock_sector_destroy(sec)
+
+
+def fock_sector_size(sec) -> int:
+    n = ctypes.c_int64()
+    _check(load().fock_sector_size(sec, ctypes.byref(n)), "fock_sector_size")
+    return n.value
+
+
+def fock_sector_rank(sec, occ, idx=None, stream=None, check: bool = True):
+    """occ: int32 CUDA tensor [count, M]; returns (int64 sector indices, status)."""
+    import torch
+    if idx is None:
+        idx = torch.empty(occ.shape[0], dtype=torch.int64, device=occ.device)
+    st = load().fock_sector_rank(sec, _dptr(occ), occ.shape[0], _dptr(idx), _stream(stream))
+    if check:
+        _check(st, "fock_sector_rank")
+    return idx, st
+
+
+def fock_sector_unrank(sec, idx, M: int, occ=None, stream=None, check: bool = True):
+    """idx: int64 CUDA tensor [count]; returns (int32 occupations [count, M], status)."""
+    import torch
+    if occ is None:
+        occ = torch.empty((idx.shape[0], M), dtype=torch.int32, device=idx.device)
+    st = load().fock_sector_unrank(sec, _dptr(idx), idx.shape[0], _dptr(occ), _stream(stream))
+    if check:
+        _check(st, "fock_sector_unrank")
+    return occ, st
+
+
+def fock_sector_terms(sec, ham) -> int:
+    n = ctypes.c_int64()
+    _check(load().fock_sector_terms(sec, ham, ctypes.byref(n)), "fock_sector_terms")
+    return n.value
+
+
+def fock_sector_workspace_size(sec, nrhs: int, precision: int) -> int:
+    b = ctypes.c_size_t()
+    _check(load().fock_sector_workspace_size(sec, int(nrhs), int(precision), ctypes.byref(b)),
+           "fock_sector_workspace_size")
+    return b.value
+
+
+def fock_sector_apply_H(sec, ham, C, sigma=None, nrhs: int = 1, precision: int = FOCK_PREC_F64,
+                        workspace=None, stream=None):
+    """sigma = H C within the sector (C: CUDA tensor [N_sec] or [N_sec, nrhs])."""
+    import torch
+    if sigma is None:
+        sigma = torch.empty_like(C)
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load().fock_sector_apply_H(sec, ham, _dptr(C), _dptr(sigma), int(nrhs), int(precision),
+                                      _dptr(workspace), ws_bytes, _stream(stream)), "fock_sector_apply_H")
+    return sigma
+
+
+def fock_sector_lanczos_ground(sec, ham, max_iter: int = 300, restart_len: int = 30, tol: float = 1e-12,
+                               seed: int = 1, precision: int = FOCK_PREC_F64, start=None,
+                               want_vector=False, stream=None):
+    """Returns (E0, residual, iterations, vector-or-None, status)."""
+    import torch
+    E0, res, it = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    vec = None
+    if want_vector:
+        vec = torch.empty(fock_sector_size(sec), dtype=torch.complex128, device="cuda")
+    st = load().fock_sector_lanczos_ground(sec, ham, int(max_iter), int(restart_len), float(tol),
+                                           ctypes.c_uint64(int(seed)), int(precision), _dptr(start),
+                                           ctypes.byref(E0), ctypes.byref(res), _dptr(vec), ctypes.byref(it),
+                                           _stream(stream))
+    _check(st, "fock_sector_lanczos_ground", allow=(FOCK_ERR_NOCONV,))
+    return E0.value, res.value, it.value, vec, st
+
+
+class Sector:
+    """The configurations of `space` with sum_i i n_i = Q."""
+
+    def __init__(self, space: Space, Q: int):
+        self.space, self.Q = space, int(Q)
+        self.handle = fock_sector_create(space.handle, Q)
+        self.size = fock_sector_size(self.handle)
+
+    def apply(self, ham: Hamiltonian, C, sigma=None, nrhs=1, precision=FOCK_PREC_F64, workspace=None):
+        return fock_sector_apply_H(self.handle, ham.handle, C, sigma, nrhs, precision, workspace)
+
+    def close(self):
+        if self.handle:
+            fock_sector_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
