@@ -327,6 +327,124 @@ def time_steps(torch, fn, steps, warmup, barrier):
     return e0.elapsed_time(e1) / steps
 
 
+def run_sector(args, w):
+    """One fixed-momentum sector of a Lieb-Liniger ring (weight sum_i i n_i =
+    w.sector_Q): one step is one sector apply sigma = H C in the requested
+    precision.  Also reports the other precisions, the end-to-end apply with
+    host buffers, and the sector's Lanczos ground state."""
+    import numpy as np
+    import torch
+
+    from paper_2005_13679_gb300 import fock
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local if ws > 1 else 0)
+    fock.load()
+    peaks, peak_src = load_peaks()
+    h, W = w.hamiltonian()
+    sp = fock.Space(w.N, w.M)
+    sec = fock.Sector(sp, w.sector_Q)
+    H = fock.Hamiltonian(sp, h, W)
+    prec = PREC[args.precision]
+    n = sec.size
+    terms = fock.fock_sector_terms(sec.handle, H.handle)
+    Cn = inputs_random_state(n, w.seed)
+    Cd = torch.from_numpy(Cn).cuda()
+    if prec == 2:
+        Cd = Cd.to(torch.complex64)
+    sig = torch.empty_like(Cd)
+    wsb = torch.empty(max(fock.fock_sector_workspace_size(sec.handle, 1, prec), 16), dtype=torch.uint8,
+                      device="cuda")
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a_, b_ in kev:
+        a_.record(); b_.record()
+    torch.cuda.synchronize()
+    counter = {"i": -1}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # larger than L2
+
+    def step():
+        i = counter["i"]
+        flush.zero_()
+        fock.fock_apply_set_events(H.handle, *(kev[i] if 0 <= i < len(kev) else (None, None)))
+        fock.fock_sector_apply_H(sec.handle, H.handle, Cd, sig, 1, prec, wsb)
+
+    def step_timed():
+        counter["i"] += 1
+        step()
+
+    clk = ClockSampler(local)
+    clk.start()
+    for _ in range(args.warmup):
+        step()
+    counter["i"] = -1
+    ms = time_steps(torch, step_timed, args.steps, 0, lambda: None)
+    clocks = clk.stop()
+    fock.fock_apply_set_events(H.handle, None, None)
+    kernel_ms = sum(a_.elapsed_time(b_) for a_, b_ in kev) / len(kev)
+    elem = 8 if prec == 2 else 16
+    nbytes = n * elem
+    # end to end: pinned host C -> device, apply, device -> host
+    Ch = torch.from_numpy(Cn).to(Cd.dtype).pin_memory()
+    Sh = torch.empty_like(Ch).pin_memory()
+
+    def e2e_step():
+        Cd.copy_(Ch, non_blocking=True)
+        fock.fock_sector_apply_H(sec.handle, H.handle, Cd, sig, 1, prec, wsb)
+        Sh.copy_(sig, non_blocking=True)
+
+    e2e_ms = time_steps(torch, e2e_step, max(3, args.steps // 2), 1, lambda: None)
+    key = (args.precision, "direct")
+    flops_term = FLOPS_PER_TERM_REAL[key] if H.real else FLOPS_PER_TERM[key]
+    alu = terms * flops_term / (kernel_ms * 1e-3) / 1e12
+    gbs = 2 * nbytes / (kernel_ms * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": terms * ws / (ms * 1e-3), "unit": "config-terms/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
+        "config": {"workload": w.name, "N": w.N, "M": w.M, "sector_weight": w.sector_Q,
+                   "total_momentum": w.sector_Q - w.N * (w.M // 2), "n_sector": n,
+                   "nc_full": math.comb(w.N + w.M - 1, w.M - 1), "precision": args.precision,
+                   "l2": "flushed before every step (256 MB write; the sector vectors fit L2)",
+                   "parallelism": f"replicas x{ws}"},
+        "sector_terms_per_apply": terms,
+        "gpu_launches": (3 if prec == 0 else 1) * args.steps,
+        "roofline": {"bound": "alu", "achieved": alu, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": alu / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "fock_sector_apply_kernel",
+                     "kernel_ms": kernel_ms, "executed_terms": terms, "flops_per_term": flops_term,
+                     "hbm_frac": gbs / peaks["hbm_gbs"], "peak_source": peak_src},
+        "e2e": {"value": terms / (e2e_ms * 1e-3), "unit": "config-terms/s", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms},
+        "clocks": clocks,
+    }
+    if args.extras:
+        extras = {}
+        for name, p in PREC.items():
+            if p == prec:
+                continue
+            X = torch.from_numpy(Cn).cuda()
+            if p == 2:
+                X = X.to(torch.complex64)
+            Y = torch.empty_like(X)
+            wsx = torch.empty(max(fock.fock_sector_workspace_size(sec.handle, 1, p), 16), dtype=torch.uint8,
+                              device="cuda")
+            t = time_steps(torch, lambda: fock.fock_sector_apply_H(sec.handle, H.handle, X, Y, 1, p, wsx),
+                           max(3, args.steps // 2), 1, lambda: None)
+            extras[name] = {"ms_per_step": t, "config_terms_per_s": terms / (t * 1e-3)}
+        out["other_precisions"] = extras
+        t0 = time.perf_counter()
+        E0, res, it, _, st = fock.fock_sector_lanczos_ground(sec.handle, H.handle, max_iter=args.lanczos_iters,
+                                                             restart_len=30, tol=1e-10, seed=w.lanczos_seed)
+        out["lanczos"] = {"seconds": time.perf_counter() - t0, "E0": E0, "residual": res, "products": it,
+                          "status": int(st), "precision": "f64"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+def inputs_random_state(n, seed):
+    from paper_2005_13679_gb300 import inputs
+    return inputs.random_state(n, seed)
+
+
 def run_batch(args):
     """64 uneven Lieb-Liniger instances (N in [10, 200], M in 4..12, log g uniform,
     capped at 10^7 configurations each): one step is one batched FP64-class
@@ -402,6 +520,11 @@ def main():
     if args.workload == "ll_batch64" and args.impl != "reference":
         return run_batch(args)
     w = inputs.WORKLOADS[args.workload]
+    if w.sector_Q is not None:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "sector workloads have no oracle timing leg"}))
+            return 0
+        return run_sector(args, w)
     if args.impl == "reference":
         return run_reference(args, w)
 

@@ -185,7 +185,8 @@ int fock_hamiltonian_is_real(const fock_ham *ham, int *is_real);
  * outside the pair).  For the two-phase evaluation of dense coefficients the
  * main kernel is the first phase (the product with the reduced coefficients
  * over the (N-2)-particle space); the second phase follows the stop event.
- * Events are cudaEvent_t passed as void*, owned by the caller; NULL, NULL
+ * Sector applies (fock_sector_apply_H) with this Hamiltonian record the pair
+ * the same way.  Events are cudaEvent_t passed as void*, owned by the caller; NULL, NULL
  * clears the hook.  Not thread-safe with concurrent applies on the same
  * Hamiltonian. */
 int fock_apply_set_events(fock_ham *ham, void *start_event, void *stop_event);

@@ -386,29 +386,38 @@ static int fock_sector_apply_internal(const fock_sector *sec, const fock_ham *ha
   a.sigma = sigma;
   a.in_exp = nullptr;
   const int M = sec->M;
+  if (precision == FOCK_PREC_F64) {
+    if (!ws || ws_bytes < sector_ws_bytes(sec, nrhs, precision)) return FOCK_ERR_ARG;
+    const int st = fock_prepare_df(C, sec->ns * (int64_t)nrhs, ws, sec->device, stream);
+    if (st) return st;
+    a.C = (const char *)ws + FOCK_WS_HEADER;
+    a.in_exp = (const int *)ws + 1;
+  }
+  // the caller's events (fock_apply_set_events) bracket the main kernel
+  if (ham->ev_start) FOCK_CUDA_TRY(cudaEventRecord(ham->ev_start, stream));
+  int st;
   switch (precision) {
-    case FOCK_PREC_F64: {
-      if (!ws || ws_bytes < sector_ws_bytes(sec, nrhs, precision)) return FOCK_ERR_ARG;
-      const int st = fock_prepare_df(C, sec->ns * (int64_t)nrhs, ws, sec->device, stream);
-      if (st) return st;
-      a.C = (const char *)ws + FOCK_WS_HEADER;
-      a.in_exp = (const int *)ws + 1;
+    case FOCK_PREC_F64:
       a.coef = ham->d_coefdf;
       a.sq = ham->d_sqrtdf;
       a.out_scale = ham->coef_scale;
-      return launch_sector<PolDFP>(a, M, sec->device, stream);
-    }
+      st = launch_sector<PolDFP>(a, M, sec->device, stream);
+      break;
     case FOCK_PREC_F64_NATIVE:
       a.coef = ham->d_coef64;
       a.sq = ham->d_sqrt64;
       a.out_scale = 1.0;
-      return launch_sector<PolF64>(a, M, sec->device, stream);
+      st = launch_sector<PolF64>(a, M, sec->device, stream);
+      break;
     default:
       a.coef = ham->d_coef32;
       a.sq = ham->d_sqrt32;
       a.out_scale = 1.0;
-      return launch_sector<PolMixedP>(a, M, sec->device, stream);
+      st = launch_sector<PolMixedP>(a, M, sec->device, stream);
+      break;
   }
+  if (st == FOCK_OK && ham->ev_stop) FOCK_CUDA_TRY(cudaEventRecord(ham->ev_stop, stream));
+  return st;
 }
 
 extern "C" int fock_sector_create(const fock_space *sp, int64_t Q, fock_sector **out) {

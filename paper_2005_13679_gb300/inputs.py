@@ -178,6 +178,7 @@ class Workload:
     nrhs: int = 1
     rhs_seeds: list = field(default_factory=list)
     lanczos_seed: int = 0
+    sector_Q: int | None = None   # total orbital weight sum_i i n_i of a sector workload
 
     @property
     def nc(self) -> int:
@@ -213,6 +214,10 @@ WORKLOADS = {
     # Profiling size of the Lieb-Liniger M = 10 workload: 20,160,075
     # configurations (complex128 C of 323 MB, larger than L2).
     "ll_n22_m10": Workload("ll_n22_m10", N=22, M=10, kind="ll", g=0.5, seed=3),
+    # Lieb-Liniger ring N = 30, M = 10, g = 0.5 restricted to total momentum 0
+    # (orbital weights sum_i i n_i = 150): 2,462,733 of the 211,915,132 configurations.
+    "ll_n30_m10_p0": Workload("ll_n30_m10_p0", N=30, M=10, kind="ll", g=0.5, seed=3, lanczos_seed=103,
+                              sector_Q=150),
     # Bose-Hubbard ring, 20 bosons on 12 sites, J = 1, U = 4: 84,672,315 configurations.
     "bh_n20_m12": Workload("bh_n20_m12", N=20, M=12, kind="bh", g=4.0, seed=6),
     # Profiling size of the Bose-Hubbard ring: 16 bosons on 12 sites,
