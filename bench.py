@@ -174,9 +174,6 @@ FLOPS_PER_TERM_REAL = {("f64", "direct"): 35, ("f32_mixed", "direct"): 6, ("f64_
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
 
 
-SMEM_OPTIN = 232448     # bytes of shared memory one block may opt into on this architecture
-
-
 def tc_shape(M):
     """Real-form sizes of the tensor-core phase 1 (fock_apply_tc.cuh)."""
     r2 = M * (M + 1)
@@ -189,29 +186,6 @@ def tc_shape_mixed(M):
     """Real-form sizes of the FP32-mixed tensor-core phase 1."""
     r2 = M * (M + 1)
     return r2, (r2 + 1 + 15) // 16 * 16, (3 * r2 + 1 + 15) // 16 * 16
-
-
-def tc_fits(N, M, mixed=False):
-    """Shared-memory layout of the tensor-core phase 1 within the per-block limit."""
-    al = lambda x: (x + 15) // 16 * 16
-    r2, nt, kt = tc_shape_mixed(M) if mixed else tc_shape(M)
-    xdim, nsq = N + M + 3, N + 4
-    o = nt * kt * 2 + 2 * 128 * kt * 2
-    o = al(o + 4 * r2)
-    o = al(o + 4 * (M - 1) * xdim)
-    o = al(o + 4 * (M - 1) * xdim)
-    o = al(o + (4 if mixed else 8) * nsq)
-    o = al(o + 56)
-    return o <= SMEM_OPTIN
-
-
-def path_of(w, prec):
-    """Which kernel family serves this workload (mirrors the library's dispatch)."""
-    if w.kind == "generic" and 2 <= w.M <= 8 and prec in (0, 2):
-        return "twophase_tc" if (w.M <= 6 and tc_fits(w.N, w.M, prec == 2)) else "twophase"
-    if w.kind == "bh" and 2 <= w.M <= 12:
-        return "nn"
-    return "direct"
 
 
 def nn_terms(w):
@@ -233,10 +207,10 @@ def tc_flops(w, mixed=False):
     return cols * (3 if mixed else 15) * r2 * r2 * 2, cols * 2 * nt * kt
 
 
-def launches_per_step(w, prec):
+def launches_per_step(path, prec):
     """Kernels of one apply: the FP32-pair input preparation (2), then the
-    two-phase pair (dense coefficients, 2 <= M <= 8) or one kernel."""
-    return (2 if prec == 0 else 0) + (2 if path_of(w, prec).startswith("twophase") else 1)
+    two-phase pair or one kernel."""
+    return (2 if prec == 0 else 0) + (2 if path.startswith("twophase") else 1)
 
 
 def executed_terms(w, h, W):
@@ -609,7 +583,7 @@ def main():
     nbytes = w.nc * w.nrhs * elem
     hbm_gbs = 2 * nbytes / (ms * 1e-3) / 1e9
     executed = executed_terms(w, h, W) * w.nrhs
-    path = path_of(w, prec)
+    path = fock.PATH_NAMES[fock.fock_apply_path(sp.handle, H.handle, w.nrhs, prec, fock.FOCK_ARM_AUTO, wsz)]
     traffic = load_traffic(w.name, args.precision)
     if path == "twophase_tc":
         # dominant kernel = phase 1 on the tensor cores (fp16 digits, FP32 accumulators)
@@ -642,7 +616,7 @@ def main():
                          "peak_note": f"HBM: measured copy bandwidth ({peak_src}); FP32 pipe: 152 SMs x 128 "
                                       "lanes x 2 flop x 2070 MHz"})
     else:
-        key = (args.precision, "twophase" if path.startswith("twophase") else path)
+        key = (args.precision, "twophase" if path.startswith("twophase") else "direct")
         flops_term = FLOPS_PER_TERM_REAL[key] if (H.real and key in FLOPS_PER_TERM_REAL) else FLOPS_PER_TERM[key]
         achieved = executed * flops_term / (kernel_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -661,7 +635,7 @@ def main():
                    "parallelism": f"replicas x{ws}"},
         "applies_per_s": applies,
         "config_terms_per_apply": terms,
-        "gpu_launches": launches_per_step(w, prec) * args.steps,
+        "gpu_launches": launches_per_step(path, prec) * args.steps,
         "roofline": roofline,
         "hbm": {"compulsory_bytes": 2 * nbytes, "achieved_gbs": hbm_gbs, "peak_gbs": peaks["hbm_gbs"],
                 "frac": hbm_gbs / peaks["hbm_gbs"], "peak_source": peak_src},

@@ -179,6 +179,56 @@ int fock_hamiltonian_is_real(const fock_ham *ham, int *is_real);
 #define FOCK_ARM_HASH 1         /* target indices from the hash on the fly    */
 #define FOCK_ARM_MAPS 2         /* target indices from the built jump maps    */
 
+/* Kernel paths of the apply (fock_apply_path, fock_apply_set_path,
+ * fock_autotune).  AUTO takes the first that can serve the call in the order
+ * listed: the two-phase evaluation through the (N-2)-particle space with its
+ * first phase on the tensor cores (dense reduced coefficients, 2 <= M <= 6,
+ * FOCK_PREC_F64 or FOCK_PREC_F32_MIXED, hash arm, the preferred workspace),
+ * the same with FP32 phase 1 (M <= 8), the nearest-neighbour kernel (h only on
+ * sites and bonds k, k+1, a ring when h_{0,M-1} != 0, W only on-site; hash
+ * arm), the register-resident dense kernel (dense coefficients, M <= 10), the
+ * sparse kernel (at most 2048 reduced coefficients), the list kernel (always;
+ * the only path for N_c >= 2^32 - 1). */
+#define FOCK_PATH_AUTO        0
+#define FOCK_PATH_TWOPHASE_TC 1
+#define FOCK_PATH_TWOPHASE    2
+#define FOCK_PATH_NN          3
+#define FOCK_PATH_DENSE       4
+#define FOCK_PATH_SPARSE      5
+#define FOCK_PATH_LIST        6
+
+/* The path an apply with these options takes (a workspace of
+ * workspace_bytes, 0 for none), honouring a path set by fock_autotune or
+ * fock_apply_set_path.  FOCK_ERR_NOT_BUILT for FOCK_ARM_MAPS without maps. */
+int fock_apply_path(const fock_space *sp, const fock_ham *ham, int32_t nrhs, int precision, int arm,
+                    size_t workspace_bytes, int32_t *path);
+
+/* Pin the path (and arm) later applies with this precision and right-hand-
+ * side class (nrhs == 1 or > 1) take when the caller passes FOCK_ARM_AUTO
+ * (or the same arm).  A path that cannot serve a call falls back to the
+ * built-in order for that call.  FOCK_PATH_AUTO clears the choice. */
+int fock_apply_set_path(fock_ham *ham, int32_t nrhs, int precision, int path, int arm);
+
+typedef struct fock_tuning {
+  int32_t path;        /* FOCK_PATH_* chosen                                  */
+  int32_t arm;         /* FOCK_ARM_HASH or FOCK_ARM_MAPS                      */
+  int32_t candidates;  /* (path, arm) pairs timed; 0 when read from the cache */
+  int32_t from_cache;  /* 1 when the choice came from cache_path              */
+  double ms;           /* mean time of one apply with the choice              */
+} fock_tuning;
+
+/* Autotuner: times every (path, arm) that can serve applies with these
+ * options (the maps arm only if maps are built) on device buffers it
+ * allocates (a deterministic test vector, the preferred workspace): one
+ * warm-up apply and three timed ones each, CUDA events on `stream`.  The
+ * fastest becomes this Hamiltonian's choice (fock_apply_set_path).  With
+ * cache_path not NULL a line keyed by (N, M, reduced coefficients, removal
+ * lists, realness, nrhs, precision, SM count) is looked up first and the
+ * measured choice appended after tuning.  Synchronous; FOCK_ERR_NOMEM when
+ * the tuning buffers do not fit. */
+int fock_autotune(const fock_space *sp, fock_ham *ham, int32_t nrhs, int precision, const char *cache_path,
+                  fock_tuning *out, void *stream);
+
 /* Profiling hook: when set, every apply with this Hamiltonian records
  * start_event immediately before and stop_event immediately after its main
  * H C kernel, on the apply's stream (the input preparation of FOCK_PREC_F64 is

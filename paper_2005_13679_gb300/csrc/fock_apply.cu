@@ -10,10 +10,12 @@
 // targets the two-body pass visits anyway).  Without W, or for N = 1, the
 // one-body list (removal k, addition l, coefficient h_kl) is used instead.
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
 #include <complex>
+#include <initializer_list>
 #include <vector>
 
 #include "fock_apply_kernel.cuh"
@@ -662,11 +664,33 @@ static void fill_args(ApplyArgs<Idx> &a, const fock_space *sp, const fock_ham *h
 
 static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Cin, void *sigma, int nrhs,
                        int precision, const int32_t *map, const int *in_exp, bool maps, bool nrhs16, int maxm,
-                       void *ws, size_t ws_bytes, cudaStream_t stream, bool *stop_recorded);
+                       void *ws, size_t ws_bytes, cudaStream_t stream, bool *stop_recorded, int force);
+
+// The tuned (path, arm) of fock_autotune for this precision and right-hand-side
+// count class, when the caller leaves the arm to the library (or asks for the
+// tuned arm).
+static void tuned_choice(const fock_ham *ham, int nrhs, int precision, int &arm, int &path) {
+  path = FOCK_PATH_AUTO;
+  const int cls = nrhs > 1 ? 1 : 0;
+  const int tp = ham->tuned_path[precision][cls], ta = ham->tuned_arm[precision][cls];
+  if (tp == FOCK_PATH_AUTO) return;
+  if (arm == FOCK_ARM_AUTO) arm = ta;
+  if (arm == ta) path = tp;
+}
+
+static int apply_path(const fock_space *sp, const fock_ham *ham, const void *C, void *sigma, int nrhs,
+                      int precision, int arm, void *ws, size_t ws_bytes, cudaStream_t stream, int force);
 
 int fock_apply_internal(const fock_space *sp, const fock_ham *ham, const void *C, void *sigma,
                         int nrhs, int precision, int arm, void *ws, size_t ws_bytes,
                         cudaStream_t stream) {
+  int path = FOCK_PATH_AUTO;
+  tuned_choice(ham, nrhs, precision, arm, path);
+  return apply_path(sp, ham, C, sigma, nrhs, precision, arm, ws, ws_bytes, stream, path);
+}
+
+static int apply_path(const fock_space *sp, const fock_ham *ham, const void *C, void *sigma, int nrhs,
+                      int precision, int arm, void *ws, size_t ws_bytes, cudaStream_t stream, int force) {
   const size_t elem = precision == FOCK_PREC_F32_MIXED ? 8 : 16;
   const size_t bytes = (size_t)sp->nc * (size_t)nrhs * elem;
   const char *c0 = (const char *)C, *s0 = (const char *)sigma;
@@ -698,71 +722,104 @@ int fock_apply_internal(const fock_space *sp, const fock_ham *ham, const void *C
   if (ham->ev_start) FOCK_CUDA_TRY(cudaEventRecord(ham->ev_start, stream));
   bool stop_recorded = false;
   const int st = launch_main(sp, ham, Cin, sigma, nrhs, precision, map, in_exp, maps, nrhs16, maxm, ws, ws_bytes,
-                             stream, &stop_recorded);
+                             stream, &stop_recorded, force);
   if (st == FOCK_OK && ham->ev_stop && !stop_recorded) FOCK_CUDA_TRY(cudaEventRecord(ham->ev_stop, stream));
   return st;
 }
 
+// Whether a kernel path can serve this apply (32-bit indices).
+static bool path_ok(int path, const fock_space *sp, const fock_ham *ham, const ApplyArgs<uint32_t> &a, int nrhs,
+                    int precision, bool maps, bool nrhs16, const void *ws, size_t ws_bytes) {
+  const bool two = !maps && ws && twophase_eligible(sp, ham, precision) &&
+                   ws_bytes >= fock_apply_ws_pref(sp, ham, nrhs, precision);
+  switch (path) {
+    case FOCK_PATH_TWOPHASE_TC: return two && tc_eligible(sp, ham, a, nrhs, precision);
+    case FOCK_PATH_TWOPHASE: return two;
+    case FOCK_PATH_NN: return !maps && ham->nn;
+    case FOCK_PATH_DENSE:
+      return ham->dense && sp->M <= 10 && !(maps && nrhs16) && precision != FOCK_PREC_F64_NATIVE;
+    case FOCK_PATH_SPARSE: return !(maps && nrhs16) && (size_t)ham->nadd * 48 <= (size_t)96 * 1024;
+    case FOCK_PATH_LIST: return true;
+    default: return false;
+  }
+}
+
+// The built-in order: two-phase (tensor cores first) for dense coefficients,
+// the nearest-neighbour kernel, the register-resident dense kernel, the
+// sparse kernel, the list kernel.
+static int default_path(const fock_space *sp, const fock_ham *ham, const ApplyArgs<uint32_t> &a, int nrhs,
+                        int precision, bool maps, bool nrhs16, const void *ws, size_t ws_bytes) {
+  static const int order[] = {FOCK_PATH_TWOPHASE_TC, FOCK_PATH_TWOPHASE, FOCK_PATH_NN, FOCK_PATH_DENSE,
+                              FOCK_PATH_SPARSE};
+  for (int p : order)
+    if (path_ok(p, sp, ham, a, nrhs, precision, maps, nrhs16, ws, ws_bytes)) return p;
+  return FOCK_PATH_LIST;
+}
+
 // For the two-phase paths the caller's stop event (fock_apply_set_events) is
 // recorded after phase 1, the dominant kernel; *stop_recorded tells the caller.
+// `force` selects a path when it can serve the apply (else the built-in order).
 static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Cin, void *sigma, int nrhs,
                        int precision, const int32_t *map, const int *in_exp, bool maps, bool nrhs16, int maxm,
-                       void *ws, size_t ws_bytes, cudaStream_t stream, bool *stop_recorded) {
+                       void *ws, size_t ws_bytes, cudaStream_t stream, bool *stop_recorded, int force) {
   if (sp->idx32) {
     ApplyArgs<uint32_t> a;
     fill_args(a, sp, ham, Cin, sigma, nrhs, precision, map, in_exp);
-    // Dense coefficients, M <= 8, enough workspace: evaluate through H(N-2, M).
-    if (!maps && ws && twophase_eligible(sp, ham, precision) &&
-        ws_bytes >= fock_apply_ws_pref(sp, ham, nrhs, precision)) {
-      TwoPhaseArgs t;
-      t.a = a;
-      t.nc2 = (uint32_t)count_nm(sp->N - 2, sp->M);
-      t.Y = (char *)ws + twophase_y_offset(sp, ham, nrhs, precision);
-      t.g1 = ham->d_gauss1;
-      t.g2 = ham->d_gauss2;
-      t.tc_a = nullptr;
-      t.tc_er = nullptr;
-      t.status = nullptr;
-      t.phase1_done = ham->ev_stop;
-      *stop_recorded = ham->ev_stop != nullptr;
-      if (tc_eligible(sp, ham, a, nrhs, precision)) {
-        const bool mixed = precision == FOCK_PREC_F32_MIXED;
-        t.tc_a = mixed ? ham->d_tc_ma : ham->d_tc_a;
-        t.tc_er = mixed ? ham->d_tc_mer : ham->d_tc_er;
-        t.status = (int *)ws + 2;
-        if (mixed) FOCK_CUDA_TRY(cudaMemsetAsync(t.status, 0, sizeof(int), stream));
-        return fock_launch_twophase_tc(t, mixed, sp->device, stream);
+    const int path = (force != FOCK_PATH_AUTO && path_ok(force, sp, ham, a, nrhs, precision, maps, nrhs16, ws, ws_bytes))
+                         ? force : default_path(sp, ham, a, nrhs, precision, maps, nrhs16, ws, ws_bytes);
+    switch (path) {
+      case FOCK_PATH_TWOPHASE_TC:
+      case FOCK_PATH_TWOPHASE: {
+        // dense coefficients, M <= 8, enough workspace: evaluate through H(N-2, M)
+        TwoPhaseArgs t;
+        t.a = a;
+        t.nc2 = (uint32_t)count_nm(sp->N - 2, sp->M);
+        t.Y = (char *)ws + twophase_y_offset(sp, ham, nrhs, precision);
+        t.g1 = ham->d_gauss1;
+        t.g2 = ham->d_gauss2;
+        t.tc_a = nullptr;
+        t.tc_er = nullptr;
+        t.status = nullptr;
+        t.phase1_done = ham->ev_stop;
+        *stop_recorded = ham->ev_stop != nullptr;
+        if (path == FOCK_PATH_TWOPHASE_TC) {
+          const bool mixed = precision == FOCK_PREC_F32_MIXED;
+          t.tc_a = mixed ? ham->d_tc_ma : ham->d_tc_a;
+          t.tc_er = mixed ? ham->d_tc_mer : ham->d_tc_er;
+          t.status = (int *)ws + 2;
+          if (mixed) FOCK_CUDA_TRY(cudaMemsetAsync(t.status, 0, sizeof(int), stream));
+          return fock_launch_twophase_tc(t, mixed, sp->device, stream);
+        }
+        return fock_launch_twophase(t, precision == FOCK_PREC_F32_MIXED, sp->device, stream);
       }
-      return fock_launch_twophase(t, precision == FOCK_PREC_F32_MIXED, sp->device, stream);
-    }
-    // Nearest-neighbour operators: one diagonal term and two hops per bond.
-    if (!maps && ham->nn) {
-      if (precision == FOCK_PREC_F64) a.out_scale = ham->nn_scale;
-      return fock_launch_nn(a, ham->d_nn_bond[precision], ham->d_nn_e[precision], ham->d_nn_t[precision],
-                            ham->nn_nb, precision, sp->device, stream);
-    }
-    // Every reduced coefficient present and M <= 10: the register-resident
-    // kernel with the addition loop unrolled at compile time.
-    if (ham->dense && sp->M <= 10 && !(maps && nrhs16)) {
-      if (precision == FOCK_PREC_F64) return fock_launch_dense_df(a, nrhs16, maps, sp->device, stream);
-      if (precision == FOCK_PREC_F32_MIXED) return fock_launch_dense_mixed(a, nrhs16, maps, sp->device, stream);
-    }
-    // Any sparsity: per-configuration prefix tables, host-precomputed segments
-    // (the term list is staged in shared memory, so it must stay small).
-    if (!(maps && nrhs16) && (size_t)ham->nadd * 48 <= (size_t)96 * 1024) {
-      SparseArgs sa;
-      sa.base = a;
-      sa.terms = ham->d_terms;
-      sa.slots = ham->d_slots;
-      sa.nadd = ham->nadd;
-      if (precision == FOCK_PREC_F64) return fock_launch_sparse_df(sa, nrhs16, maps, sp->device, stream);
-      if (precision == FOCK_PREC_F64_NATIVE) return fock_launch_sparse_f64(sa, nrhs16, maps, sp->device, stream);
-      return fock_launch_sparse_mixed(sa, nrhs16, maps, sp->device, stream);
-    }
-    switch (precision) {
-      case FOCK_PREC_F64: return fock_launch_apply_df(&a, true, maxm, nrhs16, maps, sp->device, stream);
-      case FOCK_PREC_F64_NATIVE: return fock_launch_apply_f64(&a, true, maxm, nrhs16, maps, sp->device, stream);
-      default: return fock_launch_apply_mixed(&a, true, maxm, nrhs16, maps, sp->device, stream);
+      case FOCK_PATH_NN:
+        // nearest-neighbour operators: one diagonal term and two hops per bond
+        if (precision == FOCK_PREC_F64) a.out_scale = ham->nn_scale;
+        return fock_launch_nn(a, ham->d_nn_bond[precision], ham->d_nn_e[precision], ham->d_nn_t[precision],
+                              ham->nn_nb, precision, sp->device, stream);
+      case FOCK_PATH_DENSE:
+        // every reduced coefficient present and M <= 10: the register-resident
+        // kernel with the addition loop unrolled at compile time
+        if (precision == FOCK_PREC_F64) return fock_launch_dense_df(a, nrhs16, maps, sp->device, stream);
+        return fock_launch_dense_mixed(a, nrhs16, maps, sp->device, stream);
+      case FOCK_PATH_SPARSE: {
+        // any sparsity: per-configuration prefix tables, host-precomputed
+        // segments (the term list is staged in shared memory, so it must stay small)
+        SparseArgs sa;
+        sa.base = a;
+        sa.terms = ham->d_terms;
+        sa.slots = ham->d_slots;
+        sa.nadd = ham->nadd;
+        if (precision == FOCK_PREC_F64) return fock_launch_sparse_df(sa, nrhs16, maps, sp->device, stream);
+        if (precision == FOCK_PREC_F64_NATIVE) return fock_launch_sparse_f64(sa, nrhs16, maps, sp->device, stream);
+        return fock_launch_sparse_mixed(sa, nrhs16, maps, sp->device, stream);
+      }
+      default:
+        switch (precision) {
+          case FOCK_PREC_F64: return fock_launch_apply_df(&a, true, maxm, nrhs16, maps, sp->device, stream);
+          case FOCK_PREC_F64_NATIVE: return fock_launch_apply_f64(&a, true, maxm, nrhs16, maps, sp->device, stream);
+          default: return fock_launch_apply_mixed(&a, true, maxm, nrhs16, maps, sp->device, stream);
+        }
     }
   }
   ApplyArgs<uint64_t> a;
@@ -845,5 +902,187 @@ extern "C" int fock_apply_H_host(const fock_space *sp, const fock_ham *ham, cons
     FOCK_CUDA_TRY(cudaMemcpy(&status, (const int *)H->ws + 2, sizeof(int), cudaMemcpyDeviceToHost));
     if (status) return FOCK_ERR_TIMEOUT;
   }
+  return FOCK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Path query, pinning and the autotuner
+// ---------------------------------------------------------------------------
+static int select_path(const fock_space *sp, const fock_ham *ham, int nrhs, int precision, int arm,
+                       size_t ws_bytes, int force, int *path) {
+  const bool two_body = ham->nrem > 0 && ham->h_rem[0].size == 2;
+  const int32_t *map = nullptr;
+  if (arm == FOCK_ARM_MAPS) {
+    map = two_body ? sp->d_j2 : sp->d_j1;
+    if (!map) return FOCK_ERR_NOT_BUILT;
+  }
+  if (!sp->idx32 || ham->nrem == 0) {
+    *path = FOCK_PATH_LIST;
+    return FOCK_OK;
+  }
+  ApplyArgs<uint32_t> a;
+  fill_args(a, sp, ham, nullptr, nullptr, nrhs, precision, map, nullptr);
+  const void *ws = ws_bytes ? (const void *)ham : nullptr;   // only tested for presence
+  const bool maps = map != nullptr, nrhs16 = nrhs > 1;
+  *path = (force != FOCK_PATH_AUTO && path_ok(force, sp, ham, a, nrhs, precision, maps, nrhs16, ws, ws_bytes))
+              ? force : default_path(sp, ham, a, nrhs, precision, maps, nrhs16, ws, ws_bytes);
+  return FOCK_OK;
+}
+
+extern "C" int fock_apply_path(const fock_space *sp, const fock_ham *ham, int32_t nrhs, int precision, int arm,
+                               size_t workspace_bytes, int32_t *path) {
+  if (!path) return FOCK_ERR_ARG;
+  int st = check_apply_args(sp, ham, nrhs, precision, arm);
+  if (st) return st;
+  int p = FOCK_PATH_AUTO;
+  tuned_choice(ham, nrhs, precision, arm, p);
+  int chosen = FOCK_PATH_LIST;
+  st = select_path(sp, ham, nrhs, precision, arm, workspace_bytes, p, &chosen);
+  if (!st) *path = chosen;
+  return st;
+}
+
+extern "C" int fock_apply_set_path(fock_ham *ham, int32_t nrhs, int precision, int path, int arm) {
+  if (!ham || nrhs < 1 || nrhs > FOCK_MAX_NRHS) return FOCK_ERR_ARG;
+  if (precision < FOCK_PREC_F64 || precision > FOCK_PREC_F32_MIXED) return FOCK_ERR_ARG;
+  if (path < FOCK_PATH_AUTO || path > FOCK_PATH_LIST) return FOCK_ERR_ARG;
+  if (arm != FOCK_ARM_HASH && arm != FOCK_ARM_MAPS && !(path == FOCK_PATH_AUTO && arm == FOCK_ARM_AUTO))
+    return FOCK_ERR_ARG;
+  const int cls = nrhs > 1 ? 1 : 0;
+  ham->tuned_path[precision][cls] = (int8_t)path;
+  ham->tuned_arm[precision][cls] = (int8_t)(path == FOCK_PATH_AUTO ? FOCK_ARM_AUTO : arm);
+  return FOCK_OK;
+}
+
+static unsigned grid_cap(int64_t n, int device) {
+  int64_t b = (n + 255) / 256;
+  const int64_t cap = (int64_t)fock_get_sm_count(device) * 8;
+  if (b > cap) b = cap;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+// Deterministic test values in [-0.5, 0.5) for the tuner's input vector.
+__global__ void tune_fill_kernel(float *xf, double *xd, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t h = (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+    const double v = (double)(h >> 11) * 0x1.0p-53 - 0.5;
+    if (xd) xd[i] = v;
+    else xf[i] = (float)v;
+  }
+}
+
+static void tune_key(const fock_space *sp, const fock_ham *ham, int nrhs, int precision, char *key, size_t len) {
+  snprintf(key, len, "N=%d M=%d nadd=%d nrem=%d real=%d nrhs=%d precision=%d sms=%d", sp->N, sp->M, ham->nadd,
+           ham->nrem, ham->real ? 1 : 0, nrhs, precision, fock_get_sm_count(sp->device));
+}
+
+extern "C" int fock_autotune(const fock_space *sp, fock_ham *ham, int32_t nrhs, int precision,
+                             const char *cache_path, fock_tuning *out, void *stream) {
+  if (!out) return FOCK_ERR_ARG;
+  int st = check_apply_args(sp, ham, nrhs, precision, FOCK_ARM_AUTO);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  char key[192];
+  tune_key(sp, ham, nrhs, precision, key, sizeof key);
+  if (cache_path) {
+    if (FILE *f = fopen(cache_path, "r")) {
+      char line[320];
+      bool hit = false;
+      int p = 0, arm = 0;
+      double ms = 0.0;
+      while (fgets(line, sizeof line, f)) {
+        const char *bar = strchr(line, '|');
+        if (!bar || (size_t)(bar - line) != strlen(key) || strncmp(line, key, strlen(key)) != 0) continue;
+        if (sscanf(bar + 1, "%d %d %lf", &p, &arm, &ms) == 3 && p >= FOCK_PATH_TWOPHASE_TC && p <= FOCK_PATH_LIST &&
+            (arm == FOCK_ARM_HASH || arm == FOCK_ARM_MAPS))
+          hit = true;   // the last matching line wins
+      }
+      fclose(f);
+      if (hit) {
+        fock_apply_set_path(ham, nrhs, precision, p, arm);
+        out->path = p;
+        out->arm = arm;
+        out->ms = ms;
+        out->candidates = 0;
+        out->from_cache = 1;
+        return FOCK_OK;
+      }
+    }
+  }
+  const size_t elem = precision == FOCK_PREC_F32_MIXED ? 8 : 16;
+  const size_t vbytes = (size_t)sp->nc * (size_t)nrhs * elem;
+  const size_t wsb = fock_apply_ws_pref(sp, ham, nrhs, precision);
+  void *C = nullptr, *sig = nullptr, *ws = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(C);
+    cudaFree(sig);
+    cudaFree(ws);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMalloc(&C, vbytes) != cudaSuccess || cudaMalloc(&sig, vbytes) != cudaSuccess ||
+      (wsb && cudaMalloc(&ws, wsb) != cudaSuccess)) {
+    cudaGetLastError();
+    cleanup();
+    return FOCK_ERR_NOMEM;
+  }
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cleanup();
+    return FOCK_ERR_CUDA;
+  }
+  const int64_t nvals = (int64_t)(vbytes / (elem / 2));
+  tune_fill_kernel<<<grid_cap(nvals, sp->device), 256, 0, s>>>(
+      precision == FOCK_PREC_F32_MIXED ? (float *)C : nullptr, precision == FOCK_PREC_F32_MIXED ? nullptr : (double *)C,
+      nvals);
+  // the caller's profiling events stay out of the tuning runs
+  cudaEvent_t keep0 = ham->ev_start, keep1 = ham->ev_stop;
+  ham->ev_start = ham->ev_stop = nullptr;
+  const bool two_body = ham->nrem > 0 && ham->h_rem[0].size == 2;
+  const bool have_maps = (two_body ? sp->d_j2 : sp->d_j1) != nullptr;
+  int best_path = FOCK_PATH_LIST, best_arm = FOCK_ARM_HASH, tried = 0;
+  double best_ms = 1e300;
+  static const int paths[] = {FOCK_PATH_TWOPHASE_TC, FOCK_PATH_TWOPHASE, FOCK_PATH_NN, FOCK_PATH_DENSE,
+                              FOCK_PATH_SPARSE, FOCK_PATH_LIST};
+  for (int arm : {FOCK_ARM_HASH, FOCK_ARM_MAPS}) {
+    if (arm == FOCK_ARM_MAPS && !have_maps) continue;
+    for (int p : paths) {
+      int chosen = 0;
+      st = select_path(sp, ham, nrhs, precision, arm, wsb, p, &chosen);
+      if (st) break;
+      if (chosen != p) continue;                    // this path cannot serve the call
+      st = apply_path(sp, ham, C, sig, nrhs, precision, arm, ws, wsb, s, p);
+      if (!st && cudaEventRecord(e0, s) != cudaSuccess) st = FOCK_ERR_CUDA;
+      for (int r = 0; r < 3 && !st; ++r) st = apply_path(sp, ham, C, sig, nrhs, precision, arm, ws, wsb, s, p);
+      if (!st && cudaEventRecord(e1, s) != cudaSuccess) st = FOCK_ERR_CUDA;
+      if (!st && cudaEventSynchronize(e1) != cudaSuccess) st = FOCK_ERR_CUDA;
+      float ms = 0.f;
+      if (!st && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = FOCK_ERR_CUDA;
+      if (st) break;
+      ++tried;
+      if (ms / 3.0 < best_ms) {
+        best_ms = ms / 3.0;
+        best_path = p;
+        best_arm = arm;
+      }
+    }
+    if (st) break;
+  }
+  ham->ev_start = keep0;
+  ham->ev_stop = keep1;
+  cleanup();
+  if (st) return st;
+  fock_apply_set_path(ham, nrhs, precision, best_path, best_arm);
+  if (cache_path) {
+    if (FILE *f = fopen(cache_path, "a")) {
+      fprintf(f, "%s|%d %d %.6f\n", key, best_path, best_arm, best_ms);
+      fclose(f);
+    }
+  }
+  out->path = best_path;
+  out->arm = best_arm;
+  out->ms = best_ms;
+  out->candidates = tried;
+  out->from_cache = 0;
   return FOCK_OK;
 }

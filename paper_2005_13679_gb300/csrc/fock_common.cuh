@@ -131,6 +131,10 @@ struct fock_ham {
   // workspace owned by the Hamiltonian (used when the caller passes none)
   void *ws;
   size_t ws_bytes;
+  // kernel path and arm chosen by fock_autotune / fock_apply_set_path, per
+  // precision and right-hand-side class (one, several); FOCK_PATH_AUTO = none
+  int8_t tuned_path[3][2];
+  int8_t tuned_arm[3][2];
   // profiling hook (fock_apply_set_events)
   cudaEvent_t ev_start, ev_stop;
   // buffers for fock_apply_H_host

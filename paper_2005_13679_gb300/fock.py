@@ -43,6 +43,15 @@ FOCK_ARM_AUTO = 0
 FOCK_ARM_HASH = 1
 FOCK_ARM_MAPS = 2
 
+FOCK_PATH_AUTO = 0
+FOCK_PATH_TWOPHASE_TC = 1
+FOCK_PATH_TWOPHASE = 2
+FOCK_PATH_NN = 3
+FOCK_PATH_DENSE = 4
+FOCK_PATH_SPARSE = 5
+FOCK_PATH_LIST = 6
+PATH_NAMES = {1: "twophase_tc", 2: "twophase", 3: "nn", 4: "dense", 5: "sparse", 6: "list"}
+
 # Every extern "C" symbol declared in include/fock.h.
 EXPORTS = (
     "fock_strerror", "fock_version",
@@ -50,6 +59,7 @@ EXPORTS = (
     "fock_build_jump_maps", "fock_jump_map_get", "fock_jump_maps_free",
     "fock_hamiltonian_create", "fock_hamiltonian_destroy", "fock_hamiltonian_terms",
     "fock_hamiltonian_is_real",
+    "fock_apply_path", "fock_apply_set_path", "fock_autotune",
     "fock_apply_set_events", "fock_apply_workspace_size", "fock_apply_H", "fock_apply_H_host", "fock_apply_H_noalloc",
     "fock_lanczos_ground", "fock_sil_step", "fock_density_matrices",
     "fock_sector_create", "fock_sector_destroy", "fock_sector_size", "fock_sector_rank", "fock_sector_unrank",
@@ -57,6 +67,11 @@ EXPORTS = (
     "fock_batch_create", "fock_batch_destroy", "fock_batch_offsets", "fock_batch_terms", "fock_batch_apply",
     "fock_batch_autotune", "fock_batch_lanczos_ground",
 )
+
+
+class FockTuning(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("arm", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("from_cache", ctypes.c_int32), ("ms", ctypes.c_double)]
 
 
 class FockError(RuntimeError):
@@ -99,6 +114,9 @@ def load(path: str | None = None):
         "fock_hamiltonian_destroy": [vp],
         "fock_hamiltonian_terms": [vp, P(i64)],
         "fock_hamiltonian_is_real": [vp, P(ctypes.c_int)],
+        "fock_apply_path": [vp, vp, i32, ctypes.c_int, ctypes.c_int, sz, P(i32)],
+        "fock_apply_set_path": [vp, i32, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+        "fock_autotune": [vp, vp, i32, ctypes.c_int, ctypes.c_char_p, P(FockTuning), vp],
         "fock_apply_set_events": [vp, vp, vp],
         "fock_apply_workspace_size": [vp, vp, i32, ctypes.c_int, P(sz)],
         "fock_apply_H": [vp, vp, vp, vp, i32, ctypes.c_int, ctypes.c_int, vp, sz, vp],
@@ -270,6 +288,32 @@ def fock_hamiltonian_is_real(ham) -> bool:
     r = ctypes.c_int()
     _check(load().fock_hamiltonian_is_real(ham, ctypes.byref(r)), "fock_hamiltonian_is_real")
     return bool(r.value)
+
+
+def fock_apply_path(sp, ham, nrhs: int = 1, precision: int = FOCK_PREC_F64, arm: int = FOCK_ARM_AUTO,
+                    workspace_bytes: int | None = None) -> int:
+    """FOCK_PATH_* an apply with these options takes (default: the preferred workspace)."""
+    if workspace_bytes is None:
+        workspace_bytes = fock_apply_workspace_size(sp, ham, nrhs, precision)
+    p = ctypes.c_int32()
+    _check(load().fock_apply_path(sp, ham, int(nrhs), int(precision), int(arm), int(workspace_bytes),
+                                  ctypes.byref(p)), "fock_apply_path")
+    return p.value
+
+
+def fock_apply_set_path(ham, nrhs: int, precision: int, path: int, arm: int = FOCK_ARM_HASH) -> None:
+    _check(load().fock_apply_set_path(ham, int(nrhs), int(precision), int(path),
+                                      int(FOCK_ARM_AUTO if path == FOCK_PATH_AUTO else arm)),
+           "fock_apply_set_path")
+
+
+def fock_autotune(sp, ham, nrhs: int = 1, precision: int = FOCK_PREC_F64, cache_path: str | None = None,
+                  stream=None) -> FockTuning:
+    t = FockTuning()
+    _check(load().fock_autotune(sp, ham, int(nrhs), int(precision),
+                                None if cache_path is None else cache_path.encode(), ctypes.byref(t),
+                                _stream(stream)), "fock_autotune")
+    return t
 
 
 def fock_apply_set_events(ham, start_event=None, stop_event=None) -> None:
