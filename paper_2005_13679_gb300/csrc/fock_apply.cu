@@ -125,6 +125,11 @@ static void free_ham(fock_ham *h) {
   cudaFree(h->ws);
   cudaFree(h->hb_in);
   cudaFree(h->hb_out);
+  if (h->hb_copy) {
+    cudaStreamDestroy(h->hb_copy);
+    for (int i = 0; i < 8; ++i)
+      if (h->hb_ev[i]) cudaEventDestroy(h->hb_ev[i]);
+  }
   free(h);
 }
 
@@ -662,9 +667,22 @@ static void fill_args(ApplyArgs<Idx> &a, const fock_space *sp, const fock_ham *h
   }
 }
 
+// Host-buffer applies: when the two-phase path serves the call, phase 2 runs
+// in chunks of configurations and each finished chunk of sigma is copied to
+// the host on a second stream while the next chunk is computed.
+struct HostOverlap {
+  void *sigma_host;
+  cudaStream_t copy;
+  cudaEvent_t *ev;      // kHostChunks events
+  size_t row_bytes;     // bytes of one configuration's nrhs values
+  bool done;            // set when the chunks were copied
+};
+static const int kHostChunks = 8;
+
 static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Cin, void *sigma, int nrhs,
                        int precision, const int32_t *map, const int *in_exp, bool maps, bool nrhs16, int maxm,
-                       void *ws, size_t ws_bytes, cudaStream_t stream, bool *stop_recorded, int force);
+                       void *ws, size_t ws_bytes, cudaStream_t stream, bool *stop_recorded, int force,
+                       HostOverlap *ov);
 
 // The tuned (path, arm) of fock_autotune for this precision and right-hand-side
 // count class, when the caller leaves the arm to the library (or asks for the
@@ -679,7 +697,8 @@ static void tuned_choice(const fock_ham *ham, int nrhs, int precision, int &arm,
 }
 
 static int apply_path(const fock_space *sp, const fock_ham *ham, const void *C, void *sigma, int nrhs,
-                      int precision, int arm, void *ws, size_t ws_bytes, cudaStream_t stream, int force);
+                      int precision, int arm, void *ws, size_t ws_bytes, cudaStream_t stream, int force,
+                      HostOverlap *ov = nullptr);
 
 int fock_apply_internal(const fock_space *sp, const fock_ham *ham, const void *C, void *sigma,
                         int nrhs, int precision, int arm, void *ws, size_t ws_bytes,
@@ -690,7 +709,8 @@ int fock_apply_internal(const fock_space *sp, const fock_ham *ham, const void *C
 }
 
 static int apply_path(const fock_space *sp, const fock_ham *ham, const void *C, void *sigma, int nrhs,
-                      int precision, int arm, void *ws, size_t ws_bytes, cudaStream_t stream, int force) {
+                      int precision, int arm, void *ws, size_t ws_bytes, cudaStream_t stream, int force,
+                      HostOverlap *ov) {
   const size_t elem = precision == FOCK_PREC_F32_MIXED ? 8 : 16;
   const size_t bytes = (size_t)sp->nc * (size_t)nrhs * elem;
   const char *c0 = (const char *)C, *s0 = (const char *)sigma;
@@ -722,7 +742,7 @@ static int apply_path(const fock_space *sp, const fock_ham *ham, const void *C, 
   if (ham->ev_start) FOCK_CUDA_TRY(cudaEventRecord(ham->ev_start, stream));
   bool stop_recorded = false;
   const int st = launch_main(sp, ham, Cin, sigma, nrhs, precision, map, in_exp, maps, nrhs16, maxm, ws, ws_bytes,
-                             stream, &stop_recorded, force);
+                             stream, &stop_recorded, force, ov);
   if (st == FOCK_OK && ham->ev_stop && !stop_recorded) FOCK_CUDA_TRY(cudaEventRecord(ham->ev_stop, stream));
   return st;
 }
@@ -761,7 +781,8 @@ static int default_path(const fock_space *sp, const fock_ham *ham, const ApplyAr
 // `force` selects a path when it can serve the apply (else the built-in order).
 static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Cin, void *sigma, int nrhs,
                        int precision, const int32_t *map, const int *in_exp, bool maps, bool nrhs16, int maxm,
-                       void *ws, size_t ws_bytes, cudaStream_t stream, bool *stop_recorded, int force) {
+                       void *ws, size_t ws_bytes, cudaStream_t stream, bool *stop_recorded, int force,
+                       HostOverlap *ov) {
   if (sp->idx32) {
     ApplyArgs<uint32_t> a;
     fill_args(a, sp, ham, Cin, sigma, nrhs, precision, map, in_exp);
@@ -781,16 +802,42 @@ static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Ci
         t.tc_er = nullptr;
         t.status = nullptr;
         t.phase1_done = ham->ev_stop;
+        t.phases = 3;
+        t.g_begin = 0;
+        t.g_end = a.nc;
         *stop_recorded = ham->ev_stop != nullptr;
+        const bool mixed = precision == FOCK_PREC_F32_MIXED;
         if (path == FOCK_PATH_TWOPHASE_TC) {
-          const bool mixed = precision == FOCK_PREC_F32_MIXED;
           t.tc_a = mixed ? ham->d_tc_ma : ham->d_tc_a;
           t.tc_er = mixed ? ham->d_tc_mer : ham->d_tc_er;
           t.status = (int *)ws + 2;
           if (mixed) FOCK_CUDA_TRY(cudaMemsetAsync(t.status, 0, sizeof(int), stream));
-          return fock_launch_twophase_tc(t, mixed, sp->device, stream);
         }
-        return fock_launch_twophase(t, precision == FOCK_PREC_F32_MIXED, sp->device, stream);
+        auto launch = [&]() {
+          return path == FOCK_PATH_TWOPHASE_TC ? fock_launch_twophase_tc(t, mixed, sp->device, stream)
+                                               : fock_launch_twophase(t, mixed, sp->device, stream);
+        };
+        if (!ov) return launch();
+        // phase 1, then phase 2 in chunks, each chunk of sigma copied out behind it
+        t.phases = 1;
+        int st = launch();
+        const uint32_t chunk = (a.nc + kHostChunks - 1) / kHostChunks;
+        for (int i = 0; i < kHostChunks && !st; ++i) {
+          t.phases = 2;
+          t.g_begin = (uint32_t)i * chunk;
+          t.g_end = t.g_begin + chunk < a.nc ? t.g_begin + chunk : a.nc;
+          if (t.g_begin >= t.g_end) break;
+          st = launch();
+          if (st) break;
+          FOCK_CUDA_TRY(cudaEventRecord(ov->ev[i], stream));
+          FOCK_CUDA_TRY(cudaStreamWaitEvent(ov->copy, ov->ev[i], 0));
+          FOCK_CUDA_TRY(cudaMemcpyAsync((char *)ov->sigma_host + (size_t)t.g_begin * ov->row_bytes,
+                                        (const char *)sigma + (size_t)t.g_begin * ov->row_bytes,
+                                        (size_t)(t.g_end - t.g_begin) * ov->row_bytes, cudaMemcpyDeviceToHost,
+                                        ov->copy));
+        }
+        if (!st) ov->done = true;
+        return st;
       }
       case FOCK_PATH_NN:
         // nearest-neighbour operators: one diagonal term and two hops per bond
@@ -891,12 +938,24 @@ extern "C" int fock_apply_H_host(const fock_space *sp, const fock_ham *ham, cons
     st = grow_ws(H, need);
     if (st) return st;
   }
+  if (!H->hb_copy) {
+    FOCK_CUDA_TRY(cudaStreamCreateWithFlags(&H->hb_copy, cudaStreamNonBlocking));
+    for (int i = 0; i < kHostChunks; ++i)
+      FOCK_CUDA_TRY(cudaEventCreateWithFlags(&H->hb_ev[i], cudaEventDisableTiming));
+  }
   cudaStream_t s = (cudaStream_t)stream;
   FOCK_CUDA_TRY(cudaMemcpyAsync(H->hb_in, C_host, bytes, cudaMemcpyHostToDevice, s));
-  st = fock_apply_internal(sp, ham, H->hb_in, H->hb_out, nrhs, precision, arm, H->ws, H->ws_bytes, s);
-  if (st) return st;
-  FOCK_CUDA_TRY(cudaMemcpyAsync(sigma_host, H->hb_out, bytes, cudaMemcpyDeviceToHost, s));
+  HostOverlap ov{sigma_host, H->hb_copy, H->hb_ev, (size_t)nrhs * elem, false};
+  int path = FOCK_PATH_AUTO;
+  tuned_choice(ham, nrhs, precision, arm, path);
+  st = apply_path(sp, ham, H->hb_in, H->hb_out, nrhs, precision, arm, H->ws, H->ws_bytes, s, path, &ov);
+  if (st) {
+    cudaStreamSynchronize(H->hb_copy);
+    return st;
+  }
+  if (!ov.done) FOCK_CUDA_TRY(cudaMemcpyAsync(sigma_host, H->hb_out, bytes, cudaMemcpyDeviceToHost, s));
   FOCK_CUDA_TRY(cudaStreamSynchronize(s));
+  FOCK_CUDA_TRY(cudaStreamSynchronize(H->hb_copy));
   if (precision == FOCK_PREC_F64) {
     int status = 0;
     FOCK_CUDA_TRY(cudaMemcpy(&status, (const int *)H->ws + 2, sizeof(int), cudaMemcpyDeviceToHost));

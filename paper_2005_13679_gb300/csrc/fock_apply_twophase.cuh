@@ -36,6 +36,8 @@ struct TwoPhaseArgs {
   const int *tc_er;               // its row exponents
   int *status;                    // nonzero after a bounded wait of phase 1 expired, or NULL
   cudaEvent_t phase1_done;        // recorded between the two phases when non-null (profiling hook)
+  int phases;                     // 1: phase 1 only, 2: phase 2 only, 3: both
+  uint32_t g_begin, g_end;        // configurations phase 2 computes
 };
 
 template <int M>
@@ -310,11 +312,12 @@ fock_twophase_sigma_df(const TwoPhaseArgs t) {
   // Y is incomplete if phase 1 gave up a wait: report NaN rather than a wrong sigma
   const bool failed = t.status && *(volatile const int *)t.status;
 
-  for (uint32_t tile = blockIdx.x * (uint32_t)nt; tile < nc; tile += gridDim.x * (uint32_t)nt) {
+  const uint32_t g_end = t.g_end;
+  for (uint32_t tile = t.g_begin + blockIdx.x * (uint32_t)nt; tile < g_end; tile += gridDim.x * (uint32_t)nt) {
     const uint32_t g = tile + tid;
-    const bool live = g < nc;
+    const bool live = g < g_end;
     int S[M], n[M];
-    fock_decode_fast<M>(live ? g : nc - 1u, a.N, nc, s_sat, a.xdim, S);
+    fock_decode_fast<M>(live ? g : g_end - 1u, a.N, nc, s_sat, a.xdim, S);
 #pragma unroll
     for (int m = 0; m < M; ++m) n[m] = S[m] - (m > 0 ? S[m - 1] : 0);
     float2 sq0[M], sq1[M];                                  // sqrt(n_m), sqrt(n_m - 1) as pairs
@@ -441,11 +444,12 @@ fock_twophase_sigma_mixed(const TwoPhaseArgs t) {
   const float out_scale = (t.status && *(volatile const int *)t.status) ? __int_as_float(0x7fc00000)
                                                                         : (float)a.out_scale;
 
-  for (uint32_t tile = blockIdx.x * (uint32_t)nt; tile < nc; tile += gridDim.x * (uint32_t)nt) {
+  const uint32_t g_end = t.g_end;
+  for (uint32_t tile = t.g_begin + blockIdx.x * (uint32_t)nt; tile < g_end; tile += gridDim.x * (uint32_t)nt) {
     const uint32_t g = tile + tid;
-    const bool live = g < nc;
+    const bool live = g < g_end;
     int S[M], n[M];
-    fock_decode_fast<M>(live ? g : nc - 1u, a.N, nc, s_sat, a.xdim, S);
+    fock_decode_fast<M>(live ? g : g_end - 1u, a.N, nc, s_sat, a.xdim, S);
 #pragma unroll
     for (int m = 0; m < M; ++m) n[m] = S[m] - (m > 0 ? S[m - 1] : 0);
     uint32_t P1[M], P2[M];

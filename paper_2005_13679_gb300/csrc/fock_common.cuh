@@ -137,9 +137,12 @@ struct fock_ham {
   int8_t tuned_arm[3][2];
   // profiling hook (fock_apply_set_events)
   cudaEvent_t ev_start, ev_stop;
-  // buffers for fock_apply_H_host
+  // buffers for fock_apply_H_host, and the stream and events that copy sigma
+  // out by chunks while phase 2 of the two-phase path runs
   void *hb_in, *hb_out;
   size_t hb_bytes;
+  cudaStream_t hb_copy;
+  cudaEvent_t hb_ev[8];
 };
 
 // Launch helpers implemented in fock_apply.cu and used by fock_lanczos.cu.

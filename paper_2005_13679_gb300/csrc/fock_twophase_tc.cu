@@ -146,22 +146,26 @@ size_t fock_tc_smem(int M, int xdim, int nsq, bool mixed) {
 template <int M, class Pol>
 static int launch_tc(const TwoPhaseArgs &t, int dev, cudaStream_t s) {
   const ApplyArgs<uint32_t> &a = t.a;
-  const size_t smem = tc_smem_of<Pol, M>(a.xdim, a.nsq).total;
-  cudaError_t e = cudaFuncSetAttribute(fock_twophase_x_tc<M, Pol>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return fock_cuda_status(e);
-  const uint64_t total = (uint64_t)t.nc2 * (uint64_t)a.nrhs;
-  const uint64_t tiles = (total + kTcCols - 1) / kTcCols;
-  uint64_t grid = (uint64_t)fock_get_sm_count(dev);
-  if (grid > tiles) grid = tiles;
-  if (grid < 1) grid = 1;
-  fock_twophase_x_tc<M, Pol><<<(unsigned)grid, kTcThreads, smem, s>>>(t);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return fock_cuda_status(e);
-  if (t.phase1_done) FOCK_CUDA_TRY(cudaEventRecord(t.phase1_done, s));
+  if (t.phases & 1) {
+    const size_t smem = tc_smem_of<Pol, M>(a.xdim, a.nsq).total;
+    cudaError_t e = cudaFuncSetAttribute(fock_twophase_x_tc<M, Pol>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return fock_cuda_status(e);
+    const uint64_t total = (uint64_t)t.nc2 * (uint64_t)a.nrhs;
+    const uint64_t tiles = (total + kTcCols - 1) / kTcCols;
+    uint64_t grid = (uint64_t)fock_get_sm_count(dev);
+    if (grid > tiles) grid = tiles;
+    if (grid < 1) grid = 1;
+    fock_twophase_x_tc<M, Pol><<<(unsigned)grid, kTcThreads, smem, s>>>(t);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fock_cuda_status(e);
+    if (t.phase1_done) FOCK_CUDA_TRY(cudaEventRecord(t.phase1_done, s));
+  }
+  if (!(t.phases & 2)) return FOCK_OK;
+  const uint32_t n = t.g_end - t.g_begin;
   if (std::is_same<Pol, TcPolMixed<M>>::value)
-    return fock_launch_grid(fock_twophase_sigma_mixed<M>, t, a.nc, twophase_sigma_smem(a.rows, a.xdim, a.nsq), dev, s);
-  return fock_launch_grid(fock_twophase_sigma_df<M>, t, a.nc, twophase_sigma_smem(a.rows, a.xdim, a.nsq), dev, s);
+    return fock_launch_grid(fock_twophase_sigma_mixed<M>, t, n, twophase_sigma_smem(a.rows, a.xdim, a.nsq), dev, s);
+  return fock_launch_grid(fock_twophase_sigma_df<M>, t, n, twophase_sigma_smem(a.rows, a.xdim, a.nsq), dev, s);
 }
 
 int fock_launch_twophase_tc(const TwoPhaseArgs &t, bool mixed, int dev, cudaStream_t s) {

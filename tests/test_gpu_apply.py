@@ -231,17 +231,30 @@ def test_terms_count_matches_oracle_columns(torch):
         assert H.terms == expect
 
 
-def test_host_buffer_entry_point(torch):
-    N, M = 8, 6
-    h, W = hw("generic", M)
+@pytest.mark.parametrize("prec", [fock.FOCK_PREC_F64, fock.FOCK_PREC_F32_MIXED])
+@pytest.mark.parametrize("N,M,kind,nrhs,pinned", [
+    (8, 6, "generic", 1, True),      # two-phase on the tensor cores, sigma copied out by chunks
+    (9, 6, "generic", 3, False),     # several right-hand sides, pageable host memory
+    (6, 8, "generic", 1, True),      # two-phase with FP32 phase 1
+    (10, 5, "ll", 2, True),          # sparse kernel: one copy after the apply
+])
+def test_host_buffer_entry_point(torch, N, M, kind, nrhs, pinned, prec):
+    h, W = hw(kind, M)
     sp = fock.Space(N, M)
     H = fock.Hamiltonian(sp, h, W)
-    C = inputs.random_state(sp.nc, 2)
-    ref = oracle.apply_push(N, M, h, W, C)
-    Ch = torch.from_numpy(C).pin_memory()
-    out = torch.empty_like(Ch).pin_memory()
-    fock.fock_apply_H_host(sp.handle, H.handle, Ch, out)
-    assert rel(out.numpy(), ref) <= 1e-12
+    C = np.stack([inputs.random_state(sp.nc, 2 + j) for j in range(nrhs)], axis=1)
+    Ch = torch.from_numpy(np.ascontiguousarray(C))
+    if prec == fock.FOCK_PREC_F32_MIXED:
+        Ch = Ch.to(torch.complex64)
+    out = torch.empty_like(Ch)
+    if pinned:
+        Ch, out = Ch.pin_memory(), out.pin_memory()
+    fock.fock_apply_H_host(sp.handle, H.handle, Ch, out, nrhs=nrhs, precision=prec)
+    dev_out = H.apply(Ch.cuda(), nrhs=nrhs, precision=prec).cpu()
+    assert torch.equal(out, dev_out)              # same kernels, same sums
+    for j in range(nrhs):
+        ref = oracle.apply_push(N, M, h, W, C[:, j])
+        assert rel(out.numpy().reshape(sp.nc, nrhs)[:, j].astype(np.complex128), ref) <= TOL[prec]
 
 
 # ---------------------------------------------------------------------------
