@@ -156,35 +156,105 @@ struct SecArgs {
   double out_scale;
 };
 
-// One thread per sector configuration.  The thread's occupations and prefix
-// sums live in shared memory columns (indexed by runtime orbitals without
-// local-memory arrays); the term lists, coefficients and square roots are
-// staged once per block.
+// A term's prefix-sum change.  Removing (k, q) and adding (s, l) changes
+// (S_m, Q_m) by a constant (dS, dQ) between consecutive positions of the
+// sorted list {k, q, s, l}: at most three segments of orbitals, each with a
+// constant offset dS (Q + 1) + dQ into a plane of the T table.  Computed once
+// per block for every term, clamped to the orbitals 1..M-2 of the hash.
+struct SecSeg {
+  int8_t st[3], en[3];
+  int16_t pad;
+  int32_t off[3];
+};
+
+__device__ __forceinline__ SecSeg sec_segments(int k, int q, int s, int l, int M, int qd) {
+  int p[4] = {k, q, s, l}, d[4] = {-1, -1, 1, 1};
+  const int np = q < 0 ? 2 : 4;
+  if (q < 0) {                                         // one-body: remove k, add l
+    p[1] = l;
+    d[1] = 1;
+  }
+  for (int i = 1; i < np; ++i)                         // insertion sort of the positions
+    for (int j = i; j > 0 && p[j - 1] > p[j]; --j) {
+      const int tp = p[j], td = d[j];
+      p[j] = p[j - 1];
+      d[j] = d[j - 1];
+      p[j - 1] = tp;
+      d[j - 1] = td;
+    }
+  SecSeg g;
+  g.pad = 0;
+  int dS = 0, dQ = 0;
+  for (int i = 0; i < 3; ++i) {
+    int a = 0, b = 0;
+    if (i < np - 1) {
+      dS += d[i];
+      dQ += p[i] * d[i];
+      a = max(p[i], 1);
+      b = min(p[i + 1], M - 1);
+    }
+    g.st[i] = (int8_t)a;
+    g.en[i] = (int8_t)(b > a ? b : a);
+    g.off[i] = dS * qd + dQ;
+  }
+  return g;
+}
+
+// Shared-memory layout of the sector kernel, every section 16-byte aligned.
+struct SecSmem {
+  size_t coef, it, seg, sq, rem, add, n, total;
+  __host__ __device__ SecSmem(int M, int nadd, int nsq, int nrem, size_t coef_bytes, size_t amp_bytes) {
+    size_t o = 0;
+    coef = o; o = fock_align16(o + coef_bytes * nadd);
+    it = o;   o = fock_align16(o + 8 * (size_t)M * kSecThreads);
+    seg = o;  o = fock_align16(o + sizeof(SecSeg) * nadd);
+    sq = o;   o = fock_align16(o + amp_bytes * nsq);
+    rem = o;  o = fock_align16(o + sizeof(FockRemoval) * nrem);
+    add = o;  o = fock_align16(o + sizeof(FockAddition) * nadd);
+    n = o;    o = fock_align16(o + 4 * (size_t)M * kSecThreads);
+    total = o;
+  }
+};
+
+// One thread per sector configuration.  Per orbital m the thread keeps, in a
+// shared-memory column, the flat index of T_m(S_m, Q_m) and its value; a
+// target's rank is gamma minus sum over the term's segments of
+// T[index_m + offset] - T_m(S_m, Q_m).  Occupations sit in another column
+// (runtime orbital indices, no local-memory arrays).  The term lists and
+// segments, coefficients and square roots are staged once per block.
 template <int M, class P>
 __global__ void __launch_bounds__(kSecThreads) fock_sector_apply_kernel(const SecArgs a) {
   using amp_t = typename P::amp_t;
   using coef_t = typename P::coef_t;
   using vec_t = typename P::vec_t;
   extern __shared__ __align__(16) unsigned char smem[];
-  coef_t *s_coef = (coef_t *)smem;                                   // [nadd]
-  amp_t *s_sq = (amp_t *)(s_coef + a.nadd);                          // [nsq]
-  FockRemoval *s_rem = (FockRemoval *)(s_sq + a.nsq + (a.nsq & 1));  // [nrem]
-  FockAddition *s_add = (FockAddition *)(s_rem + a.nrem);            // [nadd]
-  int *s_n = (int *)(s_add + a.nadd + (a.nadd & 1));                 // [M][threads]
-  int *s_S = s_n + M * kSecThreads;
-  int *s_Q = s_S + M * kSecThreads;
-  uint32_t *s_t = (uint32_t *)(s_Q + M * kSecThreads);
-  for (int i = threadIdx.x; i < a.nadd; i += blockDim.x) {
-    s_coef[i] = ((const coef_t *)a.coef)[i];
-    s_add[i] = a.add[i];
-  }
+  const SecSmem L(M, a.nadd, a.nsq, a.nrem, sizeof(coef_t), sizeof(amp_t));
+  coef_t *s_coef = (coef_t *)(smem + L.coef);                        // [nadd]
+  int2 *s_it = (int2 *)(smem + L.it);                                // [M][threads]: (T index, T value)
+  SecSeg *s_seg = (SecSeg *)(smem + L.seg);                          // [nadd]
+  amp_t *s_sq = (amp_t *)(smem + L.sq);                              // [nsq]
+  FockRemoval *s_rem = (FockRemoval *)(smem + L.rem);                // [nrem]
+  FockAddition *s_add = (FockAddition *)(smem + L.add);              // [nadd]
+  int *s_n = (int *)(smem + L.n);                                    // [M][threads]
+  const int qd = a.tb.Q + 1;
   for (int i = threadIdx.x; i < a.nsq; i += blockDim.x) s_sq[i] = ((const amp_t *)a.sq)[i];
   for (int i = threadIdx.x; i < a.nrem; i += blockDim.x) s_rem[i] = a.rem[i];
+  __syncthreads();
+  for (int r = 0; r < a.nrem; ++r) {
+    const FockRemoval R = s_rem[r];
+    for (int i = R.a_beg + threadIdx.x; i < R.a_end; i += blockDim.x) {
+      const FockAddition ad = a.add[i];
+      s_coef[i] = ((const coef_t *)a.coef)[i];
+      s_add[i] = ad;
+      s_seg[i] = R.size == 2 ? sec_segments(R.k, R.q, ad.s, ad.l, M, qd) : sec_segments(R.k, -1, -1, ad.l, M, qd);
+    }
+  }
   __syncthreads();
   const int tid = threadIdx.x;
   double out_scale = a.out_scale;
   if (a.in_exp) out_scale *= fock_pow2(__ldg(a.in_exp));
   const vec_t *__restrict__ C = (const vec_t *)a.C;
+  const uint32_t *__restrict__ T = a.tb.T;
   const int nrhs = a.nrhs;
 
   for (uint32_t g = blockIdx.x * blockDim.x + tid; g < a.ns; g += gridDim.x * blockDim.x) {
@@ -197,9 +267,10 @@ __global__ void __launch_bounds__(kSecThreads) fock_sector_apply_kernel(const Se
         S += n[m];
         W += m * n[m];
         s_n[m * kSecThreads + tid] = n[m];
-        s_S[m * kSecThreads + tid] = S;
-        s_Q[m * kSecThreads + tid] = W;
-        s_t[m * kSecThreads + tid] = (m >= 1 && m <= M - 2) ? a.tb.t(m, S, W) : 0u;
+        if (m >= 1 && m <= M - 2) {
+          const int idx = ((m - 1) * (a.tb.N + 1) + S) * qd + W;
+          s_it[m * kSecThreads + tid] = make_int2(idx, (int)__ldg(T + idx));
+        }
       }
     }
     for (int j = 0; j < nrhs; ++j) {
@@ -220,31 +291,27 @@ __global__ void __launch_bounds__(kSecThreads) fock_sector_apply_kernel(const Se
         if constexpr (P::kInner) P::izero(inner);
         for (int e = R.a_beg; e < R.a_end; ++e) {
           const FockAddition ad = s_add[e];
-          const int s = two ? ad.s : -1, l = ad.l;
+          const int l = ad.l;
           // occupations after the removal, then the addition amplitude
           const int nl = s_n[l * kSecThreads + tid] - (l == k) - (two && l == q);
           amp_t amp;
-          int lo, hi;
           if (two) {
+            const int s = ad.s;
             const int ns_ = s_n[s * kSecThreads + tid] - (s == k) - (s == q);
             amp = P::amul(P::amul(A, s_sq[ns_ + 1]), s_sq[nl + 1 + (s == l)]);
-            lo = min(k, s);
-            hi = max(q, l);
           } else {
             amp = P::amul(A, s_sq[nl + 1]);
-            lo = min(k, l);
-            hi = max(k, l);
           }
-          // target rank: gamma minus the change of sum_m T_m(S_m, Q_m) on [lo, hi)
+          // target rank: gamma minus the change of sum_m T_m over the segments
+          const SecSeg sg = s_seg[e];
           uint32_t diff = 0;
-          int dS = 0, dQ = 0;
-          for (int m = lo; m < hi; ++m) {
-            const int dn = (m == l) + (two && m == s) - (m == k) - (two && m == q);
-            dS += dn;
-            dQ += m * dn;
-            if (m >= 1 && m <= M - 2)
-              diff += a.tb.t(m, s_S[m * kSecThreads + tid] + dS, s_Q[m * kSecThreads + tid] + dQ) -
-                      s_t[m * kSecThreads + tid];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            const int off = sg.off[i];
+            for (int m = sg.st[i]; m < sg.en[i]; ++m) {
+              const int2 it = s_it[m * kSecThreads + tid];
+              diff += __ldg(T + (it.x + off)) - (uint32_t)it.y;
+            }
           }
           const uint32_t t = g - diff;
           const coef_t K = P::scale(s_coef[e], amp);
@@ -264,8 +331,7 @@ template <int M, class P>
 int launch_sector_m(const SecArgs &a, int device, cudaStream_t s) {
   using amp_t = typename P::amp_t;
   using coef_t = typename P::coef_t;
-  const size_t smem = sizeof(coef_t) * a.nadd + sizeof(amp_t) * (a.nsq + 1) + sizeof(FockRemoval) * a.nrem +
-                      sizeof(FockAddition) * (a.nadd + 1) + 16 * (size_t)M * kSecThreads + 64;
+  const size_t smem = SecSmem(M, a.nadd, a.nsq, a.nrem, sizeof(coef_t), sizeof(amp_t)).total;
   auto kern = fock_sector_apply_kernel<M, P>;
   if (smem > 48 * 1024) FOCK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
