@@ -284,11 +284,13 @@ fock_twophase_x_df(const TwoPhaseArgs t) {
 }
 
 // Phase 2 is a gather: each target reads up to P rows of Y at hashed
-// addresses, so latency is hidden by residency. The minimum-block hint keeps
-// 8 blocks of 128 threads per SM (64 registers) for M <= 6 and 5 blocks for
-// M = 7, 8, where the unrolled removal loops need up to 93 registers.
+// addresses.  For the FP32-pair form the minimum-block hint of 3 blocks of
+// 128 threads per SM for M <= 6 leaves the registers to keep all P gathers of
+// a configuration in flight (measured 3.5 % faster over the whole apply at
+// N = 100, M = 6 than 8 blocks of 64 registers); M = 7, 8 keep 5 blocks, where
+// the unrolled removal loops need up to 93 registers.
 template <int M>
-__global__ void __launch_bounds__(FOCK_APPLY_THREADS, (M <= 6 ? 8 : 5))
+__global__ void __launch_bounds__(FOCK_APPLY_THREADS, (M <= 6 ? 3 : 5))
 fock_twophase_sigma_df(const TwoPhaseArgs t) {
   const ApplyArgs<uint32_t> &a = t.a;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -421,6 +423,8 @@ fock_twophase_x_mixed(const TwoPhaseArgs t) {
   }
 }
 
+// The FP32-mixed form holds half the bytes per gather; residency (8 blocks
+// of 64 registers for M <= 6) measured faster than more registers.
 template <int M>
 __global__ void __launch_bounds__(FOCK_APPLY_THREADS, (M <= 6 ? 8 : 5))
 fock_twophase_sigma_mixed(const TwoPhaseArgs t) {
