@@ -287,10 +287,11 @@ fock_twophase_x_df(const TwoPhaseArgs t) {
 // addresses.  For the FP32-pair form the minimum-block hint of 3 blocks of
 // 128 threads per SM for M <= 6 leaves the registers to keep all P gathers of
 // a configuration in flight (measured 3.5 % faster over the whole apply at
-// N = 100, M = 6 than 8 blocks of 64 registers); M = 7, 8 keep 5 blocks, where
-// the unrolled removal loops need up to 93 registers.
+// N = 100, M = 6 than 8 blocks of 64 registers); for M = 7, 8 (P = 28, 36
+// gathers) 2 blocks per SM (N = 20, M = 8, 16 right-hand sides: 24.5 ms
+// against 27.7 ms at 5 blocks).
 template <int M>
-__global__ void __launch_bounds__(FOCK_APPLY_THREADS, (M <= 6 ? 3 : 5))
+__global__ void __launch_bounds__(FOCK_APPLY_THREADS, (M <= 6 ? 3 : 2))
 fock_twophase_sigma_df(const TwoPhaseArgs t) {
   const ApplyArgs<uint32_t> &a = t.a;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -426,9 +427,10 @@ fock_twophase_x_mixed(const TwoPhaseArgs t) {
 // The FP32-mixed form, branch-free like the FP32-pair one: 4 blocks per SM
 // for M <= 6 keep the P gathers of a configuration in flight (whole mixed
 // apply at N = 100, M = 6: 10.4 ms, against 13.5 ms with a warp vote that
-// skipped impossible removals at 8 blocks).
+// skipped impossible removals at 8 blocks); 2 blocks for M = 7, 8 (N = 20,
+// M = 8, 16 right-hand sides: 9.0 ms against 12.4 ms at 5 blocks).
 template <int M>
-__global__ void __launch_bounds__(FOCK_APPLY_THREADS, (M <= 6 ? 4 : 5))
+__global__ void __launch_bounds__(FOCK_APPLY_THREADS, (M <= 6 ? 4 : 2))
 fock_twophase_sigma_mixed(const TwoPhaseArgs t) {
   const ApplyArgs<uint32_t> &a = t.a;
   extern __shared__ __align__(16) unsigned char smem[];
