@@ -96,6 +96,52 @@ def dist_env():
     return ws, rank, local
 
 
+def dist_init(ws: int, local: int, backend: str = "nccl"):
+    """Process group for N > 1 ranks (one per GPU, rendezvous from the
+    MASTER_* environment); returns the barrier the timed region uses."""
+    if ws == 1:
+        return lambda: None
+    import torch
+    import torch.distributed as dist
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist.init_process_group(backend)
+    return lambda: dist.barrier()
+
+
+def dist_reduce(x: float, op: str = "max") -> float:
+    """x reduced over the ranks (max or sum); x itself for one rank."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return t.item()
+
+
+def dist_finish() -> None:
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.destroy_process_group()
+
+
+def shard(items, rank: int, ws: int) -> list:
+    """Round-robin share of one rank: every item goes to exactly one rank."""
+    return list(items)[rank::ws]
+
+
+def batch_units(ws: int, per_rank: int = 64):
+    """The independent Lieb-Liniger problems of the batch workload for ws ranks:
+    per_rank * ws instances from one seeded stream (the first 64 are the
+    single-GPU batch), each with its index in the stream (its state seed)."""
+    from paper_2005_13679_gb300 import inputs
+    return list(enumerate(inputs.uneven_ll_batch(count=per_rank * ws)))
+
+
 # --------------------------------------------------------------------------
 # CPU oracle timing (bounded sample of rows)
 # --------------------------------------------------------------------------
@@ -311,7 +357,9 @@ def run_sector(args, w):
 
     from paper_2005_13679_gb300 import fock
     ws, rank, local = dist_env()
-    torch.cuda.set_device(local if ws > 1 else 0)
+    barrier = dist_init(ws, local)          # replicas: every rank the same sector
+    if ws == 1:
+        torch.cuda.set_device(0)
     fock.load()
     peaks, peak_src = load_peaks()
     h, W = w.hamiltonian()
@@ -350,7 +398,7 @@ def run_sector(args, w):
     for _ in range(args.warmup):
         step()
     counter["i"] = -1
-    ms = time_steps(torch, step_timed, args.steps, 0, lambda: None)
+    ms = dist_reduce(time_steps(torch, step_timed, args.steps, 0, barrier), "max")
     clocks = clk.stop()
     fock.fock_apply_set_events(H.handle, None, None)
     kernel_ms = sum(a_.elapsed_time(b_) for a_, b_ in kev) / len(kev)
@@ -411,6 +459,7 @@ def run_sector(args, w):
                           "status": int(st), "precision": "f64"}
     if rank == 0:
         print(json.dumps(out), flush=True)
+    dist_finish()
     return 0
 
 
@@ -432,27 +481,35 @@ def run_batch(args):
 
     from paper_2005_13679_gb300 import fock, inputs
     ws, rank, local = dist_env()
-    torch.cuda.set_device(local if ws > 1 else 0)
+    barrier = dist_init(ws, local)
+    if ws == 1:
+        torch.cuda.set_device(0)
     fock.load()
-    inst = inputs.uneven_ll_batch()
+    # weak scaling: 64 independent problems per rank, dealt round-robin from
+    # one seeded stream of 64 x ranks (no collective on the data path)
+    mine = shard(batch_units(ws), rank, ws)
+    inst = [x for _, x in mine]
     probs = [(x.N, x.M) + inputs.lieb_liniger_hw(x.M, x.g) for x in inst]
     B = fock.Batch(probs)
     C = np.empty(B.total, dtype=np.complex128)
-    for i in range(B.count):
-        C[B.offsets[i]:B.offsets[i + 1]] = inputs.random_state(int(B.offsets[i + 1] - B.offsets[i]), 500 + i)
+    for i, (gi, _) in enumerate(mine):
+        C[B.offsets[i]:B.offsets[i + 1]] = inputs.random_state(int(B.offsets[i + 1] - B.offsets[i]), 500 + gi)
     Cd = torch.from_numpy(C).cuda()
     sig = torch.empty_like(Cd)
     cache = os.path.join(tempfile.gettempdir(), "fock_batch_tune.txt")
     tiles, blocks = B.autotune(Cd, sig, fock.FOCK_PREC_F64, cache_path=cache)
     clk = ClockSampler(local)
     clk.start()
-    ms = time_steps(torch, lambda: B.apply(Cd, sig, fock.FOCK_PREC_F64), args.steps, args.warmup, lambda: None)
+    ms = time_steps(torch, lambda: B.apply(Cd, sig, fock.FOCK_PREC_F64), args.steps, args.warmup, barrier)
     clocks = clk.stop()
+    ms_all = dist_reduce(ms, "max")
+    terms_all = dist_reduce(float(B.terms), "sum")
     out = {
-        "metric": METRIC, "value": B.terms * ws / (ms * 1e-3), "unit": "config-terms/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "metric": METRIC, "value": terms_all / (ms_all * 1e-3), "unit": "config-terms/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPE["f64"], "data": "synthetic",
-        "config": {"workload": "ll_batch64", "instances": B.count, "total_nc": B.total,
+        "config": {"workload": "ll_batch64", "instances": B.count * ws, "instances_per_rank": B.count,
+                   "total_nc_rank0": B.total,
                    "tiles_per_item": tiles, "blocks_per_sm": blocks, "l2": "inputs larger than L2 (no flush)"},
         "gpu_launches": 3 * args.steps, "clocks": clocks,
     }
@@ -472,6 +529,7 @@ def run_batch(args):
                           "converged": int(np.sum(R / np.abs(E) < 1e-6))}
     if rank == 0:
         print(json.dumps(out), flush=True)
+    dist_finish()
     return 0
 
 
@@ -507,14 +565,9 @@ def main():
 
     from paper_2005_13679_gb300 import fock
     ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-        barrier = lambda: dist.barrier()
-    else:
+    barrier = dist_init(ws, local)
+    if ws == 1:
         torch.cuda.set_device(0)
-        barrier = lambda: None
     fock.load()
     peaks, peak_src = load_peaks()
 
@@ -559,12 +612,7 @@ def main():
     clocks = clk.stop()
     fock.fock_apply_set_events(H.handle, None, None)
     kernel_ms = sum(a_.elapsed_time(b_) for a_, b_ in kev) / len(kev)
-    ms_all = ms
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_all = t.item()
+    ms_all = dist_reduce(ms, "max")
     terms = H.terms * w.nrhs
     value = terms * ws / (ms_all * 1e-3)
     applies = ws * w.nrhs / (ms_all * 1e-3)
@@ -685,9 +733,7 @@ def main():
                                "kind": "oracle", "sample": f"{n} random rows of sigma (row form), {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(out), flush=True)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    dist_finish()
     return 0
 
 
