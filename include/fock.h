@@ -58,7 +58,7 @@ extern "C" {
 #define FOCK_ERR_ALIAS          -7   /* input and output buffers overlap         */
 #define FOCK_ERR_CUDA           -8   /* a CUDA runtime call failed               */
 #define FOCK_ERR_NOCONV         -9   /* Lanczos stopped before the tolerance     */
-#define FOCK_ERR_UNSUPPORTED   -10   /* combination not provided by this build   */
+#define FOCK_ERR_UNSUPPORTED   -10   /* combination the library does not provide  */
 #define FOCK_ERR_TIMEOUT       -11   /* a bounded device wait gave up            */
 #define FOCK_ERR_NOT_BUILT     -12   /* jump maps requested but not built        */
 #define FOCK_ERR_DEVICE        -13   /* object used on another device            */
