@@ -284,13 +284,19 @@ def executed_terms(w, h, W):
     return nc(N - 2) * int(np.count_nonzero(R))
 
 
+def sources_digest(paths):
+    """First 16 hex digits of the SHA-256 of the listed source files (paths
+    relative to the package directory), in the order given."""
+    import hashlib
+    pkg = os.path.join(ROOT, "paper_2005_13679_gb300")
+    return hashlib.sha256(b"".join(open(os.path.join(pkg, f), "rb").read() for f in paths)).hexdigest()[:16]
+
+
 def load_traffic(workload, precision):
     """DRAM bytes per launch of the main kernel from the committed ncu summary of
-    this workload, if its kernel sources still match (else None)."""
-    import glob
-    import hashlib
-    src = sorted(glob.glob(os.path.join(ROOT, "paper_2005_13679_gb300", "csrc", "*.cu*")))
-    digest = hashlib.sha256(b"".join(open(f, "rb").read() for f in src)).hexdigest()[:16]
+    this workload, if the kernel's translation unit and the headers it includes
+    (listed in the summary) still match the sources the counters were taken
+    from (else None)."""
     path = os.path.join(ROOT, "profiles", f"traffic_{workload}_{precision}.txt")
     if not os.path.exists(path):
         return None
@@ -299,11 +305,11 @@ def load_traffic(workload, precision):
         if ":" in line:
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("csrc_sha256_16") != digest:
-        return None
     try:
+        if sources_digest(vals["sources"].split()) != vals["sources_sha256_16"]:
+            return None
         return float(vals["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
+    except (KeyError, ValueError, OSError):
         return None
 
 

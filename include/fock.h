@@ -206,7 +206,9 @@ int fock_apply_path(const fock_space *sp, const fock_ham *ham, int32_t nrhs, int
 /* Pin the path (and arm) later applies with this precision and right-hand-
  * side class (nrhs == 1 or > 1) take when the caller passes FOCK_ARM_AUTO
  * (or the same arm).  A path that cannot serve a call falls back to the
- * built-in order for that call.  FOCK_PATH_AUTO clears the choice. */
+ * built-in order for that call; a choice on FOCK_ARM_MAPS lapses while the
+ * jump maps are not built (freed, or never built).  FOCK_PATH_AUTO clears
+ * the choice. */
 int fock_apply_set_path(fock_ham *ham, int32_t nrhs, int precision, int path, int arm);
 
 typedef struct fock_tuning {

@@ -687,11 +687,14 @@ static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Ci
 // The tuned (path, arm) of fock_autotune for this precision and right-hand-side
 // count class, when the caller leaves the arm to the library (or asks for the
 // tuned arm).
-static void tuned_choice(const fock_ham *ham, int nrhs, int precision, int &arm, int &path) {
+static void tuned_choice(const fock_space *sp, const fock_ham *ham, int nrhs, int precision, int &arm, int &path) {
   path = FOCK_PATH_AUTO;
   const int cls = nrhs > 1 ? 1 : 0;
   const int tp = ham->tuned_path[precision][cls], ta = ham->tuned_arm[precision][cls];
   if (tp == FOCK_PATH_AUTO) return;
+  // a choice on the jump-map arm lapses while the maps are not built
+  const bool two_body = ham->nrem > 0 && ham->h_rem[0].size == 2;
+  if (ta == FOCK_ARM_MAPS && !(two_body ? sp->d_j2 : sp->d_j1)) return;
   if (arm == FOCK_ARM_AUTO) arm = ta;
   if (arm == ta) path = tp;
 }
@@ -704,7 +707,7 @@ int fock_apply_internal(const fock_space *sp, const fock_ham *ham, const void *C
                         int nrhs, int precision, int arm, void *ws, size_t ws_bytes,
                         cudaStream_t stream) {
   int path = FOCK_PATH_AUTO;
-  tuned_choice(ham, nrhs, precision, arm, path);
+  tuned_choice(sp, ham, nrhs, precision, arm, path);
   return apply_path(sp, ham, C, sigma, nrhs, precision, arm, ws, ws_bytes, stream, path);
 }
 
@@ -947,7 +950,7 @@ extern "C" int fock_apply_H_host(const fock_space *sp, const fock_ham *ham, cons
   FOCK_CUDA_TRY(cudaMemcpyAsync(H->hb_in, C_host, bytes, cudaMemcpyHostToDevice, s));
   HostOverlap ov{sigma_host, H->hb_copy, H->hb_ev, (size_t)nrhs * elem, false};
   int path = FOCK_PATH_AUTO;
-  tuned_choice(ham, nrhs, precision, arm, path);
+  tuned_choice(sp, ham, nrhs, precision, arm, path);
   st = apply_path(sp, ham, H->hb_in, H->hb_out, nrhs, precision, arm, H->ws, H->ws_bytes, s, path, &ov);
   if (st) {
     cudaStreamSynchronize(H->hb_copy);
@@ -994,7 +997,7 @@ extern "C" int fock_apply_path(const fock_space *sp, const fock_ham *ham, int32_
   int st = check_apply_args(sp, ham, nrhs, precision, arm);
   if (st) return st;
   int p = FOCK_PATH_AUTO;
-  tuned_choice(ham, nrhs, precision, arm, p);
+  tuned_choice(sp, ham, nrhs, precision, arm, p);
   int chosen = FOCK_PATH_LIST;
   st = select_path(sp, ham, nrhs, precision, arm, workspace_bytes, p, &chosen);
   if (!st) *path = chosen;

@@ -115,6 +115,13 @@ def test_autotune_chooses_a_serving_path_and_caches_it(torch, tmp_path, prec):
     assert abs(t2.ms - t.ms) <= 1e-5 * t.ms + 1e-6
     lines = open(cache).read().strip().splitlines()
     assert len(lines) == 1 and lines[0].startswith(f"N={N} M={M} ")
+    # a choice on the map arm lapses when the maps are freed
+    fock.fock_apply_set_path(H.handle, 1, prec, fock.FOCK_PATH_LIST, fock.FOCK_ARM_MAPS)
+    assert fock.fock_apply_path(sp.handle, H.handle, 1, prec) == fock.FOCK_PATH_LIST
+    fock.fock_jump_maps_free(sp.handle)
+    assert fock.fock_apply_path(sp.handle, H.handle, 1, prec) == fock.FOCK_PATH_TWOPHASE_TC
+    out = H.apply(dev(torch, C, prec), precision=prec).cpu().numpy().astype(np.complex128)
+    assert rel(out[::97], ref) <= TOL[prec]
     # clearing the choice restores the built-in order
     fock.fock_apply_set_path(H.handle, 1, prec, fock.FOCK_PATH_AUTO)
     assert fock.fock_apply_path(sp.handle, H.handle, 1, prec) == fock.FOCK_PATH_TWOPHASE_TC
