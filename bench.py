@@ -631,7 +631,19 @@ def main():
     def e2e_step():
         fock.fock_apply_H_host(sp.handle, H.handle, Ch, Sh, w.nrhs, prec, fock.FOCK_ARM_AUTO)
 
-    e2e_ms = time_steps(torch, e2e_step, max(3, args.steps // 4), 1, barrier) if args.e2e else float("nan")
+    # each call is synchronous (copies in and out included): time the calls
+    # one by one and report the median (host-side stalls of a shared machine
+    # show up as outliers), with the mean and the minimum beside it
+    e2e_ms, e2e_all = float("nan"), []
+    if args.e2e:
+        e2e_step()
+        barrier()
+        for _ in range(max(5, args.steps // 4)):
+            t0 = time.perf_counter()
+            e2e_step()
+            e2e_all.append((time.perf_counter() - t0) * 1e3)
+        barrier()
+        e2e_ms = dist_reduce(sorted(e2e_all)[len(e2e_all) // 2], "max")
     del Ch, Sh
 
     nbytes = w.nc * w.nrhs * elem
@@ -693,8 +705,11 @@ def main():
         "roofline": roofline,
         "hbm": {"compulsory_bytes": 2 * nbytes, "achieved_gbs": hbm_gbs, "peak_gbs": peaks["hbm_gbs"],
                 "frac": hbm_gbs / peaks["hbm_gbs"], "peak_source": peak_src},
-        "e2e": {"value": terms / (e2e_ms * 1e-3), "unit": "config-terms/s",
-                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms},
+        "e2e": {"value": terms * ws / (e2e_ms * 1e-3), "unit": "config-terms/s",
+                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_ms,
+                "statistic": "median of per-call host times",
+                "mean_ms": sum(e2e_all) / len(e2e_all) if e2e_all else None,
+                "min_ms": min(e2e_all) if e2e_all else None, "calls": len(e2e_all)},
         "clocks": clocks,
     }
     if rank == 0 and args.extras:
