@@ -32,8 +32,8 @@ int fock_launch_sparse_df(const SparseArgs &, bool, bool, int, cudaStream_t);
 int fock_launch_sparse_mixed(const SparseArgs &, bool, bool, int, cudaStream_t);
 int fock_launch_twophase(const TwoPhaseArgs &, bool, int, cudaStream_t);
 int fock_launch_twophase_tc(const TwoPhaseArgs &, bool, int, cudaStream_t);
-int fock_launch_nn(const ApplyArgs<uint32_t> &, const void *, const void *, const void *, int, int, int,
-                   cudaStream_t);
+int fock_launch_nn(const ApplyArgs<uint32_t> &, const void *, const void *, const void *, int, int, uint32_t,
+                   uint32_t, int, cudaStream_t);
 int fock_tc_image(int M, const std::complex<double> *R, std::vector<unsigned char> &img, std::vector<int> &er);
 int fock_tc_image_mixed(int M, const std::complex<double> *R, std::vector<unsigned char> &img, std::vector<int> &er);
 size_t fock_tc_smem(int M, int xdim, int nsq, bool mixed);
@@ -667,9 +667,10 @@ static void fill_args(ApplyArgs<Idx> &a, const fock_space *sp, const fock_ham *h
   }
 }
 
-// Host-buffer applies: when the two-phase path serves the call, phase 2 runs
-// in chunks of configurations and each finished chunk of sigma is copied to
-// the host on a second stream while the next chunk is computed.
+// Host-buffer applies: when the two-phase path (phase 2) or the
+// nearest-neighbour kernel serves the call, it runs in chunks of
+// configurations and each finished chunk of sigma is copied to the host on a
+// second stream while the next chunk is computed.
 struct HostOverlap {
   void *sigma_host;
   cudaStream_t copy;
@@ -842,11 +843,31 @@ static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Ci
         if (!st) ov->done = true;
         return st;
       }
-      case FOCK_PATH_NN:
+      case FOCK_PATH_NN: {
         // nearest-neighbour operators: one diagonal term and two hops per bond
         if (precision == FOCK_PREC_F64) a.out_scale = ham->nn_scale;
-        return fock_launch_nn(a, ham->d_nn_bond[precision], ham->d_nn_e[precision], ham->d_nn_t[precision],
-                              ham->nn_nb, precision, sp->device, stream);
+        auto launch = [&](uint32_t b, uint32_t e) {
+          return fock_launch_nn(a, ham->d_nn_bond[precision], ham->d_nn_e[precision], ham->d_nn_t[precision],
+                                ham->nn_nb, precision, b, e, sp->device, stream);
+        };
+        if (!ov) return launch(0u, a.nc);
+        // host-buffer apply: the configurations in chunks, each chunk of sigma
+        // copied out behind the kernel that computed it
+        const uint32_t chunk = (a.nc + kHostChunks - 1) / kHostChunks;
+        for (int i = 0; i < kHostChunks; ++i) {
+          const uint32_t b = (uint32_t)i * chunk, e = b + chunk < a.nc ? b + chunk : a.nc;
+          if (b >= e) break;
+          const int st = launch(b, e);
+          if (st) return st;
+          FOCK_CUDA_TRY(cudaEventRecord(ov->ev[i], stream));
+          FOCK_CUDA_TRY(cudaStreamWaitEvent(ov->copy, ov->ev[i], 0));
+          FOCK_CUDA_TRY(cudaMemcpyAsync((char *)ov->sigma_host + (size_t)b * ov->row_bytes,
+                                        (const char *)sigma + (size_t)b * ov->row_bytes,
+                                        (size_t)(e - b) * ov->row_bytes, cudaMemcpyDeviceToHost, ov->copy));
+        }
+        ov->done = true;
+        return FOCK_OK;
+      }
       case FOCK_PATH_DENSE:
         // every reduced coefficient present and M <= 10: the register-resident
         // kernel with the addition loop unrolled at compile time

@@ -92,6 +92,7 @@ struct NNArgs {
   const void *etab;           // [M][N + 1] policy amp_t: E_k(n) = h_kk n + W_kkkk n (n - 1) / 2
   const void *ttab;           // [N + 1][N + 1] policy amp_t: sqrt(a (b + 1)), or null
   int nb;                     // bonds: M - 1, or M for a ring (M > 2)
+  uint32_t g_begin, g_end;    // configurations computed
 };
 
 // TT: hop amplitudes sqrt(n_k (n_l + 1)) from the (N + 1)^2 table (one
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(kNNThreads, kNNMinBlocks) fock_apply_nn(const 
     else return P::amul(s_A[nk], s_A[nl + 1]);
   };
 
-  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < nc; g += gridDim.x * blockDim.x) {
+  for (uint32_t g = t.g_begin + blockIdx.x * blockDim.x + threadIdx.x; g < t.g_end; g += gridDim.x * blockDim.x) {
     int S[M];
     fock_decode_fast<M>(g, a.N, nc, s_sat, a.xdim, S);
     // diagonal: sum_k E_k(n_k), a real amplitude
@@ -196,7 +197,7 @@ int launch_nn_m(const NNArgs &t, int device, cudaStream_t s) {
   int per_sm = 0;
   FOCK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNNThreads, smem));
   if (per_sm < 1) return FOCK_ERR_UNSUPPORTED;
-  int64_t blocks = ((int64_t)a.nc + kNNThreads - 1) / kNNThreads;
+  int64_t blocks = ((int64_t)(t.g_end - t.g_begin) + kNNThreads - 1) / kNNThreads;
   const int64_t cap = (int64_t)per_sm * fock_get_sm_count(device);
   if (blocks > cap) blocks = cap;
   kern<<<(unsigned)(blocks < 1 ? 1 : blocks), kNNThreads, smem, s>>>(t);
@@ -237,16 +238,20 @@ int launch_nn_p(const NNArgs &t, int device, cudaStream_t s) {
 
 }  // namespace
 
-// Launch for one of the precisions; bond, etab and ttab hold that precision's
-// arrays (ttab null: hop amplitudes from the square-root table of `a`).
+// Launch for one of the precisions over configurations [g_begin, g_end); bond,
+// etab and ttab hold that precision's arrays (ttab null: hop amplitudes from
+// the square-root table of `a`).
 int fock_launch_nn(const ApplyArgs<uint32_t> &a, const void *bond, const void *etab, const void *ttab, int nb,
-                   int precision, int device, cudaStream_t s) {
+                   int precision, uint32_t g_begin, uint32_t g_end, int device, cudaStream_t s) {
   NNArgs t;
   t.a = a;
   t.bond = bond;
   t.etab = etab;
   t.ttab = ttab;
   t.nb = nb;
+  t.g_begin = g_begin;
+  t.g_end = g_end;
+  if (g_begin >= g_end) return FOCK_OK;
   if (precision == FOCK_PREC_F64) return launch_nn_p<PolDFP>(t, device, s);
   if (precision == FOCK_PREC_F32_MIXED) return launch_nn_p<PolMixedP>(t, device, s);
   return launch_nn_p<PolF64>(t, device, s);

@@ -40,6 +40,8 @@ def dev_vec(torch, C, prec):
 def hw(kind, M, seed=7, g=1.0):
     if kind == "ll":
         return inputs.lieb_liniger_hw(M, g)
+    if kind == "bh":
+        return inputs.bose_hubbard_hw(M, 1.0, 3.0, 0.3)
     if kind == "onebody":
         h, _ = inputs.random_hermitian_hw(M, seed)
         return h, None
@@ -237,6 +239,8 @@ def test_terms_count_matches_oracle_columns(torch):
     (9, 6, "generic", 3, False),     # several right-hand sides, pageable host memory
     (6, 8, "generic", 1, True),      # two-phase with FP32 phase 1
     (10, 5, "ll", 2, True),          # sparse kernel: one copy after the apply
+    (9, 6, "bh", 1, True),           # nearest-neighbour kernel, sigma copied out by chunks
+    (8, 7, "bh", 3, False),
 ])
 def test_host_buffer_entry_point(torch, N, M, kind, nrhs, pinned, prec):
     h, W = hw(kind, M)
