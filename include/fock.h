@@ -366,8 +366,9 @@ typedef struct fock_sector fock_sector;
  * otherwise).  Builds the counting tables D_m(s, q) (configurations of s
  * particles in orbitals 0..m-1 of weight q; host uint64 and device mod 2^32,
  * (2M - 3)(N + 1)(Q + 1) words on the device).  FOCK_ERR_OVERFLOW when the
- * sector holds 2^31 configurations or more.  The sector refers to `sp`, which
- * must outlive it. */
+ * sector holds 2^31 configurations or more; FOCK_ERR_UNSUPPORTED when
+ * M (N + 1)(Q + 1) exceeds 2^28 table entries.  The sector refers to `sp`,
+ * which must outlive it. */
 int fock_sector_create(const fock_space *sp, int64_t Q, fock_sector **out);
 int fock_sector_destroy(fock_sector *sec);
 int fock_sector_size(const fock_sector *sec, int64_t *n_sector);

@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <complex>
+#include <new>
 #include <initializer_list>
 #include <vector>
 
@@ -196,18 +197,18 @@ static int build_nn(fock_ham *H, const double *h_host, const double *W_host) {
   // sqrt(a (b + 1)) for a, b = 0..N (each one correctly rounded square root;
   // used by the native FP64 form)
   const int N = H->sp->N, np1 = N + 1;
-  std::vector<double> E((size_t)M * np1);
-  for (int k = 0; k < M; ++k)
-    for (int n = 0; n <= N; ++n) {
-      E[(size_t)k * np1 + n] = hre(k, k) * n + 0.5 * Wd[k] * n * (n - 1.0);
-      amax = fmax(amax, fmax(fabs(hre(k, k)), fabs(Wd[k])));
-    }
   const bool tt = np1 <= 32;
   // the kernel stages these tables and the hash tables in shared memory; beyond
   // about 24 KB per block (8 blocks per SM) the generic kernels serve instead
   const size_t smem = 32 * (size_t)M + 8 * ((size_t)M * np1 + (tt ? (size_t)np1 * np1 : (size_t)N + 4) + 1) +
                       8 * (size_t)(M - 1) * (N + M + 5);
   if (smem > 24 * 1024) return FOCK_OK;
+  std::vector<double> E((size_t)M * np1);
+  for (int k = 0; k < M; ++k)
+    for (int n = 0; n <= N; ++n) {
+      E[(size_t)k * np1 + n] = hre(k, k) * n + 0.5 * Wd[k] * n * (n - 1.0);
+      amax = fmax(amax, fmax(fabs(hre(k, k)), fabs(Wd[k])));
+    }
   std::vector<double> T(tt ? (size_t)np1 * np1 : 0);
   for (int a = 0; tt && a <= N; ++a)
     for (int b = 0; b <= N; ++b) T[(size_t)a * np1 + b] = sqrt((double)a * (b + 1));
@@ -253,8 +254,22 @@ static int build_nn(fock_ham *H, const double *h_host, const double *W_host) {
   return st;
 }
 
+static int hamiltonian_create(const fock_space *sp, const double *h_host, const double *W_host, double tol,
+                              fock_ham **out);
+
+// Host allocations (term lists, tables) that fail become FOCK_ERR_NOMEM; no
+// C++ exception crosses the C ABI.
 extern "C" int fock_hamiltonian_create(const fock_space *sp, const double *h_host,
                                        const double *W_host, double tol, fock_ham **out) {
+  try {
+    return hamiltonian_create(sp, h_host, W_host, tol, out);
+  } catch (const std::bad_alloc &) {
+    return FOCK_ERR_NOMEM;
+  }
+}
+
+static int hamiltonian_create(const fock_space *sp, const double *h_host, const double *W_host, double tol,
+                              fock_ham **out) {
   if (!sp || !h_host || !out) return FOCK_ERR_ARG;
   int cur = -1;
   if (cudaGetDevice(&cur) != cudaSuccess) return FOCK_ERR_CUDA;

@@ -29,6 +29,7 @@
 // change of sum_m T_m over that range (one table read per orbital in it).
 #include <cstring>
 #include <functional>
+#include <new>
 #include <vector>
 
 #include "fock_apply_kernel.cuh"
@@ -486,12 +487,28 @@ static int fock_sector_apply_internal(const fock_sector *sec, const fock_ham *ha
   return st;
 }
 
+static int sector_create(const fock_space *sp, int64_t Q, fock_sector **out);
+
+// The counting tables grow as M (N + 1) (Q + 1); beyond 2^28 entries (2 GB on
+// the host) the call returns FOCK_ERR_UNSUPPORTED, and a host allocation that
+// fails below that returns FOCK_ERR_NOMEM (no C++ exception crosses the ABI).
 extern "C" int fock_sector_create(const fock_space *sp, int64_t Q, fock_sector **out) {
   if (!sp || !out) return FOCK_ERR_ARG;
   int st = check_dev(sp->device);
   if (st) return st;
   const int N = sp->N, M = sp->M;
   if (Q < 0 || Q > (int64_t)N * (M - 1)) return FOCK_ERR_ARG;
+  if ((double)M * (N + 1) * ((double)Q + 1) > (double)(1u << 28)) return FOCK_ERR_UNSUPPORTED;
+  try {
+    return sector_create(sp, Q, out);
+  } catch (const std::bad_alloc &) {
+    return FOCK_ERR_NOMEM;
+  }
+}
+
+static int sector_create(const fock_space *sp, int64_t Q, fock_sector **out) {
+  int st = FOCK_OK;
+  const int N = sp->N, M = sp->M;
   fock_sector *sec = new fock_sector();
   sec->sp = sp;
   sec->N = N;
