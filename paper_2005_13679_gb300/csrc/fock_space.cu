@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <new>
 #include <vector>
 
 #include "fock_common.cuh"
@@ -127,7 +128,12 @@ extern "C" int fock_space_create(int32_t N, int32_t M, fock_space **out) {
     return FOCK_ERR_CUDA;
   }
   sp->idx32 = nc < (int64_t)0xffffffffll;
-  int st = build_tables(N, M, sp->tab);
+  int st;
+  try {                                  // no C++ exception crosses the C ABI
+    st = build_tables(N, M, sp->tab);
+  } catch (const std::bad_alloc &) {
+    st = FOCK_ERR_NOMEM;
+  }
   if (st == FOCK_OK && cudaMalloc(&sp->d_flag, 256) != cudaSuccess) st = FOCK_ERR_NOMEM;
   if (st != FOCK_OK) {
     free_tables(sp->tab);
