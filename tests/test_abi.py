@@ -52,3 +52,21 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(fock, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         fock.load(str(tmp_path / "libfock.so"))
+
+
+def test_binding_constants_match_the_header():
+    """Every FOCK_* constant the header defines has the same value in the binding."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    defs = dict(re.findall(r"#define\s+(FOCK_[A-Z0-9_]+)\s+(-?\d+)\b", text))
+    assert "FOCK_ERR_NOT_CONSERVING" in defs and "FOCK_PATH_LIST" in defs
+    for name, value in defs.items():
+        assert hasattr(fock, name), name
+        assert getattr(fock, name) == int(value), name
+
+
+def test_every_status_has_its_own_message(lib):
+    fock.load()
+    codes = sorted(v for k, v in vars(fock).items() if k.startswith("FOCK_ERR_"))
+    msgs = [fock.fock_strerror(c) for c in codes]
+    assert all("unknown" not in m for m in msgs)
+    assert len(set(msgs)) == len(msgs)
