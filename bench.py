@@ -150,7 +150,6 @@ def oracle_rate(w, h, W, C, seconds: float):
 
     import oracle
     oracle.build()
-    terms_per_cfg = None
     rng = np.random.default_rng(123)
     n = 8
     while True:
@@ -164,7 +163,100 @@ def oracle_rate(w, h, W, C, seconds: float):
     return n, dt
 
 
+def host_info():
+    """Host cores this process may use and the CPU model (lscpu, else the
+    platform string)."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"nproc": cores, "cpu_model": model}
+
+
+def _oracle_worker(args):
+    """One host core of the all-core oracle leg: attach the shared C, wait at
+    the barrier, then evaluate `n` rows of sigma with the oracle's row form."""
+    shm_name, nc, N, M, h, W, n, seed, barrier = args
+    import numpy as np
+    from multiprocessing import shared_memory
+
+    import oracle
+    shm = shared_memory.SharedMemory(name=shm_name)
+    try:
+        C = np.ndarray((nc,), dtype=np.complex128, buffer=shm.buf)
+        rows = np.random.default_rng(seed).integers(0, nc, n)
+        oracle.apply_rows(N, M, h, W, C, rows[: max(1, n // 50)])     # touch pages, load the library
+        barrier.wait()
+        t0 = time.perf_counter()
+        oracle.apply_rows(N, M, h, W, C, rows)
+        return time.perf_counter() - t0
+    finally:
+        del C
+        shm.close()
+
+
+def oracle_rate_all_cores(w, h, W, C, rows_per_core: int, cores: int):
+    """The oracle as it stands on `cores` host processes at once (spawned, no
+    CUDA context), each on its own bounded sample of rows: returns (rows in
+    all, wall seconds of the slowest process)."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    shm = shared_memory.SharedMemory(create=True, size=C.nbytes)
+    try:
+        np.ndarray(C.shape, dtype=np.complex128, buffer=shm.buf)[:] = C
+        ctx = mp.get_context("spawn")
+        with ctx.Manager() as mgr:
+            bar = mgr.Barrier(cores)
+            with ctx.Pool(cores) as pool:
+                times = pool.map(_oracle_worker, [(shm.name, C.shape[0], w.N, w.M, h, W, rows_per_core, 1000 + i, bar)
+                                                  for i in range(cores)])
+        return rows_per_core * cores, max(times)
+    finally:
+        shm.close()
+        shm.unlink()
+
+
+def cpu_baseline(w, h, W, C, per_cfg: float, seconds: float, all_cores: bool = True):
+    """cpu_baseline of the bench line: the oracle on one host core (bounded row
+    sample, calibrated to ~seconds/5 .. seconds) and, when all_cores, on every
+    host core at once (about the same work per core)."""
+    info = host_info()
+    n1, dt1 = oracle_rate(w, h, W, C, seconds)
+    one = per_cfg * n1 / dt1
+    out = {"value": one, "unit": "config-terms/s", "cores": 1, "kind": "oracle",
+           "sample": f"{n1} random rows of sigma (row form), {dt1:.1f} s on one core", **info}
+    if all_cores and info["nproc"] > 1:
+        per_core = max(8, int(n1 * max(1.0, 0.5 * seconds / dt1)))
+        nall, wall = oracle_rate_all_cores(w, h, W, C, per_core, info["nproc"])
+        allc = per_cfg * nall / wall
+        out.update({"value": allc, "cores": info["nproc"],
+                    "sample": f"{nall} random rows of sigma (row form) on {info['nproc']} processes, "
+                              f"{wall:.1f} s wall",
+                    "single_core": {"value": one, "unit": "config-terms/s", "rows": n1, "seconds": dt1},
+                    "parallel_speedup": allc / one})
+    return out
+
+
 def run_reference(args, w):
+    """The oracle as it stands, on every host core: each step is one bounded
+    sample of rows of sigma per core (all cores at once), timed on the host."""
     import numpy as np
 
     from paper_2005_13679_gb300 import inputs  # noqa: F401  (input generator only)
@@ -175,29 +267,28 @@ def run_reference(args, w):
     C = w.state() if w.nrhs == 1 else w.state()[:, 0].copy()
     terms_total = terms_formula(w, h, W)
     per_cfg = terms_total / w.nc
-    budget = max(5.0, min(60.0, 120.0 / max(1, args.steps + args.warmup)))
-    rows_per_step, _ = oracle_rate(w, h, W, C, budget)
-    import oracle
-    rng = np.random.default_rng(7)
+    info = host_info()
+    budget = max(3.0, min(30.0, 90.0 / max(1, args.steps + args.warmup)))
+    rows_per_core, dt1 = oracle_rate(w, h, W, C, budget)
     for _ in range(args.warmup):
-        oracle.apply_rows(w.N, w.M, h, W, C, rng.integers(0, w.nc, max(1, rows_per_step // 8)))
-    times = []
+        oracle_rate_all_cores(w, h, W, C, max(1, rows_per_core // 8), info["nproc"])
+    rows_all, wall = 0, 0.0
     for _ in range(args.steps):
-        rows = rng.integers(0, w.nc, rows_per_step)
-        t0 = time.perf_counter()
-        oracle.apply_rows(w.N, w.M, h, W, C, rows)
-        times.append(time.perf_counter() - t0)
-    tot = sum(times)
-    value = per_cfg * rows_per_step * args.steps / tot
+        n, t = oracle_rate_all_cores(w, h, W, C, rows_per_core, info["nproc"])
+        rows_all += n
+        wall += t
+    value = per_cfg * rows_all / wall
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "config-terms/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "N": w.N, "M": w.M, "nc": w.nc},
-        "cpu_baseline": {"value": value, "unit": "config-terms/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{rows_per_step} random rows of sigma per step (row form of the oracle), "
-                                   f"{per_cfg:.1f} config-terms per configuration"},
+        "cpu_baseline": {"value": value, "unit": "config-terms/s", "cores": info["nproc"], "kind": "oracle",
+                         "sample": f"{rows_per_core} random rows of sigma per core per step (row form of the "
+                                   f"oracle), {per_cfg:.1f} config-terms per configuration",
+                         "single_core": {"value": per_cfg * rows_per_core / dt1, "unit": "config-terms/s"},
+                         **info},
         "e2e": {"value": value, "unit": "config-terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -221,17 +312,21 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
 
 
 def tc_shape(M):
-    """Real-form sizes of the tensor-core phase 1 (fock_apply_tc.cuh)."""
+    """Real-form sizes of the tensor-core phase 1 (fock_apply_tc.cuh): 2P real
+    indices, the two MMA chains (N1 x K1 and N2 x K2), 20 digit pairs
+    (levels i + j <= 7 with six digits of R and five of X)."""
     r2 = M * (M + 1)
-    k1, k2 = (3 * r2 + 15) // 16 * 16, (2 * r2 + 15) // 16 * 16
-    nt = 16 * ((r2 + 2) // 3)
-    return r2, nt, k1 + k2
+    k1, k2 = (3 * r2 + 1 + 15) // 16 * 16, (2 * r2 + 15) // 16 * 16
+    n2 = (3 * r2 + 1 + 15) // 16 * 16
+    n1 = (n2 + 3 * r2 + 15) // 16 * 16
+    return r2, n1 * k1 + n2 * k2, 20
 
 
 def tc_shape_mixed(M):
-    """Real-form sizes of the FP32-mixed tensor-core phase 1."""
+    """Real-form sizes of the FP32-mixed tensor-core phase 1 (one chain N x K)
+    and its 3 products (R_h X_h, R_h X_l, R_l X_h)."""
     r2 = M * (M + 1)
-    return r2, (r2 + 1 + 15) // 16 * 16, (3 * r2 + 1 + 15) // 16 * 16
+    return r2, ((r2 + 1 + 15) // 16 * 16) * ((3 * r2 + 1 + 15) // 16 * 16), 3
 
 
 def nn_terms(w):
@@ -241,16 +336,15 @@ def nn_terms(w):
     return w.nc * (1 + 2 * nb)
 
 
-def tc_flops(w, mixed=False):
-    """Tensor-core work of phase 1 per apply and the MMA work executed, for
-    every (N-2)-space column: FP64-class, the 15 digit-pair products of the
-    error-free split (levels i + j <= 6) over the (2P)^2 real-form entries;
-    FP32-mixed, the 3 products of the fp16 hi/lo split (R_h X_h, R_h X_l,
-    R_l X_h); 2 flop per product.  Executed: 2 N K per column with the MMA's
-    N (level or row columns) and K (digit positions)."""
-    r2, nt, kt = tc_shape_mixed(w.M) if mixed else tc_shape(w.M)
+def tc_flops(w, nnz_r, mixed=False):
+    """Phase 1 per apply: the method's own work, one complex multiply-add
+    (8 flop) per nonzero reduced coefficient per (N-2)-space column; the
+    emulation's digit-pair products over the (2P)^2 real-form entries (2 flop
+    each); and the MMA work executed (2 N K per column summed over the
+    chains)."""
+    r2, nk, pairs = tc_shape_mixed(w.M) if mixed else tc_shape(w.M)
     cols = math.comb(w.N - 2 + w.M - 1, w.M - 1) * w.nrhs
-    return cols * (3 if mixed else 15) * r2 * r2 * 2, cols * 2 * nt * kt
+    return cols * 8 * nnz_r, cols * pairs * r2 * r2 * 2, cols * 2 * nk
 
 
 def launches_per_step(path, prec):
@@ -259,15 +353,11 @@ def launches_per_step(path, prec):
     return (2 if prec == 0 else 0) + (2 if path.startswith("twophase") else 1)
 
 
-def executed_terms(w, h, W):
-    """Removal-addition pairs the kernel visits: each listed two-body pair is
-    taken by the N_c(N-2, M) configurations that allow its removal (one-body:
-    N_c(N-1, M))."""
+def reduced_nnz(w, h, W):
+    """Nonzero reduced coefficients (removal multiset, addition multiset) with
+    the one-body part folded in, as the library forms them."""
     import numpy as np
-    N, M = w.N, w.M
-    nc = lambda n: math.comb(n + M - 1, M - 1) if n >= 0 else 0
-    if W is None or N < 2:
-        return nc(N - 1) * int(np.count_nonzero(h))
+    M, N = w.M, w.N
     P = M * (M + 1) // 2
     idx = {}
     for k in range(M):
@@ -281,7 +371,19 @@ def executed_terms(w, h, W):
                     R[idx[(min(k, q), max(k, q))], idx[(min(s, l), max(s, l))]] += W[k, q, s, l]
                     if q == s:
                         R[idx[(min(k, q), max(k, q))], idx[(min(s, l), max(s, l))]] += h[k, l] / (N - 1)
-    return nc(N - 2) * int(np.count_nonzero(R))
+    return int(np.count_nonzero(R))
+
+
+def executed_terms(w, h, W):
+    """Removal-addition pairs the kernel visits: each listed two-body pair is
+    taken by the N_c(N-2, M) configurations that allow its removal (one-body:
+    N_c(N-1, M))."""
+    import numpy as np
+    N, M = w.N, w.M
+    nc = lambda n: math.comb(n + M - 1, M - 1) if n >= 0 else 0
+    if W is None or N < 2:
+        return nc(N - 1) * int(np.count_nonzero(h))
+    return nc(N - 2) * reduced_nnz(w, h, W)
 
 
 def sources_digest(paths):
@@ -292,12 +394,13 @@ def sources_digest(paths):
     return hashlib.sha256(b"".join(open(os.path.join(pkg, f), "rb").read() for f in paths)).hexdigest()[:16]
 
 
-def load_traffic(workload, precision):
-    """DRAM bytes per launch of the main kernel from the committed ncu summary of
-    this workload, if the kernel's translation unit and the headers it includes
-    (listed in the summary) still match the sources the counters were taken
-    from (else None)."""
-    path = os.path.join(ROOT, "profiles", f"traffic_{workload}_{precision}.txt")
+def load_traffic(workload, precision, phase=""):
+    """DRAM bytes per launch of the main kernel (phase="") or of the second
+    phase of a two-phase apply (phase="_phase2") from the committed ncu summary
+    of this workload, if the kernel's translation unit and the headers it
+    includes (listed in the summary) still match the sources the counters were
+    taken from (else None)."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}_{precision}{phase}.txt")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -549,6 +652,7 @@ def main():
     ap.add_argument("--precision", default="f64", choices=list(PREC))
     ap.add_argument("--extras", type=int, default=1, help="also time the other precisions and forms")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-all-cores", type=int, default=1, help="also time the oracle on every host core")
     ap.add_argument("--e2e", type=int, default=1, help="also time the host-buffer entry point")
     ap.add_argument("--lanczos-iters", type=int, default=240, help="batched Lanczos budget (ll_batch64)")
     args = ap.parse_args()
@@ -652,13 +756,30 @@ def main():
     path = fock.PATH_NAMES[fock.fock_apply_path(sp.handle, H.handle, w.nrhs, prec, fock.FOCK_ARM_AUTO, wsz)]
     traffic = load_traffic(w.name, args.precision)
     if path == "twophase_tc":
-        # dominant kernel = phase 1 on the tensor cores (fp16 digits, FP32 accumulators)
-        alg, mma = tc_flops(w, prec == 2)
+        # dominant kernel = phase 1 on the tensor cores (fp16 digits, FP32
+        # accumulators): the fraction is taken on the method's own flops; the
+        # digit-pair work of the error-free split and the MMA work executed are
+        # reported beside it
+        nnz_r = reduced_nnz(w, h, W)
+        alg, digit, mma = tc_flops(w, nnz_r, prec == 2)
         achieved = alg / (kernel_ms * 1e-3) / 1e12
+        P = w.M * (w.M + 1) // 2
+        ybytes = math.comb(w.N - 2 + w.M - 1, w.M - 1) * w.nrhs * P * (8 if prec == 2 else 16)
+        traffic2 = load_traffic(w.name, args.precision, "_phase2")
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                     "frac": achieved / peaks["bf16_tflops"], "traffic": traffic, "kernel": "fock_twophase_x_tc",
-                    "kernel_ms": kernel_ms, "algorithmic_flops": alg, "executed_mma_flops": mma,
-                    "executed_tflops": mma / (kernel_ms * 1e-3) / 1e12, "path": path,
+                    "kernel_ms": kernel_ms, "method_flops": alg,
+                    "method_flops_note": "8 flop per nonzero reduced coefficient per (N-2)-space column",
+                    "emulation": {"digit_pair_flops": digit, "executed_mma_flops": mma,
+                                  "executed_tflops": mma / (kernel_ms * 1e-3) / 1e12,
+                                  "executed_frac": mma / (kernel_ms * 1e-3) / 1e12 / peaks["bf16_tflops"]},
+                    "hbm_frac_kernel": 2 * nbytes / (kernel_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                    "hbm_frac_step": 2 * nbytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                    "hbm_note": "compulsory bytes of the apply (C read, sigma written) over the phase-1 and the "
+                                "whole-step time",
+                    "y_bytes_written": ybytes, "traffic_phase2": traffic2,
+                    "traffic_apply": (traffic + traffic2) if (traffic and traffic2) else None,
+                    "path": path,
                     "peak_note": "fp16 dense has the nominal bf16 rate on this part: measured bf16 burst "
                                  f"({peak_src}); of measured"}
     elif path == "nn":
@@ -748,10 +869,8 @@ def main():
                 "note": "host-synchronous call incl. its workspace allocation and the input split; "
                         "Gram matrices over the (N-1)- and (N-2)-particle spaces"}
             del X
-        n, dt = oracle_rate(w, h, W, Cn if w.nrhs == 1 else Cn[:, 0].copy(), args.cpu_seconds)
-        per_cfg = H.terms / w.nc
-        out["cpu_baseline"] = {"value": per_cfg * n / dt, "unit": "config-terms/s", "cores": 1,
-                               "kind": "oracle", "sample": f"{n} random rows of sigma (row form), {dt:.1f} s"}
+        out["cpu_baseline"] = cpu_baseline(w, h, W, Cn if w.nrhs == 1 else Cn[:, 0].copy(), H.terms / w.nc,
+                                           args.cpu_seconds, all_cores=bool(args.cpu_all_cores))
     if rank == 0:
         print(json.dumps(out), flush=True)
     dist_finish()

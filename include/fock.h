@@ -12,7 +12,7 @@
  * on coefficient vectors over the Fock basis of N bosons in M orbitals
  * (Eq. nc, N_c(N, M) = C(N+M-1, M-1) configurations), together with the
  * configuration hash (Eq. TotalCost, Algorithms 1 and 2), the single- and
- * double-jump index maps of Sec. 3, and a Lanczos ground-state driver (Sec. 5).
+ * double-jump index maps of Sec. 4, and a Lanczos ground-state driver (Sec. 6).
  *
  * Conventions used by every entry point:
  *   - orbitals are numbered 0..M-1, an occupation vector is int32 n[0..M-1]
@@ -72,7 +72,7 @@ const char *fock_strerror(int status);
 int fock_version(void);
 
 /* ------------------------------------------------------------------------- */
-/* Configuration space H(N, M)  (Eq. nc; Sec. 2)                             */
+/* Configuration space H(N, M)  (Eq. nc; Sec. 3)                             */
 /* ------------------------------------------------------------------------- */
 typedef struct fock_space fock_space;
 
@@ -104,7 +104,7 @@ int fock_unrank(const fock_space *sp, const int64_t *idx_dev, int64_t count,
                 int32_t *occ_dev, void *stream);
 
 /* ------------------------------------------------------------------------- */
-/* Jump maps  (Sec. 3, "Mapping routines"; Fig. 4)                          */
+/* Jump maps  (Sec. 4, "Mapping routines"; Fig. 4)                          */
 /* ------------------------------------------------------------------------- */
 #define FOCK_MAP_SINGLE 1   /* one particle k -> l                           */
 #define FOCK_MAP_DOUBLE 2   /* two particles {k, q} -> {s, l}                */
@@ -135,7 +135,7 @@ int fock_jump_map_get(const fock_space *sp, int which, const int32_t **map_dev,
 int fock_jump_maps_free(fock_space *sp);
 
 /* ------------------------------------------------------------------------- */
-/* Hamiltonian  (Eqs. noninteracting, interacting; Sec. 1)                   */
+/* Hamiltonian  (Eqs. noninteracting, interacting; Sec. 2)                   */
 /* ------------------------------------------------------------------------- */
 typedef struct fock_ham fock_ham;
 
@@ -261,6 +261,29 @@ int fock_apply_H(const fock_space *sp, const fock_ham *ham, const void *C_dev,
                  void *sigma_dev, int32_t nrhs, int precision, int arm,
                  void *workspace_dev, size_t workspace_bytes, void *stream);
 
+/* Status of the last apply that ran the tensor-core phase 1 (the first path
+ * of the list above) with this workspace.  Its bounded device waits give up
+ * after about a second; phase 2 then writes NaN to sigma.  fock_apply_H and
+ * fock_apply_H_noalloc return before the device work ends, so they report
+ * FOCK_OK in that case; this call waits on `stream` and returns
+ * FOCK_ERR_TIMEOUT if that apply's wait gave up, FOCK_OK otherwise.
+ * workspace_dev is the workspace passed to fock_apply_H (NULL: the
+ * Hamiltonian's own workspace, the one fock_apply_H with a NULL workspace and
+ * fock_apply_H_host use); with noalloc != 0 the fixed array of
+ * fock_apply_H_noalloc on the space's device is read instead.  Reads 4 bytes
+ * from the device; allocates nothing.  fock_apply_H_host checks this itself. */
+int fock_apply_check(const fock_space *sp, const fock_ham *ham, const void *workspace_dev, int noalloc,
+                     void *stream);
+
+/* Test hook, process-wide: poll budget of the bounded waits inside the
+ * tensor-core phase 1 (its producer, MMA-issue and epilogue roles).
+ * polls < 0 restores the default (2^20 polls, about a second); 0 makes every
+ * such wait give up at once, so that the abort path (status word, NaN sigma,
+ * FOCK_ERR_TIMEOUT) runs without a fault or a hang.  The wait that lets the
+ * MMAs already issued finish before tensor memory is released always keeps
+ * the default.  FOCK_ERR_ARG for polls above the default. */
+int fock_debug_set_wait_polls(int64_t polls);
+
 /* Same as fock_apply_H with host buffers: copies C_host to the device, applies
  * and copies sigma back into sigma_host, then waits on `stream`.  Device
  * buffers are owned by `ham` and reused across calls.  For pinned (page-locked)
@@ -294,11 +317,16 @@ int fock_apply_H_noalloc(const fock_space *sp, const fock_ham *ham, const void *
                          void *sigma_dev, int32_t nrhs, int arm, void *stream);
 
 /* ------------------------------------------------------------------------- */
-/* Lanczos ground state  (Sec. 5)                                            */
+/* Lanczos ground state  (Sec. 6)                                            */
 /* ------------------------------------------------------------------------- */
 /* Lowest eigenvalue of H by Lanczos with full re-orthogonalisation inside
- * restart cycles of restart_len vectors (explicit restart from the current
- * Ritz vector).  Krylov vectors and all orthogonalisation are FP64 (real when
+ * restart cycles of restart_len vectors.  A cycle ends with a thick restart
+ * (Wu and Simon): the next cycle starts from the lowest Ritz vectors of the
+ * cycle (min(restart_len / 3, 8) of them, at least one) and the last residual
+ * direction.  With FOCK_PREC_F32_MIXED products the solver first converges to
+ * the mixed apply's own floor (1e-5 relative residual), then continues with
+ * FOCK_PREC_F64 products from the current Ritz vector (final FP64
+ * refinement).  Krylov vectors and all orthogonalisation are FP64 (real when
  * the Hamiltonian is real, complex otherwise); the H C products use
  * `precision`; the returned E0 is the FP64 Rayleigh quotient of the final
  * unit vector with a FOCK_PREC_F64 apply, and *residual (may be NULL) is
@@ -314,7 +342,7 @@ int fock_lanczos_ground(const fock_space *sp, const fock_ham *ham, int32_t max_i
                         void *vec_dev, int32_t *iters, void *stream);
 
 /* Short-iterative-Lanczos time step C <- exp(-i H dt) C (the SIL integrator
- * the paper names as a consumer of H C, Sec. 1).  C_dev: N_c complex128 on
+ * the paper names as a consumer of H C, Sec. 2).  C_dev: N_c complex128 on
  * the space's device, overwritten.  The Krylov space of C (Lanczos vectors
  * orthogonalised twice against all previous ones) grows until the weight of
  * the next vector in exp(-i T dt) e_0 is below tol (relative to ||C||), the
@@ -351,10 +379,10 @@ int fock_density_matrices(const fock_space *sp, const void *C_dev, double *rho1_
 /* ------------------------------------------------------------------------- */
 /* Sectors of fixed total orbital weight Q = sum_i i n_i                     */
 /* ------------------------------------------------------------------------- */
-/* With the plane-wave orbitals of Sec. 5 (orbital i of momentum
+/* With the plane-wave orbitals of Sec. 6 (orbital i of momentum
  * (i - floor(M/2)) 2 pi / L) a sector is a total-momentum sector,
  * P = (Q - N floor(M/2)) 2 pi / L.  An operator with diagonal h and
- * W_kqsl = 0 unless k + q = s + l (Lieb-Liniger, Sec. 5) maps each sector into
+ * W_kqsl = 0 unless k + q = s + l (Lieb-Liniger, Sec. 6) maps each sector into
  * itself (total momentum is conserved), so its eigenproblem and its dynamics
  * restrict to one sector, about N (M - 1) + 1 times smaller than H(N, M).
  * This restriction is not in the paper; it follows from the conservation law.

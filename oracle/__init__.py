@@ -10,10 +10,12 @@ Contents (Andriati & Gammal, arXiv:2005.13679):
 
 * ``nc``, ``rank``, ``unrank`` -- Eq. nc, Algorithm 1, Algorithm 2 (C, in
   ``fock_oracle.c``);
-* ``single_jump_map``, ``double_jump_map`` -- the jump maps of Sec. 3, built by
+* ``single_jump_map``, ``double_jump_map`` -- the jump maps of Sec. 4, built by
   definition (unrank, move particles, rank);
 * ``apply_push``, ``apply_rows``, ``dense_hamiltonian`` -- sigma = H C of
   Eq. Haction from the operator strings of Eqs. noninteracting/interacting;
+* ``column_terms`` -- the number of those operator strings that survive on one
+  configuration (the per-configuration operation count);
 * ``rho1``, ``rho2`` -- the one- and two-body density matrices of Eqs. rho1
   and rho2, each element by its definition <C| O C> with O the unit one- or
   two-body operator applied by ``apply_push``;
@@ -23,7 +25,7 @@ Contents (Andriati & Gammal, arXiv:2005.13679):
   orbital weight sum_i i n_i (total momentum for plane waves) in the order of
   the full space, and sigma = H C restricted to them (embed, push, restrict);
 * ``lanczos_ground`` -- Lanczos with complete re-orthogonalisation and a
-  tridiagonal eigen-solve, as in Sec. 5;
+  tridiagonal eigen-solve, as in Sec. 6;
 * ``bethe_ground_energy`` -- the Lieb-Liniger ground state from the Bethe
   equations (Eqs. LLsystem and LLE0), by Newton's method.
 
@@ -129,7 +131,7 @@ def unrank_batch(N: int, M: int, idx) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
-# Jump maps (Sec. 3)
+# Jump maps (Sec. 4)
 # --------------------------------------------------------------------------
 def single_jump_map(N: int, M: int) -> np.ndarray:
     """J1[gamma, k, l]: index after moving one particle k -> l; -1 if n_k = 0."""
@@ -145,7 +147,7 @@ def removal_count(M: int, occ) -> int:
 
 
 def double_jump_map(N: int, M: int):
-    """Variable-length rows of Sec. 3: returns (row_off[Nc+1], data).
+    """Variable-length rows of Sec. 4: returns (row_off[Nc+1], data).
 
     Row gamma holds one stride of M*M entries per allowed removal pair
     (k <= q, lexicographic); entry s*M + l of a stride is the index after
@@ -198,6 +200,9 @@ def dense_hamiltonian(N: int, M: int, h, W) -> np.ndarray:
 
 
 def column_terms(N: int, M: int, h, W, gamma: int) -> int:
+    """Operator strings with a nonzero coefficient that do not annihilate
+    configuration gamma (Eqs. noninteracting, interacting), counted before
+    equal targets are merged."""
     hh = _cplx(h, (M, M))
     WW = None if W is None else _cplx(W, (M, M, M, M))
     return int(_load().oracle_column_terms(N, M, _ptr(hh), None if WW is None else _ptr(WW), int(gamma)))
@@ -237,7 +242,7 @@ def rho2(N: int, M: int, C) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
-# Time evolution (the propagator of the SIL integrator named in Sec. 1)
+# Time evolution (the propagator of the SIL integrator named in Sec. 2)
 # --------------------------------------------------------------------------
 def evolve(N: int, M: int, h, W, C, dt: float) -> np.ndarray:
     """exp(-i H dt) C for a tiny space: H = U diag(E) U^H from the dense
@@ -254,7 +259,7 @@ def evolve(N: int, M: int, h, W, C, dt: float) -> np.ndarray:
 # --------------------------------------------------------------------------
 def sector_indices(N: int, M: int, Q: int) -> np.ndarray:
     """Full-space indices, ascending, of the configurations with
-    sum_i i n_i = Q.  For the plane-wave orbitals of Sec. 5 (orbital i has
+    sum_i i n_i = Q.  For the plane-wave orbitals of Sec. 6 (orbital i has
     momentum (i - floor(M/2)) 2 pi / L) this is the sector of total momentum
     (Q - N floor(M/2)) 2 pi / L, which H preserves when h is diagonal and
     W_kqsl = 0 unless k + q = s + l.  The sector's basis is ordered as the
@@ -274,7 +279,7 @@ def sector_apply(N: int, M: int, Q: int, h, W, Cs) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
-# Lanczos with complete re-orthogonalisation (Sec. 5)
+# Lanczos with complete re-orthogonalisation (Sec. 6)
 # --------------------------------------------------------------------------
 def lanczos_ground(apply, v0: np.ndarray, max_iter: int, tol: float = 1e-13):
     """Lowest eigenvalue of a Hermitian operator by Lanczos.

@@ -8,7 +8,7 @@
  * paper states it, in IEEE double precision with a fixed loop order.
  *
  * Conventions (Andriati & Gammal, arXiv:2005.13679):
- *   - orbitals are numbered 0..M-1 (Sec. 2, "Mapping Fock states to integers");
+ *   - orbitals are numbered 0..M-1 (Sec. 3, "Mapping Fock states to integers");
  *   - an occupation vector n[0..M-1] holds N particles in total (Eq. constraint);
  *   - complex numbers are stored interleaved (re, im);
  *   - h[k*M + l] multiplies a^dag_k a_l;
@@ -42,7 +42,7 @@ int64_t oracle_nc(int64_t n, int64_t m)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Algorithm 1 (Get index from a configuration), Sec. 2.  The index is the  */
+/* Algorithm 1 (Get index from a configuration), Sec. 3.  The index is the  */
 /* total cost of Eq. TotalCost: going from the highest orbital down to      */
 /* orbital 1, each particle placed in orbital m adds N_c(s, m), where s is  */
 /* the number of particles still in the basket.                            */
@@ -64,7 +64,7 @@ int64_t oracle_rank(int N, int M, const int32_t *n)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Algorithm 2 (Build configuration from index), Sec. 2.  Starting from the */
+/* Algorithm 2 (Build configuration from index), Sec. 3.  Starting from the */
 /* top orbital with all N particles in the basket, a particle is put in     */
 /* orbital m whenever the remaining index is at least its cost N_c(s, m);  */
 /* otherwise the search moves one orbital down.  What is left in the basket */
@@ -97,7 +97,7 @@ void oracle_unrank_batch(int N, int M, const int64_t *idx, int64_t count, int32_
 }
 
 /* ------------------------------------------------------------------------ */
-/* Single-jump map (Sec. 3, "Mapping routines"): for every configuration    */
+/* Single-jump map (Sec. 4, "Mapping routines"): for every configuration    */
 /* gamma and every pair (k, l), the index of the configuration reached by   */
 /* removing one particle from k and placing it in l, or -1 when orbital k   */
 /* is empty.  Layout [Nc][M][M].  Built by definition: Alg. 2, edit, Alg. 1.*/
@@ -124,7 +124,7 @@ void oracle_single_jump_map(int N, int M, int32_t *out)
 
 /* A pair of annihilations a_q a_k (k <= q) can act on n iff both orbitals   */
 /* hold a particle, and, when k == q, the orbital holds at least two        */
-/* (a_k a_k on a single particle gives zero).  Sec. 3 and Fig. 4.           */
+/* (a_k a_k on a single particle gives zero).  Sec. 4 and Fig. 4.           */
 static int removal_allowed(const int32_t *n, int k, int q)
 {
     if (k == q) return n[k] >= 2;
@@ -142,7 +142,7 @@ int32_t oracle_removal_count(int M, const int32_t *n)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Double-jump map with variable-length rows (Sec. 3 and Fig. 4).  Row gamma */
+/* Double-jump map with variable-length rows (Sec. 4 and Fig. 4).  Row gamma */
 /* lists, for every allowed removal pair (k <= q) in lexicographic order, a */
 /* stride of M*M entries: entry s*M + l is the index of the configuration   */
 /* after removing one particle from k and one from q and adding one to s    */
@@ -182,7 +182,7 @@ void oracle_double_jump_map(int N, int M, int64_t *row_off, int32_t *out)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Bosonic ladder operators on an occupation vector (Sec. 1 commutation     */
+/* Bosonic ladder operators on an occupation vector (Sec. 2 commutation     */
 /* relation): a_k |..n_k..> = sqrt(n_k) |..n_k - 1..> (zero if n_k = 0) and  */
 /* a^dag_k |..n_k..> = sqrt(n_k + 1) |..n_k + 1..>.  *amp accumulates the   */
 /* square-root factors; the return value is 0 when the state vanishes.     */

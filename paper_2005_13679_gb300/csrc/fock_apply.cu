@@ -757,6 +757,8 @@ static int apply_path(const fock_space *sp, const fock_ham *ham, const void *C, 
     in_exp = words + 1;
     Cin = (const char *)ws + kWsHeader;
   }
+  if (precision == FOCK_PREC_F32_MIXED && ws && ws_bytes >= 3 * sizeof(int))
+    FOCK_CUDA_TRY(cudaMemsetAsync((int *)ws + 2, 0, sizeof(int), stream));   // status word of this apply
   const bool maps = map != nullptr;
   if (ham->ev_start) FOCK_CUDA_TRY(cudaEventRecord(ham->ev_start, stream));
   bool stop_recorded = false;
@@ -820,6 +822,7 @@ static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Ci
         t.tc_a = nullptr;
         t.tc_er = nullptr;
         t.status = nullptr;
+        t.polls = 0;
         t.phase1_done = ham->ev_stop;
         t.phases = 3;
         t.g_begin = 0;
@@ -829,8 +832,7 @@ static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Ci
         if (path == FOCK_PATH_TWOPHASE_TC) {
           t.tc_a = mixed ? ham->d_tc_ma : ham->d_tc_a;
           t.tc_er = mixed ? ham->d_tc_mer : ham->d_tc_er;
-          t.status = (int *)ws + 2;
-          if (mixed) FOCK_CUDA_TRY(cudaMemsetAsync(t.status, 0, sizeof(int), stream));
+          t.status = (int *)ws + 2;                        // cleared at the start of the apply
         }
         auto launch = [&]() {
           return path == FOCK_PATH_TWOPHASE_TC ? fock_launch_twophase_tc(t, mixed, sp->device, stream)
@@ -955,6 +957,27 @@ extern "C" int fock_apply_H(const fock_space *sp, const fock_ham *ham, const voi
                              workspace_bytes, (cudaStream_t)stream);
 }
 
+extern "C" int fock_apply_check(const fock_space *sp, const fock_ham *ham, const void *workspace_dev, int noalloc,
+                                void *stream) {
+  if (!sp || !ham || ham->sp != sp) return FOCK_ERR_ARG;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return FOCK_ERR_CUDA;
+  if (cur != sp->device) return FOCK_ERR_DEVICE;
+  const void *ws = workspace_dev ? workspace_dev : ham->ws;
+  if (noalloc) {
+    void *p = nullptr;
+    const int st = fock_noalloc_scratch(sp->device, &p);
+    if (st) return st;
+    ws = p;
+  }
+  if (!ws) return FOCK_OK;                               // no workspace: the tensor-core path never ran
+  int status = 0;
+  FOCK_CUDA_TRY(cudaMemcpyAsync(&status, (const int *)ws + 2, sizeof(int), cudaMemcpyDeviceToHost,
+                                (cudaStream_t)stream));
+  FOCK_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  return status ? FOCK_ERR_TIMEOUT : FOCK_OK;
+}
+
 extern "C" int fock_apply_H_host(const fock_space *sp, const fock_ham *ham, const void *C_host,
                                  void *sigma_host, int32_t nrhs, int precision, int arm, void *stream) {
   int st = check_apply_args(sp, ham, nrhs, precision, arm);
@@ -995,7 +1018,7 @@ extern "C" int fock_apply_H_host(const fock_space *sp, const fock_ham *ham, cons
   if (!ov.done) FOCK_CUDA_TRY(cudaMemcpyAsync(sigma_host, H->hb_out, bytes, cudaMemcpyDeviceToHost, s));
   FOCK_CUDA_TRY(cudaStreamSynchronize(s));
   FOCK_CUDA_TRY(cudaStreamSynchronize(H->hb_copy));
-  if (precision == FOCK_PREC_F64) {
+  if (H->ws && precision != FOCK_PREC_F64_NATIVE) {     // the other two clear the word at their start
     int status = 0;
     FOCK_CUDA_TRY(cudaMemcpy(&status, (const int *)H->ws + 2, sizeof(int), cudaMemcpyDeviceToHost));
     if (status) return FOCK_ERR_TIMEOUT;

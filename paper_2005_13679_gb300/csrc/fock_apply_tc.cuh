@@ -4,36 +4,51 @@
 // Phase 1 is the dense product Y = R X with R the P x P reduced coefficients
 // and X[a][n'] = B_a(n') C[n' + a] over the (N-2)-particle configurations.  In
 // real form (rows and columns interleaved as (Re, Im)) it is a 2P x 2P matrix
-// times a 2P x (configurations x rhs) matrix.  Both factors are split into five
+// times a 2P x (configurations x rhs) matrix.  Both factors are split into
 // signed base-2^9 digits with a power-of-two scale per row of R and per column
 // of X (the error-free splitting of Ozaki, Ogita, Oishi and Rump, "Error-free
 // transformations of matrix multiplication by using fast routines of matrix
 // multiplication", Numer. Algorithms 59 (2012)):
 //
-//     R~[rho][k] = 2^(e_rho - 8) sum_{i=1..5} rho_i 2^(-9(i-1)),   |rho_i| <= 256,
-//     X~[k][c]   = 2^(e_c - 8)   sum_{j=1..5} xi_j  2^(-9(j-1)),   |xi_j|  <= 265.
+//     R~[rho][k] = 2^(e_rho - 8) sum_{i=1..6} rho_i 2^(-9(i-1)) + dR,   |rho_i| <= 256,
+//     X[k][c]    = 2^(e_c - 8)   sum_{j=1..5} xi_j  2^(-9(j-1)) + dX,
+//                  |xi_1|, |xi_2|, |xi_5| <= 256, |xi_3| <= 268, |xi_4| <= 513,
 //
-// Digits are integers held exactly in fp16.  For a level l = i + j the sum
-// S_l = sum_{i+j=l} sum_k rho_i xi_j has at most 5 pairs x 42 terms of
-// magnitude <= 256 * 265, below 2^24, so the tensor core's FP32 accumulation
-// of S_l is exact whatever its internal order.  Levels 2..6 are kept:
+// with |R~[rho][k]| < 2^e_rho over the row and |X[k][c]| < 2^e_c over the
+// column.  Digits are integers, exact in fp16.  The level sums
+// S_l = sum_{i+j=l} sum_k rho_i xi_j, l = 2..7, hold at most five digit pairs,
+// so |S_l| <= 2P * 256 * (256 + 256 + 268 + 513 + 256) = 16,654,848 < 2^24 at
+// M = 6 (2P = 42): every partial sum is an integer below 2^24 and the tensor
+// core's FP32 accumulation of S_l is exact in any order.  The epilogue forms
 //
-//     Y = 2^(e_rho + e_c - 16) sum_{l=2..6} 2^(-9(l-2)) S_l,
+//     Y = 2^(e_rho + e_c - 16) sum_{l=2..7} 2^(-9(l-2)) S_l
 //
-// whose dropped terms and digit remainders are below 2^-44 of
-// max|R~ row| * max|X~ column| * 2P; the five level sums are combined into an
-// FP32 pair (TwoSum) for phase 2.
+// as an FP32 pair.  What the product leaves out, per entry (rho, c):
+//   * levels 8..11 (i + j >= 8): at most 2P * 256 * 1293 * 2^-70 2^(e_rho+e_c),
+//     below 2^-46.2 2^(e_rho + e_c);
+//   * the remainder of R~ after six digits, |dR| <= 2^-54 2^e_rho: below
+//     2P 2^-54 2^(e_rho + e_c);
+//   * the remainder of X after five digits, |dX| <= (2^-45 + 2^-59) 2^e_c:
+//     below 2^-45 2^e_c ||R~_rho||_1.
+// With 2^e_c < 2 max_k |X[k][c]| and 2^e_rho < 2 max_k |R~[rho][k]| <= 2 ||R~_rho||_1,
+// and the pair rounding of the combination (below 2^-46 of the same scale),
+//
+//     |Y^[rho][c] - Y[rho][c]| <= 2^-42.5 ||R~_rho||_1 max_k |X[k][c]|,
+//
+// i.e. 1.6e-13 of the largest value the row can produce on that column.
 //
 // The MMA computes the transposed product: its M = 128 rows are the tile's
 // (configuration, rhs) columns, so tensor-memory lane c holds everything of
-// column c, and its N columns are (real row, level) combinations.  Real rows
-// come in groups of three, 16 tensor-memory columns per group: column
-// 16 g + 5 i + (6 - l) holds level l of real row 3 g + i, and column 15 (the
-// spare of group 0) receives the column exponent, which the producer stores at
-// K position K1 - 1 and a unit row of the coefficient image copies.  An
-// epilogue thread reads its own lane: two groups (32 columns) hold three
-// complex rows (Re and Im), so no data crosses lanes.  K is ordered
-// [digits 1..3 of every real index, interleaved | digits 4, 5 interleaved].
+// column c, and its N columns are (real row, level) combinations in two
+// blocks: columns 3 rho + (7 - l) hold levels l = 7, 6, 5 of real row rho
+// (0 <= rho < 2P), column 3 * 2P receives the column exponent, and from N2 on
+// columns N2 + 3 rho + (4 - l) hold levels 4, 3, 2.  K is ordered
+// [digits 1..3 of every real index, interleaved, and the column exponent |
+//  digits 4, 5 interleaved].  Digits 4 and 5 of X only meet levels 5..7, so
+// the product runs as two MMA chains into the same accumulators: part 1, K1
+// positions (digits 1..3) against all N1 columns, and part 2, K2 positions
+// (digits 4, 5) against the first N2 columns only.  An epilogue thread reads
+// its own lane, so no data crosses lanes.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -45,22 +60,28 @@ constexpr int kTcCols = 128;        // (configuration, rhs) columns per tile = M
 constexpr int kTcProducers = 128;   // producer group: 4 warps, one thread per column
 constexpr int kTcThreads = 416;     // two producer groups (warps 0-3 even tiles, 4-7 odd tiles),
                                     // warps 8-11 epilogue (warp 8 + q: tile columns 32q .. 32q+31), warp 12 MMA
-constexpr int kTcTmemCols = 512;    // two tiles x NT (<= 224) columns, at 0 and 256
+constexpr int kTcTmemCols = 512;    // two tiles x NT (<= 256) columns, at 0 and 256
 constexpr uint32_t kTcPolls = 1u << 20;
 constexpr int kTcExpCol = 15;       // tensor-memory column of the column exponent
 
 // Shape of the real-form product for M orbitals (2 <= M <= 6).
 struct TcShape {
-  int P, R2, NG, NT, K1, K2, KT;
+  int P, R2, K1, K2, KT, N2, N1;
   __host__ __device__ constexpr explicit TcShape(int m)
-      : P(m * (m + 1) / 2), R2(m * (m + 1)), NG((m * (m + 1) + 2) / 3), NT(16 * ((m * (m + 1) + 2) / 3)),
-        K1((3 * m * (m + 1) + 15) / 16 * 16), K2((2 * m * (m + 1) + 15) / 16 * 16),
-        KT((3 * m * (m + 1) + 15) / 16 * 16 + (2 * m * (m + 1) + 15) / 16 * 16) {}
-  // bytes of the coefficient image (NT rows x KT, fp16) and of one digit tile
-  __host__ __device__ constexpr int r_bytes() const { return NT * KT * 2; }
+      : P(m * (m + 1) / 2), R2(m * (m + 1)), K1((3 * m * (m + 1) + 1 + 15) / 16 * 16),
+        K2((2 * m * (m + 1) + 15) / 16 * 16),
+        KT((3 * m * (m + 1) + 1 + 15) / 16 * 16 + (2 * m * (m + 1) + 15) / 16 * 16),
+        N2((3 * m * (m + 1) + 1 + 15) / 16 * 16),
+        N1(((3 * m * (m + 1) + 1 + 15) / 16 * 16 + 3 * m * (m + 1) + 15) / 16 * 16) {}
+  // bytes of the coefficient image: part 1 (N1 rows x K1), then part 2 (N2 rows x K2), fp16
+  __host__ __device__ constexpr int r1_bytes() const { return N1 * K1 * 2; }
+  __host__ __device__ constexpr int r_bytes() const { return N1 * K1 * 2 + N2 * K2 * 2; }
+  // bytes of one digit tile (128 columns x KT)
   __host__ __device__ constexpr int b_bytes() const { return kTcCols * KT * 2; }
   // K position of the column exponent (the last of part 1, never a digit)
   __host__ __device__ constexpr int exp_pos() const { return K1 - 1; }
+  // tensor-memory column of the column exponent
+  __host__ __device__ constexpr int exp_col() const { return 3 * R2; }
   // additions swept by the producer, padding included, so that every 16-byte
   // chunk of both K parts is written
   __host__ __device__ constexpr int a_end() const {
@@ -68,19 +89,21 @@ struct TcShape {
     const int m = P > c1 ? (P > c2 ? P : c2) : (c1 > c2 ? c1 : c2);
     return (m + 3) / 4 * 4;
   }
-  // tensor-memory column of level l of real row rho
-  __host__ __device__ constexpr int col(int rho, int l) const { return 16 * (rho / 3) + 5 * (rho % 3) + (6 - l); }
+  // tensor-memory column of level l (2..7) of real row rho
+  __host__ __device__ constexpr int col(int rho, int l) const {
+    return l >= 5 ? 3 * rho + (7 - l) : N2 + 3 * rho + (4 - l);
+  }
 };
 
-// Shared-memory layout of the kernel for a policy with an nt x kt coefficient
-// image, kt-deep digit tiles, r2 row exponents and a square-root table of
-// sq_bytes per entry.
+// Shared-memory layout of the kernel for a policy with an image of r_bytes,
+// kt-deep digit tiles, r2 row exponents and a square-root table of sq_bytes
+// per entry.
 struct TcSmem {
   size_t off_r, off_b0, off_b1, off_er, off_mod, off_sat, off_sq, off_bar, total;
-  __host__ __device__ TcSmem(int nt, int kt, int r2, int M, int xdim, int nsq, int sq_bytes) {
+  __host__ __device__ TcSmem(int r_bytes, int kt, int r2, int M, int xdim, int nsq, int sq_bytes) {
     const int rows = M > 1 ? M - 1 : 1;
     size_t o = 0;
-    off_r = o;    o += (size_t)nt * kt * 2;
+    off_r = o;    o += (size_t)r_bytes;
     off_b0 = o;   o += (size_t)kTcCols * kt * 2;
     off_b1 = o;   o += (size_t)kTcCols * kt * 2;
     off_er = o;   o = fock_align16(o + 4 * (size_t)r2);
@@ -124,38 +147,42 @@ __device__ __forceinline__ void tc_scale(float &h, float &l, int e) {
 
 constexpr float kTcMagic = 12582912.f;   // 1.5 * 2^23
 
-// d = x m rounded to the nearest integer (ties to even) and the exact
-// remainder r = x m - d, for m a power of two and |x m| < 2^22.
-__device__ __forceinline__ float tc_digit(float x, float m, float &r) {
-  const float d = __fsub_rn(__fmaf_rn(x, m, kTcMagic), kTcMagic);
-  r = __fmaf_rn(x, m, -d);
+// One digit on both packed lanes without negations: from x (true sign) with
+// m and nm = -m, d = RN(x m) and y = d - x m (the remainder, negated); from a
+// negated remainder y with the constants -512 and 512, d = RN(512 r) and the
+// next negated remainder d - 512 r.  |x m| < 2^22, m a power of two, so
+// every step is exact (the 1.5 * 2^23 rounding of the FP32 significand).
+__device__ __forceinline__ fp2_t tc_digit2(fp2_t x, fp2_t m, fp2_t nm, fp2_t &y) {
+  const fp2_t mg = fp2_make(kTcMagic, kTcMagic);
+  const fp2_t d = fp2_sub(fp2_fma(x, m, mg), mg);
+  y = fp2_fma(x, nm, d);
   return d;
 }
 
-__device__ __forceinline__ float tc_round(float x, float m) {
-  return __fsub_rn(__fmaf_rn(x, m, kTcMagic), kTcMagic);
-}
-
-// Digits of v = (xh + xl) 2^E, the pair of one real value of X at its column
-// scale (f = 2^E, f18 = 2^(E+18), |xh f| < 256, |xl f| <= 3 2^-16):
+// Digits of v = (xh + xl) 2^E on both lanes (the real and imaginary parts of
+// one complex value of X at its column scale; f = 2^E, f18 = 2^(E+18),
+// |xh f| < 256, |xl f| <= 3 2^-16):
 //     v = c1 + c2 2^-9 + c3 2^-18 + c4 2^-27 + c5 2^-36 + r,   |r| <= 2^-37 (+ 2^-51).
 // The high word gives c1..c4 with exact remainders, the low word adds to c3
 // and c4, the two remainders share c5 (their FP32 sum is rounded far below
 // the digit's unit), and one carry folds c5 back into [-256, 256]:
-// |c1|, |c2|, |c5| <= 256, |c3| <= 268, |c4| <= 513.
-__device__ __forceinline__ void tc_digits(float xh, float xl, float f, float f18, float (&c)[5]) {
-  float r, u;
-  c[0] = tc_digit(xh, f, r);
-  c[1] = tc_digit(r, 512.f, r);
-  const float d3 = tc_digit(r, 512.f, r);
-  const float d4 = tc_digit(r, 512.f, r);
-  const float e3 = tc_digit(xl, f18, u);
-  const float e4 = tc_digit(u, 512.f, u);
-  const float c5 = tc_round(__fadd_rn(r, u), 512.f);
-  const float q = tc_round(c5, 1.f / 512.f);
-  c[4] = __fmaf_rn(q, -512.f, c5);
-  c[3] = __fadd_rn(__fadd_rn(d4, e4), q);
-  c[2] = __fadd_rn(d3, e3);
+// |c1|, |c2|, |c5| <= 256, |c3| <= 268, |c4| <= 513.  27 packed operations.
+__device__ __forceinline__ void tc_digits2(fp2_t xh, fp2_t xl, fp2_t f, fp2_t nf, fp2_t f18, fp2_t nf18,
+                                           fp2_t (&c)[5]) {
+  const fp2_t k512 = fp2_make(512.f, 512.f), n512 = fp2_make(-512.f, -512.f);
+  const fp2_t i512 = fp2_make(1.f / 512.f, 1.f / 512.f), mg = fp2_make(kTcMagic, kTcMagic);
+  fp2_t y, u;
+  c[0] = tc_digit2(xh, f, nf, y);            // y = -(remainder)
+  c[1] = tc_digit2(y, n512, k512, y);
+  const fp2_t d3 = tc_digit2(y, n512, k512, y);
+  const fp2_t d4 = tc_digit2(y, n512, k512, y);
+  const fp2_t e3 = tc_digit2(xl, f18, nf18, u);
+  const fp2_t e4 = tc_digit2(u, n512, k512, u);
+  const fp2_t c5 = fp2_sub(fp2_fma(fp2_add(y, u), n512, mg), mg);    // RN(512 (r_hi + r_lo))
+  const fp2_t q = fp2_sub(fp2_fma(c5, i512, mg), mg);
+  c[4] = fp2_fma(q, n512, c5);
+  c[3] = fp2_add(fp2_add(d4, e4), q);
+  c[2] = fp2_add(d3, e3);
 }
 
 __device__ __forceinline__ uint32_t tc_pack(float a, float b) {
@@ -197,9 +224,10 @@ __device__ __forceinline__ void tc_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc_smem_addr(bar)) : "memory");
 }
 
-// Bounded wait that also gives up as soon as another role raised the abort flag.
-__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile int *flag) {
-  for (uint32_t i = 0; i < kTcPolls; ++i) {
+// Bounded wait (at most `polls` polls) that also gives up as soon as another
+// role raised the abort flag.
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile int *flag, uint32_t polls) {
+  for (uint32_t i = 0; i < polls; ++i) {
     if (tc_mbar_try_wait(bar, parity)) return true;
     if (*flag) return false;
   }
@@ -252,7 +280,7 @@ __device__ __forceinline__ void tc_produce(const TwoPhaseArgs &t, uint32_t tile,
     const int s = pr.s[ai], l = pr.l[ai];
     v[ai] = __ldg(C + (size_t)(base - U[s] - V[l]) * nrhs + jr);
   }
-  uint32_t ebits = 0;
+  float vmax = 0.f;
 #pragma unroll
   for (int ai = 0; ai < P; ++ai) {
     const int s = pr.s[ai], l = pr.l[ai];
@@ -261,9 +289,9 @@ __device__ __forceinline__ void tc_produce(const TwoPhaseArgs &t, uint32_t tile,
     fp2_dprod(fp2_make(v[ai].x, v[ai].y), fp2_make(v[ai].z, v[ai].w), fp2_make(amp.x, amp.x),
               fp2_make(amp.y, amp.y), Xh, Xl);
     v[ai] = make_float4(fp2_x(Xh), fp2_y(Xh), fp2_x(Xl), fp2_y(Xl));   // (Re hi, Im hi, Re lo, Im lo)
-    ebits = max(ebits, max(__float_as_uint(v[ai].x) & 0x7f800000u, __float_as_uint(v[ai].y) & 0x7f800000u));
+    vmax = fmaxf(vmax, fmaxf(fabsf(v[ai].x), fabsf(v[ai].y)));
   }
-  const int field = (int)(ebits >> 23);
+  const int field = (int)((__float_as_uint(vmax) >> 23) & 0xffu);
   const int e_c = field > 0 ? field - 126 : 0;         // |X| < 2^e_c; all-zero column: digits 0
   int E = 8 - e_c;                                      // v = X 2^E, |v| < 256
   if (E > 109) {                                        // columns ~2^-100 below the largest amplitude:
@@ -275,22 +303,25 @@ __device__ __forceinline__ void tc_produce(const TwoPhaseArgs &t, uint32_t tile,
     E -= 64;
   }
   const float f = tc_pow2(E), f18 = tc_pow2(E + 18);
+  const fp2_t F = fp2_make(f, f), NF = fp2_make(-f, -f), F18 = fp2_make(f18, f18), NF18 = fp2_make(-f18, -f18);
 
   unsigned char *colbase = bbuf + (size_t)(cl >> 3) * (CHT * 128) + (cl & 7) * 16;
 #pragma unroll
   for (int bi = 0; bi < AE / 4; ++bi) {
-    float dig[8][5];
+    fp2_t dig[4][5];                                    // four additions, (Re, Im) lanes
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int k = 8 * bi + r;                         // real index 2a + (0 Re, 1 Im)
-      if (k < 2 * P) {
-        const float4 x = v[k >> 1];
-        tc_digits((k & 1) ? x.y : x.x, (k & 1) ? x.w : x.z, f, f18, dig[r]);
+    for (int r = 0; r < 4; ++r) {
+      const int ai = 4 * bi + r;
+      if (ai < P) {
+        const float4 x = v[ai];
+        tc_digits2(fp2_make(x.x, x.y), fp2_make(x.z, x.w), F, NF, F18, NF18, dig[r]);
       } else {
 #pragma unroll
-        for (int j = 0; j < 5; ++j) dig[r][j] = 0.f;
+        for (int j = 0; j < 5; ++j) dig[r][j] = 0ull;
       }
     }
+    // digit j (1-based) of real index 8 bi + rr, rr = 2 (addition) + (0 Re, 1 Im)
+    auto D = [&](int rr, int j) -> float { return (rr & 1) ? fp2_y(dig[rr >> 1][j - 1]) : fp2_x(dig[rr >> 1][j - 1]); };
     // part 1: positions 3k + (j - 1), j = 1..3; the exponent at exp_pos()
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
@@ -300,8 +331,8 @@ __device__ __forceinline__ void tc_produce(const TwoPhaseArgs &t, uint32_t tile,
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int p0 = 8 * ch + 2 * e, p1 = p0 + 1;
-          const float lo = dig[p0 / 3][p0 % 3];
-          const float hi = 8 * chunk + 2 * e + 1 == sh.exp_pos() ? (float)e_c : dig[p1 / 3][p1 % 3];
+          const float lo = D(p0 / 3, p0 % 3 + 1);
+          const float hi = 8 * chunk + 2 * e + 1 == sh.exp_pos() ? (float)e_c : D(p1 / 3, p1 % 3 + 1);
           w[e] = tc_pack(lo, hi);
         }
         *(uint4 *)(colbase + chunk * 128) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -314,27 +345,36 @@ __device__ __forceinline__ void tc_produce(const TwoPhaseArgs &t, uint32_t tile,
       if (chunk < CH2) {
         uint32_t w[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) w[e] = tc_pack(dig[(8 * ch + 2 * e) / 2][3], dig[(8 * ch + 2 * e) / 2][4]);
+        for (int e = 0; e < 4; ++e) w[e] = tc_pack(D((8 * ch + 2 * e) / 2, 4), D((8 * ch + 2 * e) / 2, 5));
         *(uint4 *)(colbase + (CH1 + chunk) * 128) = make_uint4(w[0], w[1], w[2], w[3]);
       }
     }
   }
 }
 
-// Combination of the five level sums of one real row into an FP32 pair.
-__device__ __forceinline__ void tc_combine(float s2, float s3, float s4, float s5, float s6, float &hi, float &lo) {
-  const float a3 = __fmul_rn(s3, 1.f / 512.f);
-  const float a4 = __fmul_rn(s4, 1.f / 262144.f);
-  const float a56 = __fmaf_rn(s6, 1.f / 68719476736.f, __fmul_rn(s5, 1.f / 134217728.f));
-  float s = __fadd_rn(s2, a3);
-  float bb = __fsub_rn(s, s2);
-  float e = __fadd_rn(__fsub_rn(s2, __fsub_rn(s, bb)), __fsub_rn(a3, bb));
-  const float s1 = __fadd_rn(s, a4);
-  bb = __fsub_rn(s1, s);
-  e = __fadd_rn(e, __fadd_rn(__fsub_rn(s, __fsub_rn(s1, bb)), __fsub_rn(a4, bb)));
-  e = __fadd_rn(e, a56);
-  hi = __fadd_rn(s1, e);
-  lo = __fsub_rn(e, __fsub_rn(hi, s1));
+// Combination of the six level sums of two real rows (packed lanes) into
+// FP32 pairs: V = s2 + s3 2^-9 + s4 2^-18 + s5 2^-27 + s6 2^-36 + s7 2^-45
+// with the s_l exact integers below 2^24.  The scalings are exact; the first
+// four terms are added by TwoSum (their errors collected in e), the last two
+// (below 2^-12 of the unit) join e directly.  The rounding of e is below
+// 2^-46 of the largest partial sum, i.e. of sum_k |R~ X| for the row.
+__device__ __forceinline__ void tc_combine2(fp2_t s2, fp2_t s3, fp2_t s4, fp2_t s5, fp2_t s6, fp2_t s7, fp2_t &hi,
+                                            fp2_t &lo) {
+  const fp2_t a3 = fp2_mul(s3, fp2_make(0x1p-9f, 0x1p-9f));
+  const fp2_t a4 = fp2_mul(s4, fp2_make(0x1p-18f, 0x1p-18f));
+  const fp2_t a5 = fp2_mul(s5, fp2_make(0x1p-27f, 0x1p-27f));
+  fp2_t s = fp2_add(s2, a3);
+  fp2_t bb = fp2_sub(s, s2);
+  fp2_t e = fp2_add(fp2_sub(s2, fp2_sub(s, bb)), fp2_sub(a3, bb));
+  fp2_t t = fp2_add(s, a4);
+  bb = fp2_sub(t, s);
+  e = fp2_add(e, fp2_add(fp2_sub(s, fp2_sub(t, bb)), fp2_sub(a4, bb)));
+  s = fp2_add(t, a5);
+  bb = fp2_sub(s, t);
+  e = fp2_add(e, fp2_add(fp2_sub(t, fp2_sub(s, bb)), fp2_sub(a5, bb)));
+  e = fp2_fma(s7, fp2_make(0x1p-45f, 0x1p-45f), fp2_fma(s6, fp2_make(0x1p-36f, 0x1p-36f), e));
+  hi = fp2_add(s, e);
+  lo = fp2_sub(e, fp2_sub(hi, s));
 }
 
 // ---------------------------------------------------------------------------
@@ -425,54 +465,72 @@ __device__ __forceinline__ void tc_produce_mixed(const TwoPhaseArgs &t, uint32_t
 template <int M>
 struct TcPolDF {                                         // FP64-class: exact digits, level sums
   static constexpr TcShape sh{M};
-  static constexpr int NT = sh.NT, KT = sh.KT, R2 = sh.R2, R_BYTES = sh.r_bytes();
+  static constexpr int NT = sh.N1, KT = sh.KT, R2 = sh.R2, R_BYTES = sh.r_bytes();
   using sq_t = float2;
   __device__ static void produce(const TwoPhaseArgs &t, uint32_t tile, uint32_t total, int cl, unsigned char *bbuf,
                                  const uint32_t *s_mod, const uint32_t *s_sat, const void *s_sq) {
     tc_produce<M>(t, tile, total, cl, bbuf, s_mod, s_sat, (const float2 *)s_sq);
   }
-  // Lane-local epilogue: 32 tensor-memory columns (three complex rows) per
-  // pass; the next pass's load overlaps the combination of the current one.
+  // The two MMA chains of one tile into the accumulators at d: part 1 (digits
+  // 1..3 and the exponent, K1) against all N1 columns, then part 2 (digits 4,
+  // 5, K2) against the first N2 columns (levels 5..7).
+  __device__ static void issue(uint32_t d, uint32_t x_addr, uint32_t r_addr) {
+    constexpr int CHT = KT / 8, CH1 = sh.K1 / 8, CH2 = sh.K2 / 8;
+    constexpr uint32_t idesc1 = tc_idesc_f16(kTcCols, sh.N1), idesc2 = tc_idesc_f16(kTcCols, sh.N2);
+    const uint32_t r2_addr = r_addr + (uint32_t)sh.r1_bytes();
+#pragma unroll
+    for (int kk = 0; kk < sh.K1 / 16; ++kk)
+      tc_mma_f16(d, tc_desc_kmajor(x_addr + kk * 256, 128, CHT * 128), tc_desc_kmajor(r_addr + kk * 256, 128, CH1 * 128),
+                 idesc1, kk > 0);
+#pragma unroll
+    for (int kk = 0; kk < sh.K2 / 16; ++kk)
+      tc_mma_f16(d, tc_desc_kmajor(x_addr + CH1 * 128 + kk * 256, 128, CHT * 128),
+                 tc_desc_kmajor(r2_addr + kk * 256, 128, CH2 * 128), idesc2, 1u);
+  }
+  // Lane-local epilogue in passes of four complex rows: levels 7, 6, 5 of a
+  // complex row r sit in columns 6r .. 6r+5 (Re row, then Im row) and levels
+  // 4, 3, 2 in N2 + 6r .. N2 + 6r + 5, read as 8-column loads.  The last pass
+  // runs first, so the column exponent is read with the first loads.
   __device__ static void drain(const TwoPhaseArgs &t, uint32_t tq, uint32_t colg, bool live, const int *s_er) {
-    constexpr int NPASS = (NT + 31) / 32;
-    constexpr TcShape shp(M);
+    constexpr int P = sh.P, NPASS = (P + 3) / 4;
     float4 *__restrict__ Y = (float4 *)t.Y;
-    float v[32];
-    tc_ld_x16(tq, *reinterpret_cast<float(*)[16]>(&v[0]));
-    tc_ld_x16(tq + 16u, *reinterpret_cast<float(*)[16]>(&v[16]));
+    const float ecf = tc_ld_x1(tq + (uint32_t)sh.exp_col());
     int ec = 0;
 #pragma unroll
-    for (int pass = 0; pass < NPASS; ++pass) {
+    for (int pass = NPASS - 1; pass >= 0; --pass) {
+      const int nrow = P - 4 * pass < 4 ? P - 4 * pass : 4;
+      const int nch = (6 * nrow + 7) / 8;
+      float A[24], B[24];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        if (c < nch) {
+          tc_ld_x8(tq + (uint32_t)(24 * pass + 8 * c), *reinterpret_cast<float(*)[8]>(&A[8 * c]));
+          tc_ld_x8(tq + (uint32_t)(sh.N2 + 24 * pass + 8 * c), *reinterpret_cast<float(*)[8]>(&B[8 * c]));
+        }
       tc_wait_ld();
-      float w[32];
+      if (pass == NPASS - 1) ec = (int)ecf - 16;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) w[i] = v[i];
-      if (pass + 1 < NPASS) {
-        tc_ld_x16(tq + (uint32_t)(32 * (pass + 1)), *reinterpret_cast<float(*)[16]>(&v[0]));
-        if (32 * (pass + 1) + 16 < NT)
-          tc_ld_x16(tq + (uint32_t)(32 * (pass + 1) + 16), *reinterpret_cast<float(*)[16]>(&v[16]));
-      }
-      if (pass == 0) ec = (int)w[kTcExpCol] - 16;
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const int r = 3 * pass + j;                      // complex row
-        if (2 * r < R2) {
-          float hv[2], lv[2];
-#pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const int rho = 2 * r + c;
-            const int b = shp.col(rho, 6) - 32 * pass;   // levels 6..2 at b .. b+4
-            tc_combine(w[b + 4], w[b + 3], w[b + 2], w[b + 1], w[b], hv[c], lv[c]);
-            const int e = s_er[rho] + ec;
-            if (e >= -126) {
-              const float sc = tc_pow2(e);
-              hv[c] = __fmul_rn(hv[c], sc);
-              lv[c] = __fmul_rn(lv[c], sc);
-            } else {
-              tc_scale(hv[c], lv[c], e);
-            }
+      for (int j = 0; j < 4; ++j) {
+        if (j < nrow) {
+          const int r = 4 * pass + j;                    // complex row
+          fp2_t hi, lo;
+          tc_combine2(fp2_make(B[6 * j + 2], B[6 * j + 5]), fp2_make(B[6 * j + 1], B[6 * j + 4]),
+                      fp2_make(B[6 * j], B[6 * j + 3]), fp2_make(A[6 * j + 2], A[6 * j + 5]),
+                      fp2_make(A[6 * j + 1], A[6 * j + 4]), fp2_make(A[6 * j], A[6 * j + 3]), hi, lo);
+          const int e0 = s_er[2 * r] + ec, e1 = s_er[2 * r + 1] + ec;
+          float4 y;
+          if (e0 >= -126 && e1 >= -126) {
+            const fp2_t sc = fp2_make(tc_pow2(e0), tc_pow2(e1));
+            hi = fp2_mul(hi, sc);
+            lo = fp2_mul(lo, sc);
+            y = make_float4(fp2_x(hi), fp2_y(hi), fp2_x(lo), fp2_y(lo));
+          } else {
+            float h0 = fp2_x(hi), h1 = fp2_y(hi), l0 = fp2_x(lo), l1 = fp2_y(lo);
+            tc_scale(h0, l0, e0);
+            tc_scale(h1, l1, e1);
+            y = make_float4(h0, h1, l0, l1);
           }
-          if (live) Y[twophase_yidx(r, colg, shp.P)] = make_float4(hv[0], hv[1], lv[0], lv[1]);
+          if (live) Y[twophase_yidx(r, colg, P)] = y;
         }
       }
     }
@@ -487,6 +545,15 @@ struct TcPolMixed {                                      // FP32-mixed: fp16 hi/
   __device__ static void produce(const TwoPhaseArgs &t, uint32_t tile, uint32_t total, int cl, unsigned char *bbuf,
                                  const uint32_t *s_mod, const uint32_t *s_sat, const void *s_sq) {
     tc_produce_mixed<M>(t, tile, total, cl, bbuf, s_mod, s_sat, (const float *)s_sq);
+  }
+  // One MMA chain of the tile: K = KT against all NT columns.
+  __device__ static void issue(uint32_t d, uint32_t x_addr, uint32_t r_addr) {
+    constexpr int CHT = KT / 8;
+    constexpr uint32_t idesc = tc_idesc_f16(kTcCols, NT);
+#pragma unroll
+    for (int kk = 0; kk < KT / 16; ++kk)
+      tc_mma_f16(d, tc_desc_kmajor(x_addr + kk * 256, 128, CHT * 128), tc_desc_kmajor(r_addr + kk * 256, 128, CHT * 128),
+                 idesc, kk > 0);
   }
   // Y = D 2^(e_rho + e_c - 30): the row scale 2^(15 - e_rho) of the image and
   // the column scale 2^(15 - e_c) of the digits taken out.
@@ -514,7 +581,7 @@ struct TcPolMixed {                                      // FP32-mixed: fp16 hi/
 
 template <class Pol, int M>
 __host__ __device__ inline TcSmem tc_smem_of(int xdim, int nsq) {
-  return TcSmem(Pol::NT, Pol::KT, Pol::R2, M, xdim, nsq, (int)sizeof(typename Pol::sq_t));
+  return TcSmem(Pol::R_BYTES, Pol::KT, Pol::R2, M, xdim, nsq, (int)sizeof(typename Pol::sq_t));
 }
 
 // ---------------------------------------------------------------------------
@@ -528,7 +595,6 @@ __host__ __device__ inline TcSmem tc_smem_of(int xdim, int nsq) {
 // ---------------------------------------------------------------------------
 template <int M, class Pol>
 __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPhaseArgs t) {
-  constexpr int NT = Pol::NT, CHT = Pol::KT / 8;
   const ApplyArgs<uint32_t> &a = t.a;
   extern __shared__ __align__(16) unsigned char smem[];
   const TcSmem L = tc_smem_of<Pol, M>(a.xdim, a.nsq);
@@ -583,7 +649,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
     const void *s_sq = smem + L.off_sq;
     unsigned char *bbuf = smem + (g ? L.off_b1 : L.off_b0);
     for (uint32_t k = g; k < mytiles; k += 2) {
-      if (k >= 2 && !tc_wait(&done[g], ((k - 2) >> 1) & 1u, flag)) {
+      if (k >= 2 && !tc_wait(&done[g], ((k - 2) >> 1) & 1u, flag, t.polls)) {
         tc_abort(flag, t.status);
         break;
       }
@@ -594,22 +660,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
   } else if (warp == 12) {
     // ---------------- MMA issue ----------------
     if (lane == 0) {
-      const uint32_t idesc = tc_idesc_f16(kTcCols, NT);
       const uint32_t r_addr = tc_smem_addr(smem + L.off_r);
       for (uint32_t k = 0; k < mytiles; ++k) {
         const int s = k & 1;
-        if (!tc_wait(&full[s], (k >> 1) & 1u, flag) ||
-            (k >= 2 && !tc_wait(&empty[s], ((k - 2) >> 1) & 1u, flag))) {
+        if (!tc_wait(&full[s], (k >> 1) & 1u, flag, t.polls) ||
+            (k >= 2 && !tc_wait(&empty[s], ((k - 2) >> 1) & 1u, flag, t.polls))) {
           tc_abort(flag, t.status);
           break;
         }
         tc_fence_after_sync();
-        const uint32_t d = tbase + (uint32_t)s * 256u;
-        const uint32_t x_addr = tc_smem_addr(smem + (s ? L.off_b1 : L.off_b0));
-#pragma unroll
-        for (int kk = 0; kk < Pol::KT / 16; ++kk)
-          tc_mma_f16(d, tc_desc_kmajor(x_addr + kk * 256, 128, CHT * 128),
-                     tc_desc_kmajor(r_addr + kk * 256, 128, CHT * 128), idesc, kk > 0);
+        Pol::issue(tbase + (uint32_t)s * 256u, tc_smem_addr(smem + (s ? L.off_b1 : L.off_b0)), r_addr);
         tc_commit(&done[s]);
         issued = k + 1;
       }
@@ -620,7 +680,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
     const int *s_er = (const int *)(smem + L.off_er);
     for (uint32_t k = 0; k < mytiles; ++k) {
       const int s = k & 1;
-      if (!tc_wait(&done[s], (k >> 1) & 1u, flag)) {
+      if (!tc_wait(&done[s], (k >> 1) & 1u, flag, t.polls)) {
         tc_abort(flag, t.status);
         break;
       }

@@ -35,6 +35,7 @@ struct TwoPhaseArgs {
   const void *tc_a;               // tensor-core phase 1: digit image of R (fock_apply_tc.cuh), or NULL
   const int *tc_er;               // its row exponents
   int *status;                    // nonzero after a bounded wait of phase 1 expired, or NULL
+  uint32_t polls;                 // poll budget of each bounded wait of the tensor-core phase 1
   cudaEvent_t phase1_done;        // recorded between the two phases when non-null (profiling hook)
   int phases;                     // 1: phase 1 only, 2: phase 2 only, 3: both
   uint32_t g_begin, g_end;        // configurations phase 2 computes

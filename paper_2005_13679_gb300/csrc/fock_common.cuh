@@ -146,6 +146,9 @@ struct fock_ham {
 };
 
 // Launch helpers implemented in fock_apply.cu and used by fock_lanczos.cu.
+// Device address of the fixed scratch array of fock_apply_H_noalloc on `dev`
+// (looked up once per device with that device current, then cached).
+int fock_noalloc_scratch(int dev, void **addr);
 int fock_apply_internal(const fock_space *sp, const fock_ham *ham, const void *C, void *sigma,
                         int nrhs, int precision, int arm, void *ws, size_t ws_bytes,
                         cudaStream_t stream);

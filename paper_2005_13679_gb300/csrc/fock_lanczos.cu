@@ -1,9 +1,9 @@
-// fock_lanczos.cu -- Lanczos ground state of H (Sec. 5).
+// fock_lanczos.cu -- Lanczos ground state of H (Sec. 6).
 //
 // Krylov vectors are complex128 in device memory.  Inside a cycle of at most
 // restart_len vectors every new vector is orthogonalised against all previous
 // ones of the cycle (classical Gram-Schmidt applied twice, the complete
-// re-orthogonalisation of Sec. 5); a cycle ends with a thick restart that keeps
+// re-orthogonalisation of Sec. 6); a cycle ends with a thick restart that keeps
 // the lowest Ritz vectors.  The small projected eigen-problem is solved on the
 // host by Jacobi rotations.
 //
@@ -452,7 +452,7 @@ extern "C" int fock_lanczos_ground(const fock_space *sp, const fock_ham *ham, in
 }
 
 // ---------------------------------------------------------------------------
-// Short-iterative-Lanczos time step (the consumer of H C named in Sec. 1):
+// Short-iterative-Lanczos time step (the consumer of H C named in Sec. 2):
 // C <- exp(-i H dt) C by the Krylov space of C.  With v_0 = C / ||C|| and the
 // Lanczos vectors v_0 .. v_{m-1} (every new vector orthogonalised twice
 // against all previous ones), T = V^H H V is tridiagonal and

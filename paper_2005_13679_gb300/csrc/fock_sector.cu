@@ -1,7 +1,7 @@
 // fock_sector.cu -- configurations of one total orbital weight
 //     Q = sum_i i n_i,
 // with plane-wave orbitals (orbital i of momentum (i - floor(M/2)) 2 pi / L,
-// Sec. 5) the sector of total momentum (Q - N floor(M/2)) 2 pi / L.  An
+// Sec. 6) the sector of total momentum (Q - N floor(M/2)) 2 pi / L.  An
 // operator with diagonal h and W_kqsl = 0 unless k + q = s + l (the
 // Lieb-Liniger selection rule) maps a sector into itself, so its eigenproblem
 // splits into sectors of about N_c / (N (M - 1) + 1) configurations or fewer.

@@ -3,7 +3,7 @@
 //   Eq. nc        N_c(N, M) = C(N + M - 1, M - 1)            -> fock_space_create
 //   Algorithm 1   configuration -> index                      -> fock_rank
 //   Algorithm 2   index -> configuration                      -> fock_unrank
-//   Sec. 3        single / double jump maps (Fig. 4)          -> fock_build_jump_maps
+//   Sec. 4        single / double jump maps (Fig. 4)          -> fock_build_jump_maps
 #include <stdlib.h>
 #include <string.h>
 
@@ -141,6 +141,11 @@ extern "C" int fock_space_create(int32_t N, int32_t M, fock_space **out) {
     free(sp);
     return st;
   }
+  // Resolve the no-alloc scratch array on this device now (loading its module
+  // under lazy loading), so that fock_apply_H_noalloc never has to.  A failure
+  // here is not an error of the space; that entry point retries and reports it.
+  void *scratch = nullptr;
+  fock_noalloc_scratch(sp->device, &scratch);
   *out = sp;
   return FOCK_OK;
 }
@@ -269,7 +274,7 @@ extern "C" int fock_unrank(const fock_space *sp, const int64_t *idx_dev, int64_t
 }
 
 // ---------------------------------------------------------------------------
-// Jump maps (Sec. 3).  One thread per configuration; every slot is written
+// Jump maps (Sec. 4).  One thread per configuration; every slot is written
 // for every configuration, so consecutive threads write consecutive words.
 // ---------------------------------------------------------------------------
 __global__ void fock_single_map_kernel(int N, int M, int64_t nc, const uint64_t *__restrict__ sat,

@@ -5,6 +5,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
 #include <complex>
 #include <type_traits>
 #include <vector>
@@ -14,14 +15,20 @@
 // Digit image of the real form of R (P x P complex, row r = removal pair,
 // column a = addition pair, already divided by the coefficient scale):
 // rows 2r, 2r+1 are (Re, Im) of Y_r, columns 2a, 2a+1 multiply (Re, Im) of X_a.
-// Each real row rho gets e_rho with |R~[rho][k]| < 2^e_rho for all k and five
+// Each real row rho gets e_rho with |R~[rho][k]| < 2^e_rho for all k and six
 // base-2^9 digits of R~ 2^(8 - e_rho), computed exactly in FP64.  The image is
-// the MMA's B operand (N = (real row, level) combinations, K-major) in
-// tensor-core shared-memory layout.
+// the MMA's B operand in tensor-core shared-memory layout (K-major), in two
+// parts: part 1 has N1 rows (tensor-memory columns, TcShape::col) by K1
+// positions 3k + (j - 1) for X digits j = 1..3, plus the exponent row, which
+// copies the column exponent stored at K position exp_pos(); part 2 has N2
+// rows (levels 5..7) by K2 positions 2k + (j - 4) for X digits j = 4, 5.  The
+// entry of row (rho, level l) at (k, j) is digit i = l - j of R~[rho][k]
+// (zero when i is outside 1..6).
 int fock_tc_image(int M, const std::complex<double> *R, std::vector<unsigned char> &img, std::vector<int> &er) {
   if (M < 2 || M > 6) return FOCK_ERR_UNSUPPORTED;
   const TcShape sh(M);
   const int P = sh.P, R2 = sh.R2;
+  constexpr int kDig = 6;
   std::vector<double> Rt((size_t)R2 * R2);
   for (int r = 0; r < P; ++r)
     for (int a = 0; a < P; ++a) {
@@ -32,7 +39,7 @@ int fock_tc_image(int M, const std::complex<double> *R, std::vector<unsigned cha
       Rt[(size_t)(2 * r + 1) * R2 + 2 * a + 1] = v.real();
     }
   er.assign(R2, 0);
-  std::vector<float> dig((size_t)R2 * R2 * 5, 0.f);
+  std::vector<float> dig((size_t)R2 * R2 * kDig, 0.f);
   for (int rho = 0; rho < R2; ++rho) {
     int e = INT_MIN;
     for (int k = 0; k < R2; ++k) {
@@ -47,37 +54,36 @@ int fock_tc_image(int M, const std::complex<double> *R, std::vector<unsigned cha
     er[rho] = e;
     for (int k = 0; k < R2; ++k) {
       double v = ldexp(Rt[(size_t)rho * R2 + k], 8 - e);
-      for (int i = 0; i < 5; ++i) {
+      for (int i = 0; i < kDig; ++i) {
         const double d = nearbyint(v);
-        dig[((size_t)rho * R2 + k) * 5 + i] = (float)d;
+        dig[((size_t)rho * R2 + k) * kDig + i] = (float)d;
         v = (v - d) * 512.0;
       }
     }
   }
-  // rows of the image: level l of real row rho at sh.col(rho, l); row 15
-  // copies the column exponent stored at K position exp_pos()
-  const int CHT = sh.KT / 8;
   img.assign(sh.r_bytes(), 0);
+  unsigned char *part2 = img.data() + sh.r1_bytes();
+  const int ch1 = sh.K1 / 8, ch2 = sh.K2 / 8;
+  auto put = [&](unsigned char *base, int row, int p, int chunks, float v) {
+    const __half h = __float2half(v);
+    memcpy(base + tc_kmajor_offset(row, p, chunks), &h, 2);
+  };
   for (int rho = 0; rho < R2; ++rho)
-    for (int level = 2; level <= 6; ++level) {
+    for (int level = 2; level <= 7; ++level) {
       const int row = sh.col(rho, level);
-      for (int p = 0; p < sh.KT; ++p) {
-        int k, j;
-        if (p < sh.K1) {
-          k = p / 3;
-          j = p % 3 + 1;
-        } else {
-          k = (p - sh.K1) / 2;
-          j = 4 + (p - sh.K1) % 2;
+      for (int k = 0; k < R2; ++k) {
+        for (int j = 1; j <= 5; ++j) {
+          const int i = level - j;
+          if (i < 1 || i > kDig) continue;
+          const float d = dig[((size_t)rho * R2 + k) * kDig + (i - 1)];
+          if (j <= 3)
+            put(img.data(), row, 3 * k + (j - 1), ch1, d);
+          else if (level >= 5)
+            put(part2, row, 2 * k + (j - 4), ch2, d);
         }
-        const int i = level - j;
-        if (k >= R2 || i < 1 || i > 5) continue;
-        const __half h = __float2half(dig[((size_t)rho * R2 + k) * 5 + (i - 1)]);
-        memcpy(img.data() + tc_kmajor_offset(row, p, CHT), &h, 2);
       }
     }
-  const __half one = __float2half(1.f);
-  memcpy(img.data() + tc_kmajor_offset(kTcExpCol, sh.exp_pos(), CHT), &one, 2);
+  put(img.data(), sh.exp_col(), sh.exp_pos(), ch1, 1.f);
   return FOCK_OK;
 }
 
@@ -143,8 +149,22 @@ size_t fock_tc_smem(int M, int xdim, int nsq, bool mixed) {
   return (size_t)-1;
 }
 
+// Poll budget of the bounded waits inside phase 1 (producers, MMA issue,
+// epilogue).  The default is kTcPolls (about a second); fock_debug_set_wait_polls
+// lowers it so that tests can make the waits give up.  The wait that lets
+// committed MMAs finish before tensor memory is freed always keeps kTcPolls.
+static std::atomic<uint32_t> g_tc_polls{kTcPolls};
+
+extern "C" int fock_debug_set_wait_polls(int64_t polls) {
+  if (polls > (int64_t)kTcPolls) return FOCK_ERR_ARG;
+  g_tc_polls.store(polls < 0 ? kTcPolls : (uint32_t)polls);
+  return FOCK_OK;
+}
+
 template <int M, class Pol>
-static int launch_tc(const TwoPhaseArgs &t, int dev, cudaStream_t s) {
+static int launch_tc(const TwoPhaseArgs &targ, int dev, cudaStream_t s) {
+  TwoPhaseArgs t = targ;
+  t.polls = g_tc_polls.load();
   const ApplyArgs<uint32_t> &a = t.a;
   if (t.phases & 1) {
     const size_t smem = tc_smem_of<Pol, M>(a.xdim, a.nsq).total;

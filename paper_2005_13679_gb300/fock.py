@@ -60,7 +60,8 @@ EXPORTS = (
     "fock_hamiltonian_create", "fock_hamiltonian_destroy", "fock_hamiltonian_terms",
     "fock_hamiltonian_is_real",
     "fock_apply_path", "fock_apply_set_path", "fock_autotune",
-    "fock_apply_set_events", "fock_apply_workspace_size", "fock_apply_H", "fock_apply_H_host", "fock_apply_H_noalloc",
+    "fock_apply_set_events", "fock_apply_workspace_size", "fock_apply_H", "fock_apply_check", "fock_debug_set_wait_polls",
+    "fock_apply_H_host", "fock_apply_H_noalloc",
     "fock_lanczos_ground", "fock_sil_step", "fock_density_matrices",
     "fock_sector_create", "fock_sector_destroy", "fock_sector_size", "fock_sector_rank", "fock_sector_unrank",
     "fock_sector_terms", "fock_sector_workspace_size", "fock_sector_apply_H", "fock_sector_lanczos_ground",
@@ -122,6 +123,8 @@ def load(path: str | None = None):
         "fock_apply_H": [vp, vp, vp, vp, i32, ctypes.c_int, ctypes.c_int, vp, sz, vp],
         "fock_apply_H_host": [vp, vp, vp, vp, i32, ctypes.c_int, ctypes.c_int, vp],
         "fock_apply_H_noalloc": [vp, vp, vp, vp, i32, ctypes.c_int, vp],
+        "fock_apply_check": [vp, vp, vp, ctypes.c_int, vp],
+        "fock_debug_set_wait_polls": [i64],
         "fock_lanczos_ground": [vp, vp, i32, i32, dbl, ctypes.c_uint64, ctypes.c_int, vp,
                                 P(dbl), P(dbl), vp, P(i32), vp],
         "fock_density_matrices": [vp, vp, vp, vp, vp],
@@ -341,6 +344,20 @@ def fock_apply_H(sp, ham, C, sigma=None, nrhs: int = 1, precision: int = FOCK_PR
     _check(load().fock_apply_H(sp, ham, _dptr(C), _dptr(sigma), int(nrhs), int(precision), int(arm),
                                _dptr(workspace), ws_bytes, _stream(stream)), "fock_apply_H")
     return sigma
+
+
+def fock_apply_check(sp, ham, workspace=None, noalloc: bool = False, stream=None) -> int:
+    """Status of the last apply that ran the tensor-core phase 1 with this
+    workspace (None: the Hamiltonian's own; noalloc: the fixed array):
+    FOCK_OK or FOCK_ERR_TIMEOUT.  Waits on the stream."""
+    st = load().fock_apply_check(sp, ham, _dptr(workspace), int(bool(noalloc)), _stream(stream))
+    _check(st, "fock_apply_check", allow=(FOCK_ERR_TIMEOUT,))
+    return st
+
+
+def fock_debug_set_wait_polls(polls: int) -> None:
+    """Test hook: poll budget of phase 1's bounded waits (< 0: default, 0: give up at once)."""
+    _check(load().fock_debug_set_wait_polls(int(polls)), "fock_debug_set_wait_polls")
 
 
 def fock_apply_H_host(sp, ham, C_host, sigma_host, nrhs: int = 1, precision: int = FOCK_PREC_F64,

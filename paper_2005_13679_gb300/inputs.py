@@ -16,7 +16,7 @@ Conventions (arXiv:2005.13679):
 
 Recipes:
 
-* Lieb-Liniger ring in plane waves (Sec. 5): orbital i carries momentum
+* Lieb-Liniger ring in plane waves (Sec. 6): orbital i carries momentum
   p_i = 2 pi (i - floor(M/2)) / L, so M = 5 gives -2..2 and M = 10 gives -5..4;
   h_kk = p_k^2 / 2 (hbar = m = 1), W_kqsl = g / L when p_k + p_q = p_s + p_l.
 * Generic Hermitian model: h = (A + A^dag) / 2 with Re and Im of A drawn
@@ -167,7 +167,7 @@ def uneven_ll_batch(count: int = 64, seed: int = 5, cap: int = 10 ** 7,
 
 @dataclass
 class Workload:
-    """A named synthetic workload (sizes of the paper's Sec. 3-5 experiments)."""
+    """A named synthetic workload (sizes of the experiments of the paper's Secs. 4-6)."""
     name: str
     N: int
     M: int

@@ -1,4 +1,4 @@
-"""GPU parity of the hash (Algorithms 1 and 2) and the jump maps (Sec. 3)
+"""GPU parity of the hash (Algorithms 1 and 2) and the jump maps (Sec. 4)
 against the oracle, through the C ABI.  Bit-exact."""
 import math
 

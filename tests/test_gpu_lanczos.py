@@ -1,4 +1,4 @@
-"""GPU Lanczos ground state (Sec. 5) against the oracle's dense diagonalisation
+"""GPU Lanczos ground state (Sec. 6) against the oracle's dense diagonalisation
 and Lanczos, through the C ABI.  Energies must match to 1e-10 relative."""
 import numpy as np
 import pytest

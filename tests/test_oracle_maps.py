@@ -1,4 +1,4 @@
-"""Pins for the oracle's single- and double-jump maps (Sec. 3, Fig. 4).
+"""Pins for the oracle's single- and double-jump maps (Sec. 4, Fig. 4).
 
 The maps are checked entry by entry against a dictionary from brute-force
 enumeration (no call to Algorithm 1), and their sizes against the paper's

@@ -1,4 +1,4 @@
-"""Pins for the oracle's Lanczos solver and Bethe-ansatz energy (Sec. 5).
+"""Pins for the oracle's Lanczos solver and Bethe-ansatz energy (Sec. 6).
 
 * Lanczos against LAPACK's dense Hermitian eigen-solver on the oracle's dense H;
 * the Bethe-ansatz solver against three independent facts: the two-body ring

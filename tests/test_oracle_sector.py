@@ -1,5 +1,5 @@
 """Pins of the oracle's fixed-weight sectors (sum_i i n_i = Q; total momentum
-for the plane-wave orbitals of Sec. 5) against facts that do not come from the
+for the plane-wave orbitals of Sec. 6) against facts that do not come from the
 oracle's own sector code:
 
 * sector sizes are the coefficients of the Gaussian binomial coefficient
