@@ -577,6 +577,34 @@ def inputs_random_state(n, seed):
     return inputs.random_state(n, seed)
 
 
+def measure_one_by_one(torch, fock, probs, B, Cd, batch_ms):
+    """The same FP64-class applies one instance at a time (each its own space,
+    operator and the library's path for it, workspaces allocated beforehand),
+    beside the one persistent launch over all instances."""
+    objs = []
+    for (N, M, h, W) in probs:
+        sp = fock.Space(N, M)
+        objs.append((sp, fock.Hamiltonian(sp, h, W)))
+    sig = torch.empty_like(Cd)
+    paths = {}
+
+    def run():
+        for i, (sp, H) in enumerate(objs):
+            b, e = int(B.offsets[i]), int(B.offsets[i + 1])
+            fock.fock_apply_H(sp.handle, H.handle, Cd[b:e], sig[b:e], 1, fock.FOCK_PREC_F64)
+    run()                                        # workspaces and first launches
+    for sp, H in objs:
+        p = fock.PATH_NAMES[fock.fock_apply_path(sp.handle, H.handle)]
+        paths[p] = paths.get(p, 0) + 1
+    t = time_steps(torch, run, 3, 1, lambda: None)
+    ref = B.apply(Cd)
+    err = float(torch.linalg.vector_norm(sig - ref) / torch.linalg.vector_norm(ref))
+    del objs, sig, ref
+    torch.cuda.empty_cache()
+    return {"ms_per_step": t, "batched_ms": batch_ms, "batched_speedup": t / batch_ms, "paths": paths,
+            "rel_diff_vs_batched": err}
+
+
 def run_batch(args):
     """64 uneven Lieb-Liniger instances (N in [10, 200], M in 4..12, log g uniform,
     capped at 10^7 configurations each): one step is one batched FP64-class
@@ -623,6 +651,7 @@ def run_batch(args):
         "gpu_launches": 3 * args.steps, "clocks": clocks,
     }
     if args.extras:
+        out["one_by_one"] = measure_one_by_one(torch, fock, probs, B, Cd, ms_all)
         C32 = Cd.to(torch.complex64)
         s32 = torch.empty_like(C32)
         B.autotune(C32, s32, fock.FOCK_PREC_F32_MIXED, cache_path=cache)
@@ -631,15 +660,129 @@ def run_batch(args):
         del C32, s32, Cd, sig
         torch.cuda.empty_cache()
         t0 = time.perf_counter()
-        E, R, it, st = B.lanczos_ground(max_iter=args.lanczos_iters, restart_len=12, tol=1e-9, seed=11)
+        E, R, it, st = B.lanczos_ground(max_iter=args.lanczos_iters, restart_len=args.batch_restart, tol=1e-9,
+                                        seed=11)
         dt = time.perf_counter() - t0
         out["lanczos"] = {"seconds": dt, "status": int(st), "products_max": int(it.max()),
+                          "restart_len": args.batch_restart, "budget": args.lanczos_iters,
                           "products_mean": float(it.mean()), "max_rel_residual": float(np.max(R / np.abs(E))),
                           "converged": int(np.sum(R / np.abs(E) < 1e-6))}
     if rank == 0:
         print(json.dumps(out), flush=True)
     dist_finish()
     return 0
+
+
+def measure_separate(torch, fock, sp, H, Cn, w, steps):
+    """The block of nrhs vectors in one apply against nrhs separate
+    single-vector applies of the same operator (each column stored on its own),
+    per precision: the block shares one decode and one set of targets and
+    amplitudes per configuration."""
+    res = {}
+    for name in ("f64", "f32_mixed"):
+        p = PREC[name]
+        dt = torch.complex64 if p == 2 else torch.complex128
+        blk = torch.from_numpy(Cn).to(dt).cuda()
+        sblk = torch.empty_like(blk)
+        wsb = torch.empty(max(fock.fock_apply_workspace_size(sp.handle, H.handle, w.nrhs, p), 16),
+                          dtype=torch.uint8, device="cuda")
+        t_blk = time_steps(torch, lambda: fock.fock_apply_H(sp.handle, H.handle, blk, sblk, w.nrhs, p,
+                                                             fock.FOCK_ARM_AUTO, wsb), steps, 1, lambda: None)
+        del wsb
+        cols = [torch.from_numpy(Cn[:, j].copy()).to(dt).cuda() for j in range(w.nrhs)]
+        outs = [torch.empty_like(c) for c in cols]
+        ws1 = torch.empty(max(fock.fock_apply_workspace_size(sp.handle, H.handle, 1, p), 16), dtype=torch.uint8,
+                          device="cuda")
+
+        def sep():
+            for c, o in zip(cols, outs):
+                fock.fock_apply_H(sp.handle, H.handle, c, o, 1, p, fock.FOCK_ARM_AUTO, ws1)
+        t_sep = time_steps(torch, sep, steps, 1, lambda: None)
+        err = max(float(torch.linalg.vector_norm(outs[j] - sblk[:, j]) / torch.linalg.vector_norm(sblk[:, j]))
+                  for j in range(w.nrhs))
+        res[name] = {"block_ms": t_blk, "separate_ms": t_sep, "block_speedup": t_sep / t_blk,
+                     "block_path": fock.PATH_NAMES[fock.fock_apply_path(sp.handle, H.handle, w.nrhs, p)],
+                     "single_path": fock.PATH_NAMES[fock.fock_apply_path(sp.handle, H.handle, 1, p)],
+                     "max_rel_diff_block_vs_single": err}
+        del blk, sblk, cols, outs, ws1
+        torch.cuda.empty_cache()
+    return res
+
+
+def measure_arms(torch, fock, sp, H, Cn, w, steps):
+    """Jump-map tables (Sec. 4, Fig. 4) against the on-the-fly hash: build both
+    maps, time the apply on the maps arm in each precision beside the hash arm,
+    then free the maps."""
+    import ctypes
+    res = {}
+    need = ctypes.c_size_t()
+    fock.load().fock_build_jump_maps(sp.handle, 3, 1, ctypes.byref(need), fock._stream(None))
+    res["map_bytes"] = need.value
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    vec = w.nc * w.nrhs * 16
+    if need.value + 4 * vec > free:
+        res["skipped"] = f"maps need {need.value / 1e9:.1f} GB, {free / 1e9:.1f} GB free"
+        return res
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = fock.load().fock_build_jump_maps(sp.handle, 3, 0, None, fock._stream(None))
+    torch.cuda.synchronize()
+    res["build_s"] = time.perf_counter() - t0
+    if st != 0:
+        res["skipped"] = f"build failed: {fock.fock_strerror(st)}"
+        return res
+    try:
+        for name, p in PREC.items():
+            dt = torch.complex64 if p == 2 else torch.complex128
+            X = torch.from_numpy(Cn).to(dt).cuda()
+            Yh, Ym = torch.empty_like(X), torch.empty_like(X)
+            wsb = torch.empty(max(fock.fock_apply_workspace_size(sp.handle, H.handle, w.nrhs, p), 16),
+                              dtype=torch.uint8, device="cuda")
+            row = {}
+            for arm_name, arm, out in (("hash", fock.FOCK_ARM_HASH, Yh), ("maps", fock.FOCK_ARM_MAPS, Ym)):
+                n = 1 if p == 1 else steps
+                t = time_steps(torch, lambda: fock.fock_apply_H(sp.handle, H.handle, X, out, w.nrhs, p, arm, wsb),
+                               n, 1, lambda: None)
+                row[arm_name] = {"ms_per_step": t, "path": fock.PATH_NAMES[fock.fock_apply_path(
+                    sp.handle, H.handle, w.nrhs, p, arm, wsb.numel())]}
+            row["maps_over_hash_time"] = row["maps"]["ms_per_step"] / row["hash"]["ms_per_step"]
+            row["max_rel_diff"] = float(torch.linalg.vector_norm(Ym - Yh) / torch.linalg.vector_norm(Yh))
+            res[name] = row
+            del X, Yh, Ym, wsb
+            torch.cuda.empty_cache()
+    finally:
+        fock.load().fock_jump_maps_free(sp.handle)
+    return res
+
+
+def measure_lanczos_precision(torch, fock, sp, H, Cn, w, max_iter):
+    """The precision form inside the Lanczos solver (Sec. 6): the FP32-mixed
+    apply's error against the FP64-class apply on the workload's state, and
+    the ground-state energy with mixed products (then FP64-class refinement)
+    against FP64-class products throughout, each within max_iter products."""
+    res = {}
+    X = torch.from_numpy(Cn).cuda()
+    ref = fock.fock_apply_H(sp.handle, H.handle, X, None, 1, fock.FOCK_PREC_F64)
+    mixed = fock.fock_apply_H(sp.handle, H.handle, X.to(torch.complex64), None, 1, fock.FOCK_PREC_F32_MIXED)
+    res["apply_rel_err_mixed_vs_f64"] = float(torch.linalg.vector_norm(mixed.to(torch.complex128) - ref)
+                                              / torch.linalg.vector_norm(ref))
+    del X, ref, mixed
+    torch.cuda.empty_cache()
+    runs = {}
+    for name in ("f64", "f32_mixed"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        E0, r, it, _, st = fock.fock_lanczos_ground(sp.handle, H.handle, max_iter=max_iter, restart_len=24,
+                                                   tol=1e-10, seed=w.lanczos_seed, precision=PREC[name])
+        runs[name] = {"E0": E0, "residual": r, "products": it, "status": int(st),
+                      "seconds": time.perf_counter() - t0}
+        torch.cuda.empty_cache()
+    runs["rel_energy_diff_mixed_vs_f64"] = abs(runs["f32_mixed"]["E0"] - runs["f64"]["E0"]) / abs(runs["f64"]["E0"])
+    res["lanczos"] = runs
+    res["note"] = ("FP64 Krylov vectors and re-orthogonalisation; the mixed run switches to FP64-class products "
+                   "at a relative residual of 1e-5 and ends with an FP64-class Rayleigh quotient")
+    return res
 
 
 def main():
@@ -654,7 +797,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cpu-all-cores", type=int, default=1, help="also time the oracle on every host core")
     ap.add_argument("--e2e", type=int, default=1, help="also time the host-buffer entry point")
-    ap.add_argument("--lanczos-iters", type=int, default=240, help="batched Lanczos budget (ll_batch64)")
+    ap.add_argument("--lanczos-iters", type=int, default=480, help="batched Lanczos budget (ll_batch64)")
+    ap.add_argument("--batch-restart", type=int, default=16, help="batched Lanczos restart length (ll_batch64)")
+    ap.add_argument("--arms", type=int, default=1, help="also time the jump-map arm (generic workloads)")
+    ap.add_argument("--lanczos", type=int, default=1, help="Lanczos in both precisions (Lieb-Liniger workloads)")
+    ap.add_argument("--lanczos-steps", type=int, default=200, help="product budget of that Lanczos run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -851,6 +998,14 @@ def main():
             extras[name] = {"ms_per_step": t, "config_terms_per_s": terms / (t * 1e-3)}
             del X, Y
         out["other_precisions"] = extras
+        del wsb
+        torch.cuda.empty_cache()
+        if w.nrhs > 1:
+            out["separate_applies"] = measure_separate(torch, fock, sp, H, Cn, w, max(3, args.steps // 4))
+        if args.arms and w.kind != "ll":
+            out["arms"] = measure_arms(torch, fock, sp, H, Cn, w, max(2, args.steps // 8))
+        if args.lanczos and w.kind == "ll":
+            out["lanczos_precision"] = measure_lanczos_precision(torch, fock, sp, H, Cn, w, args.lanczos_steps)
         if w.nrhs == 1 and w.M <= 12:
             # one- and two-body density matrices of the same state (Eqs. rho1, rho2)
             X = torch.from_numpy(Cn).cuda()

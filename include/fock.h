@@ -188,7 +188,14 @@ int fock_hamiltonian_is_real(const fock_ham *ham, int *is_real);
  * sites and bonds k, k+1, a ring when h_{0,M-1} != 0, W only on-site; hash
  * arm), the register-resident dense kernel (dense coefficients, M <= 10), the
  * sparse kernel (at most 2048 reduced coefficients), the list kernel (always;
- * the only path for N_c >= 2^32 - 1). */
+ * the only path for N_c >= 2^32 - 1).  The two-phase evaluation for operators
+ * that conserve the pair weight (FOCK_PATH_TWOPHASE_BLOCK: every reduced
+ * coefficient links pairs {k, q} and {s, l} with k + q = s + l, as the
+ * Lieb-Liniger ring in plane waves, Sec. 6, where k + q is the pair's
+ * momentum; 2 <= M <= 12, FOCK_PREC_F64 or FOCK_PREC_F32_MIXED, hash arm, the
+ * preferred workspace) comes after the dense two-phase paths: its reduced
+ * coefficients are block diagonal by the pair sum, so phase 1 evaluates
+ * sum_K |block K|^2 products per (N-2)-particle configuration. */
 #define FOCK_PATH_AUTO        0
 #define FOCK_PATH_TWOPHASE_TC 1
 #define FOCK_PATH_TWOPHASE    2
@@ -196,6 +203,7 @@ int fock_hamiltonian_is_real(const fock_ham *ham, int *is_real);
 #define FOCK_PATH_DENSE       4
 #define FOCK_PATH_SPARSE      5
 #define FOCK_PATH_LIST        6
+#define FOCK_PATH_TWOPHASE_BLOCK 7
 
 /* The path an apply with these options takes (a workspace of
  * workspace_bytes, 0 for none), honouring a path set by fock_autotune or

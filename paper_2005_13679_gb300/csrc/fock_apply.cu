@@ -38,6 +38,10 @@ int fock_launch_nn(const ApplyArgs<uint32_t> &, const void *, const void *, cons
 int fock_tc_image(int M, const std::complex<double> *R, std::vector<unsigned char> &img, std::vector<int> &er);
 int fock_tc_image_mixed(int M, const std::complex<double> *R, std::vector<unsigned char> &img, std::vector<int> &er);
 size_t fock_tc_smem(int M, int xdim, int nsq, bool mixed);
+int fock_launch_twophase_block(const TwoPhaseArgs &, bool, int, cudaStream_t);
+bool fock_block_tables(int M, const std::complex<double> *R, double scale, std::vector<float4> &df,
+                       std::vector<float2> &mx);
+size_t fock_block_smem(int M, int xdim, int nsq, bool mixed);
 
 // Segment form of one term (see fock_apply_sparse.cuh): the removal (k, q)
 // (q = -1 for one particle) and the addition (s, l) (s = -1 for one particle)
@@ -117,6 +121,8 @@ static void free_ham(fock_ham *h) {
   cudaFree(h->d_tc_er);
   cudaFree(h->d_tc_ma);
   cudaFree(h->d_tc_mer);
+  cudaFree(h->d_blk_df);
+  cudaFree(h->d_blk_32);
   for (int i = 0; i < 3; ++i) {
     cudaFree(h->d_nn_bond[i]);
     cudaFree(h->d_nn_e[i]);
@@ -476,6 +482,16 @@ static int hamiltonian_create(const fock_space *sp, const double *h_host, const 
     if (!st) st = upload(&H->d_tc_ma, img.data(), img.size());
     if (!st) st = upload(&H->d_tc_mer, er.data(), er.size());
   }
+  if (!st && two_body && !H->dense && M >= 2 && M <= 12) {
+    // pair-weight-conserving operators: block tables for the two-phase path
+    std::vector<float4> bdf;
+    std::vector<float2> b32;
+    if (fock_block_tables(M, R.data(), H->coef_scale, bdf, b32)) {
+      st = upload(&H->d_blk_df, bdf.data(), bdf.size());
+      if (!st) st = upload(&H->d_blk_32, b32.data(), b32.size());
+      if (!st) H->pairsum = true;
+    }
+  }
   if (!st) st = build_nn(H, h_host, W_host);
   if (!st) st = upload(&H->d_terms, terms.data(), nadd);
   if (!st) st = upload(&H->d_slots, slots.data(), nadd);
@@ -583,7 +599,7 @@ size_t fock_apply_ws_bytes(const fock_space *sp, const fock_ham *ham, int nrhs, 
 // coefficients with 2 <= M <= 8 and 32-bit indices, in the FP32-pair and
 // FP32-mixed forms; it needs an (N-2)-space buffer of P values per configuration.
 static bool twophase_eligible(const fock_space *sp, const fock_ham *ham, int precision) {
-  return ham->dense && sp->idx32 && sp->M >= 2 && sp->M <= 8 && sp->N >= 2 &&
+  return ((ham->dense && sp->M <= 8) || ham->pairsum) && sp->idx32 && sp->M >= 2 && sp->N >= 2 &&
          (precision == FOCK_PREC_F64 || precision == FOCK_PREC_F32_MIXED);
 }
 
@@ -768,14 +784,23 @@ static int apply_path(const fock_space *sp, const fock_ham *ham, const void *C, 
   return st;
 }
 
+// The pair-weight two-phase path: its phase-1 shared memory within the
+// device's per-block limit.
+static bool block_eligible(const fock_space *sp, const ApplyArgs<uint32_t> &a, int precision) {
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, sp->device) != cudaSuccess) return false;
+  return fock_block_smem(sp->M, a.xdim, a.nsq, precision == FOCK_PREC_F32_MIXED) <= (size_t)optin;
+}
+
 // Whether a kernel path can serve this apply (32-bit indices).
 static bool path_ok(int path, const fock_space *sp, const fock_ham *ham, const ApplyArgs<uint32_t> &a, int nrhs,
                     int precision, bool maps, bool nrhs16, const void *ws, size_t ws_bytes) {
   const bool two = !maps && ws && twophase_eligible(sp, ham, precision) &&
                    ws_bytes >= fock_apply_ws_pref(sp, ham, nrhs, precision);
   switch (path) {
-    case FOCK_PATH_TWOPHASE_TC: return two && tc_eligible(sp, ham, a, nrhs, precision);
-    case FOCK_PATH_TWOPHASE: return two;
+    case FOCK_PATH_TWOPHASE_TC: return two && ham->dense && tc_eligible(sp, ham, a, nrhs, precision);
+    case FOCK_PATH_TWOPHASE: return two && ham->dense;
+    case FOCK_PATH_TWOPHASE_BLOCK: return two && ham->pairsum && block_eligible(sp, a, precision);
     case FOCK_PATH_NN: return !maps && ham->nn;
     case FOCK_PATH_DENSE:
       return ham->dense && sp->M <= 10 && !(maps && nrhs16) && precision != FOCK_PREC_F64_NATIVE;
@@ -790,8 +815,8 @@ static bool path_ok(int path, const fock_space *sp, const fock_ham *ham, const A
 // sparse kernel, the list kernel.
 static int default_path(const fock_space *sp, const fock_ham *ham, const ApplyArgs<uint32_t> &a, int nrhs,
                         int precision, bool maps, bool nrhs16, const void *ws, size_t ws_bytes) {
-  static const int order[] = {FOCK_PATH_TWOPHASE_TC, FOCK_PATH_TWOPHASE, FOCK_PATH_NN, FOCK_PATH_DENSE,
-                              FOCK_PATH_SPARSE};
+  static const int order[] = {FOCK_PATH_TWOPHASE_TC, FOCK_PATH_TWOPHASE, FOCK_PATH_TWOPHASE_BLOCK, FOCK_PATH_NN,
+                              FOCK_PATH_DENSE, FOCK_PATH_SPARSE};
   for (int p : order)
     if (path_ok(p, sp, ham, a, nrhs, precision, maps, nrhs16, ws, ws_bytes)) return p;
   return FOCK_PATH_LIST;
@@ -811,7 +836,8 @@ static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Ci
                          ? force : default_path(sp, ham, a, nrhs, precision, maps, nrhs16, ws, ws_bytes);
     switch (path) {
       case FOCK_PATH_TWOPHASE_TC:
-      case FOCK_PATH_TWOPHASE: {
+      case FOCK_PATH_TWOPHASE:
+      case FOCK_PATH_TWOPHASE_BLOCK: {
         // dense coefficients, M <= 8, enough workspace: evaluate through H(N-2, M)
         TwoPhaseArgs t;
         t.a = a;
@@ -821,6 +847,7 @@ static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Ci
         t.g2 = ham->d_gauss2;
         t.tc_a = nullptr;
         t.tc_er = nullptr;
+        t.blk = precision == FOCK_PREC_F32_MIXED ? (const void *)ham->d_blk_32 : (const void *)ham->d_blk_df;
         t.status = nullptr;
         t.polls = 0;
         t.phase1_done = ham->ev_stop;
@@ -835,8 +862,9 @@ static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Ci
           t.status = (int *)ws + 2;                        // cleared at the start of the apply
         }
         auto launch = [&]() {
-          return path == FOCK_PATH_TWOPHASE_TC ? fock_launch_twophase_tc(t, mixed, sp->device, stream)
-                                               : fock_launch_twophase(t, mixed, sp->device, stream);
+          if (path == FOCK_PATH_TWOPHASE_TC) return fock_launch_twophase_tc(t, mixed, sp->device, stream);
+          if (path == FOCK_PATH_TWOPHASE_BLOCK) return fock_launch_twophase_block(t, mixed, sp->device, stream);
+          return fock_launch_twophase(t, mixed, sp->device, stream);
         };
         if (!ov) return launch();
         // phase 1, then phase 2 in chunks, each chunk of sigma copied out behind it
@@ -948,7 +976,13 @@ extern "C" int fock_apply_H(const fock_space *sp, const fock_ham *ham, const voi
   if (!C_dev || !sigma_dev) return FOCK_ERR_ARG;
   const size_t need = fock_apply_ws_pref(sp, ham, nrhs, precision);
   if (need > 0 && !workspace_dev) {
+    // the preferred workspace selects the fastest path; when it does not fit,
+    // the minimum one still serves the apply
     st = grow_ws((fock_ham *)ham, need);
+    if (st) {
+      cudaGetLastError();
+      st = grow_ws((fock_ham *)ham, fock_apply_ws_bytes(sp, ham, nrhs, precision));
+    }
     if (st) return st;
     workspace_dev = ham->ws;
     workspace_bytes = ham->ws_bytes;
@@ -1066,7 +1100,7 @@ extern "C" int fock_apply_path(const fock_space *sp, const fock_ham *ham, int32_
 extern "C" int fock_apply_set_path(fock_ham *ham, int32_t nrhs, int precision, int path, int arm) {
   if (!ham || nrhs < 1 || nrhs > FOCK_MAX_NRHS) return FOCK_ERR_ARG;
   if (precision < FOCK_PREC_F64 || precision > FOCK_PREC_F32_MIXED) return FOCK_ERR_ARG;
-  if (path < FOCK_PATH_AUTO || path > FOCK_PATH_LIST) return FOCK_ERR_ARG;
+  if (path < FOCK_PATH_AUTO || path > FOCK_PATH_TWOPHASE_BLOCK) return FOCK_ERR_ARG;
   if (arm != FOCK_ARM_HASH && arm != FOCK_ARM_MAPS && !(path == FOCK_PATH_AUTO && arm == FOCK_ARM_AUTO))
     return FOCK_ERR_ARG;
   const int cls = nrhs > 1 ? 1 : 0;
@@ -1114,7 +1148,7 @@ extern "C" int fock_autotune(const fock_space *sp, fock_ham *ham, int32_t nrhs, 
       while (fgets(line, sizeof line, f)) {
         const char *bar = strchr(line, '|');
         if (!bar || (size_t)(bar - line) != strlen(key) || strncmp(line, key, strlen(key)) != 0) continue;
-        if (sscanf(bar + 1, "%d %d %lf", &p, &arm, &ms) == 3 && p >= FOCK_PATH_TWOPHASE_TC && p <= FOCK_PATH_LIST &&
+        if (sscanf(bar + 1, "%d %d %lf", &p, &arm, &ms) == 3 && p >= FOCK_PATH_TWOPHASE_TC && p <= FOCK_PATH_TWOPHASE_BLOCK &&
             (arm == FOCK_ARM_HASH || arm == FOCK_ARM_MAPS))
           hit = true;   // the last matching line wins
       }
@@ -1163,8 +1197,8 @@ extern "C" int fock_autotune(const fock_space *sp, fock_ham *ham, int32_t nrhs, 
   const bool have_maps = (two_body ? sp->d_j2 : sp->d_j1) != nullptr;
   int best_path = FOCK_PATH_LIST, best_arm = FOCK_ARM_HASH, tried = 0;
   double best_ms = 1e300;
-  static const int paths[] = {FOCK_PATH_TWOPHASE_TC, FOCK_PATH_TWOPHASE, FOCK_PATH_NN, FOCK_PATH_DENSE,
-                              FOCK_PATH_SPARSE, FOCK_PATH_LIST};
+  static const int paths[] = {FOCK_PATH_TWOPHASE_TC, FOCK_PATH_TWOPHASE, FOCK_PATH_TWOPHASE_BLOCK, FOCK_PATH_NN,
+                              FOCK_PATH_DENSE, FOCK_PATH_SPARSE, FOCK_PATH_LIST};
   for (int arm : {FOCK_ARM_HASH, FOCK_ARM_MAPS}) {
     if (arm == FOCK_ARM_MAPS && !have_maps) continue;
     for (int p : paths) {

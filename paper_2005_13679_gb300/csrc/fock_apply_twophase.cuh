@@ -34,6 +34,7 @@ struct TwoPhaseArgs {
   const float4 *g1, *g2;          // FP32-pair form: Gauss coefficients (see fock_apply.cu)
   const void *tc_a;               // tensor-core phase 1: digit image of R (fock_apply_tc.cuh), or NULL
   const int *tc_er;               // its row exponents
+  const void *blk;                // pair-weight blocks: coefficient tables by block (fock_twophase_block.cu), or NULL
   int *status;                    // nonzero after a bounded wait of phase 1 expired, or NULL
   uint32_t polls;                 // poll budget of each bounded wait of the tensor-core phase 1
   cudaEvent_t phase1_done;        // recorded between the two phases when non-null (profiling hook)

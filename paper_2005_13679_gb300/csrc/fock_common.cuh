@@ -119,6 +119,11 @@ struct fock_ham {
   int *d_tc_er;             // its row exponents
   unsigned char *d_tc_ma;   // the same for the FP32-mixed form (fp16 hi/lo split of R)
   int *d_tc_mer;
+  // operators that conserve the pair weight k + q = s + l (reduced coefficients
+  // block diagonal by the pair sum; fock_twophase_block.cu)
+  bool pairsum;
+  float4 *d_blk_df;         // block tables, (re_hi, im_hi, re_lo, im_lo) of coef / coef_scale
+  float2 *d_blk_32;         // block tables, complex float, unscaled
   // nearest-neighbour operators (h on sites and bonds k, k + 1 mod M, W only
   // on-site): per-bond and per-site coefficients, indexed by the precision
   bool nn;
@@ -160,6 +165,7 @@ int fock_get_sm_count(int device);
 // H x -> y for the Lanczos driver: (precision, x, y, workspace, its bytes, stream).
 typedef std::function<int(int, const void *, void *, void *, size_t, cudaStream_t)> FockApplyFn;
 int fock_lanczos_run(int64_t n_vec, bool ham_real, int device, const FockApplyFn &apply_fn, size_t ws_bytes,
+                     size_t ws_min,
                      int32_t max_iter, int32_t restart_len, double tol, uint64_t seed, int precision,
                      const void *start_dev, double *E0, double *residual, void *vec_dev, int32_t *iters,
                      cudaStream_t stream);

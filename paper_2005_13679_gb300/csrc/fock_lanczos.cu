@@ -277,7 +277,7 @@ void jacobi_eigen(std::vector<double> A, int n, std::vector<double> &evals, std:
 // H x -> y in the requested precision on the stream (x, y device vectors of
 // the precision's storage type, ws a workspace of ws_bytes).
 int fock_lanczos_run(int64_t n_vec, bool ham_real, int device, const FockApplyFn &apply_fn, size_t ws_bytes,
-                     int32_t max_iter, int32_t restart_len, double tol, uint64_t seed, int precision,
+                     size_t ws_min, int32_t max_iter, int32_t restart_len, double tol, uint64_t seed, int precision,
                      const void *start_dev, double *E0, double *residual, void *vec_dev, int32_t *iters,
                      cudaStream_t stream) {
   if (!E0 || max_iter < 1 || restart_len < 2 || restart_len > 256 || !(tol > 0.0) || n_vec < 1)
@@ -316,10 +316,16 @@ int fock_lanczos_run(int64_t n_vec, bool ham_real, int device, const FockApplyFn
   TRY(cudaMalloc(&V, sizeof(double2) * (size_t)n * (m + 8)) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
   TRY(cudaMalloc(&w, sizeof(double2) * (size_t)n) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
   TRY(cudaMalloc(&c.partial_d, sizeof(double2) * kDotBlocks * kChunk) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
-  if (ws_bytes) TRY(cudaMalloc(&ws, ws_bytes) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
   if (precision == FOCK_PREC_F32_MIXED) {
     TRY(cudaMalloc(&c64a, sizeof(float2) * (size_t)n) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
     TRY(cudaMalloc(&c64b, sizeof(float2) * (size_t)n) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
+  }
+  // the preferred workspace (it selects the fastest path), else the minimum
+  if (ws_bytes && cudaMalloc(&ws, ws_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ws = nullptr;
+    ws_bytes = ws_min;
+    if (ws_bytes) TRY(cudaMalloc(&ws, ws_bytes) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
   }
 
   // H x -> y with the requested precision (y, x complex128)
@@ -447,7 +453,7 @@ extern "C" int fock_lanczos_ground(const fock_space *sp, const fock_ham *ham, in
     return fock_apply_internal(sp, ham, x, y, 1, prec, FOCK_ARM_HASH, ws, ws_bytes, s);
   };
   return fock_lanczos_run(sp->nc, ham->real, sp->device, apply, fock_apply_ws_pref(sp, ham, 1, FOCK_PREC_F64),
-                          max_iter, restart_len, tol, seed, precision, start_dev, E0, residual, vec_dev, iters,
+                          fock_apply_ws_bytes(sp, ham, 1, FOCK_PREC_F64), max_iter, restart_len, tol, seed, precision, start_dev, E0, residual, vec_dev, iters,
                           (cudaStream_t)stream);
 }
 
@@ -484,7 +490,7 @@ extern "C" int fock_sil_step(const fock_space *sp, const fock_ham *ham, void *C_
   double2 *V = nullptr, *w = nullptr;
   float2 *c64a = nullptr, *c64b = nullptr;
   void *ws = nullptr;
-  const size_t ws_bytes = fock_apply_ws_pref(sp, ham, 1, precision);
+  size_t ws_bytes = fock_apply_ws_pref(sp, ham, 1, precision);
   int st = FOCK_OK;
   auto cleanup = [&]() {
     cudaFree(V);
@@ -502,7 +508,12 @@ extern "C" int fock_sil_step(const fock_space *sp, const fock_ham *ham, void *C_
   TRY(cudaMalloc(&V, sizeof(double2) * (size_t)n * K) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
   TRY(cudaMalloc(&w, sizeof(double2) * (size_t)n) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
   TRY(cudaMalloc(&c.partial_d, sizeof(double2) * kDotBlocks * kChunk) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
-  if (ws_bytes) TRY(cudaMalloc(&ws, ws_bytes) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
+  if (ws_bytes && cudaMalloc(&ws, ws_bytes) != cudaSuccess) {   // preferred, else minimum workspace
+    cudaGetLastError();
+    ws = nullptr;
+    ws_bytes = fock_apply_ws_bytes(sp, ham, 1, precision);
+    if (ws_bytes) TRY(cudaMalloc(&ws, ws_bytes) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
+  }
   if (precision == FOCK_PREC_F32_MIXED) {
     TRY(cudaMalloc(&c64a, sizeof(float2) * (size_t)n) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);
     TRY(cudaMalloc(&c64b, sizeof(float2) * (size_t)n) == cudaSuccess ? FOCK_OK : FOCK_ERR_NOMEM);

@@ -673,6 +673,6 @@ extern "C" int fock_sector_lanczos_ground(const fock_sector *sec, const fock_ham
   FockApplyFn apply = [sec, ham](int prec, const void *x, void *y, void *ws, size_t ws_bytes, cudaStream_t s) {
     return fock_sector_apply_internal(sec, ham, x, y, 1, prec, ws, ws_bytes, s);
   };
-  return fock_lanczos_run(sec->ns, ham->real, sec->device, apply, wsb, max_iter, restart_len, tol, seed,
+  return fock_lanczos_run(sec->ns, ham->real, sec->device, apply, wsb, wsb, max_iter, restart_len, tol, seed,
                           precision, start_dev, E0, residual, vec_dev, iters, (cudaStream_t)stream);
 }

@@ -50,7 +50,8 @@ FOCK_PATH_NN = 3
 FOCK_PATH_DENSE = 4
 FOCK_PATH_SPARSE = 5
 FOCK_PATH_LIST = 6
-PATH_NAMES = {1: "twophase_tc", 2: "twophase", 3: "nn", 4: "dense", 5: "sparse", 6: "list"}
+FOCK_PATH_TWOPHASE_BLOCK = 7
+PATH_NAMES = {1: "twophase_tc", 2: "twophase", 3: "nn", 4: "dense", 5: "sparse", 6: "list", 7: "twophase_block"}
 
 # Every extern "C" symbol declared in include/fock.h.
 EXPORTS = (

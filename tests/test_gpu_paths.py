@@ -14,8 +14,8 @@ from paper_2005_13679_gb300 import fock, inputs
 pytestmark = pytest.mark.gpu
 
 TOL = {fock.FOCK_PREC_F64: 1e-12, fock.FOCK_PREC_F64_NATIVE: 1e-12, fock.FOCK_PREC_F32_MIXED: 5e-6}
-PATHS = [fock.FOCK_PATH_TWOPHASE_TC, fock.FOCK_PATH_TWOPHASE, fock.FOCK_PATH_NN, fock.FOCK_PATH_DENSE,
-         fock.FOCK_PATH_SPARSE, fock.FOCK_PATH_LIST]
+PATHS = [fock.FOCK_PATH_TWOPHASE_TC, fock.FOCK_PATH_TWOPHASE, fock.FOCK_PATH_TWOPHASE_BLOCK, fock.FOCK_PATH_NN,
+         fock.FOCK_PATH_DENSE, fock.FOCK_PATH_SPARSE, fock.FOCK_PATH_LIST]
 
 
 @pytest.fixture(scope="module")
@@ -34,11 +34,23 @@ def dev(torch, C, prec):
     return (t.to(torch.complex64) if prec == fock.FOCK_PREC_F32_MIXED else t).cuda()
 
 
+def pair_weight_hw(M, seed):
+    """A complex operator that conserves the pair weight (W_kqsl = 0 unless
+    k + q = s + l) with a complex diagonal-free h = 0: the random symmetrised
+    W masked by the selection rule, plus real site energies."""
+    h, W = inputs.random_hermitian_hw(M, seed)
+    k, q, s_, l = np.meshgrid(*(np.arange(M),) * 4, indexing="ij")
+    W = np.where(k + q == s_ + l, W, 0.0)
+    return np.diag(np.diag(h).real).astype(np.complex128), W
+
+
 def hw(kind, M):
     if kind == "generic":
         return inputs.random_hermitian_hw(M, 21)
     if kind == "ll":
         return inputs.lieb_liniger_hw(M, 0.9)
+    if kind == "llc":
+        return pair_weight_hw(M, 23)
     return inputs.nearest_neighbour_hw(M, 4, True, True)
 
 
@@ -47,7 +59,9 @@ CASES = [
     (9, 6, "generic", {fock.FOCK_PATH_TWOPHASE_TC, fock.FOCK_PATH_TWOPHASE, fock.FOCK_PATH_DENSE,
                        fock.FOCK_PATH_SPARSE, fock.FOCK_PATH_LIST}),
     (6, 8, "generic", {fock.FOCK_PATH_TWOPHASE, fock.FOCK_PATH_DENSE, fock.FOCK_PATH_SPARSE, fock.FOCK_PATH_LIST}),
-    (10, 5, "ll", {fock.FOCK_PATH_SPARSE, fock.FOCK_PATH_LIST}),
+    (10, 5, "ll", {fock.FOCK_PATH_TWOPHASE_BLOCK, fock.FOCK_PATH_SPARSE, fock.FOCK_PATH_LIST}),
+    (7, 10, "ll", {fock.FOCK_PATH_TWOPHASE_BLOCK, fock.FOCK_PATH_SPARSE, fock.FOCK_PATH_LIST}),
+    (6, 12, "llc", {fock.FOCK_PATH_TWOPHASE_BLOCK, fock.FOCK_PATH_SPARSE, fock.FOCK_PATH_LIST}),
     (7, 6, "nn", {fock.FOCK_PATH_NN, fock.FOCK_PATH_SPARSE, fock.FOCK_PATH_LIST}),
 ]
 
@@ -73,7 +87,8 @@ def test_every_path_against_oracle(torch, N, M, kind, must, prec):
         assert served == must
     assert fock.FOCK_PATH_LIST in served
     if prec == fock.FOCK_PREC_F64_NATIVE:
-        assert not served & {fock.FOCK_PATH_TWOPHASE_TC, fock.FOCK_PATH_TWOPHASE, fock.FOCK_PATH_DENSE}
+        assert not served & {fock.FOCK_PATH_TWOPHASE_TC, fock.FOCK_PATH_TWOPHASE, fock.FOCK_PATH_TWOPHASE_BLOCK,
+                             fock.FOCK_PATH_DENSE}
 
 
 def test_path_query_without_workspace_and_with_maps(torch):
