@@ -137,6 +137,9 @@ static void free_ham(fock_ham *h) {
     for (int i = 0; i < 8; ++i)
       if (h->hb_ev[i]) cudaEventDestroy(h->hb_ev[i]);
   }
+  if (h->hb_copy_in) cudaStreamDestroy(h->hb_copy_in);
+  for (int i = 0; i < 9; ++i)
+    if (h->hb_in_ev[i]) cudaEventDestroy(h->hb_in_ev[i]);
   free(h);
 }
 
@@ -554,11 +557,27 @@ __global__ void fock_max_exponent_kernel(const double *__restrict__ x, int64_t n
   if ((threadIdx.x & 31) == 0 && best > 0) atomicMax(out, best);
 }
 
-// out_exp = e_max - 1023 so that |C| * 2^-out_exp < 2.
+// The input scale 2^sh of the FP32-pair copy: none (sh = 0) when the largest
+// magnitude lies in [2^-20, 2^21), else sh = 1023 - e_max so that |C| 2^sh < 2.
+// Inside that band every value is held exactly as an FP32 pair without the
+// scale (values below 2^-125 flush either way, 2^-105 below the largest), so the
+// band rule lets an input be split in chunks before its largest value is known
+// (fock_apply_H_host) with the same result.
+__device__ __forceinline__ int fock_input_shift(int eb) {
+  eb = max(eb, 1);
+  const int e = eb - 1023;                               // |C| < 2^(e + 1)
+  return (e >= -20 && e <= 20) ? 0 : 1023 - eb;
+}
+static bool input_in_band(int eb) {
+  eb = eb > 1 ? eb : 1;
+  return eb - 1023 >= -20 && eb - 1023 <= 20;
+}
+
+// out_exp = -sh (the scale taken back out of sigma).  With band_only the
+// split assumes the band (sh = 0) whatever ebits holds.
 __global__ void fock_split_kernel(const double2 *__restrict__ x, int64_t n, const int *ebits,
-                                  float4 *__restrict__ y, int *out_exp) {
-  const int eb = max(__ldg(ebits), 1);
-  const int sh = 1023 - eb;
+                                  float4 *__restrict__ y, int *out_exp, int band_only = 0) {
+  const int sh = band_only ? 0 : fock_input_shift(__ldg(ebits));
   if (blockIdx.x == 0 && threadIdx.x == 0) out_exp[0] = -sh;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -585,6 +604,27 @@ int fock_prepare_df(const void *C, int64_t n, void *ws, int device, cudaStream_t
   if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
   fock_split_kernel<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, stream>>>((const double2 *)C, n, words, split,
                                                                              words + 1);
+  FOCK_CUDA_TRY(cudaGetLastError());
+  return FOCK_OK;
+}
+
+// One chunk [b, e) of the FP32-pair preparation for the overlapped host-buffer
+// apply: the chunk's largest exponent joins ws word 0 and the chunk is split
+// without a scale (the band of fock_input_shift, checked after the apply).
+static int prepare_df_chunk(const void *C, int64_t b, int64_t e, void *ws, int device, cudaStream_t stream) {
+  int *words = (int *)ws;
+  float4 *split = (float4 *)((char *)ws + kWsHeader);
+  const int64_t n = e - b;
+  if (n <= 0) return FOCK_OK;
+  const int sms = fock_get_sm_count(device);
+  int64_t blocks = (2 * n + 255) / 256;
+  if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+  fock_max_exponent_kernel<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, stream>>>((const double *)C + 2 * b, 2 * n,
+                                                                                      words);
+  blocks = (n + 255) / 256;
+  if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+  fock_split_kernel<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, stream>>>((const double2 *)C + b, n, words,
+                                                                             split + b, words + 1, 1);
   FOCK_CUDA_TRY(cudaGetLastError());
   return FOCK_OK;
 }
@@ -708,8 +748,54 @@ struct HostOverlap {
   cudaEvent_t *ev;      // kHostChunks events
   size_t row_bytes;     // bytes of one configuration's nrhs values
   bool done;            // set when the chunks were copied
+  // chunked input (two-phase paths): C arrives in kHostChunks configuration
+  // ranges on the stream `copy_in`, ev_in[i] marking chunk i; phase 1 runs in
+  // column ranges, each after the input chunks it gathers from
+  const void *in_dev;   // the device copy of C being filled, or NULL: C is already there
+  cudaEvent_t *ev_in;
 };
 static const int kHostChunks = 8;
+
+// Host closed forms of Eq. TotalCost (index = N_c - 1 - sum_m C(S_m + m, m + 1)
+// with prefix sums S_m) and its greedy inverse, for the configurations that
+// bound the gathers of a phase-1 column range.
+static uint64_t host_binom(int64_t x, int64_t j) {
+  if (j < 0 || x < j) return 0;
+  unsigned __int128 r = 1;
+  for (int64_t i = 1; i <= j; ++i) r = r * (unsigned __int128)(x - j + i) / (unsigned __int128)i;
+  return (uint64_t)r;
+}
+static uint64_t host_rank(int Nn, int M, const int *n) {
+  uint64_t acc = (uint64_t)count_nm(Nn, M) - 1;
+  int S = 0;
+  for (int m = 0; m < M - 1; ++m) {
+    S += n[m];
+    acc -= host_binom(S + m, m + 1);
+  }
+  return acc;
+}
+static void host_unrank(int Nn, int M, uint64_t idx, int *n) {
+  uint64_t rem = (uint64_t)count_nm(Nn, M) - 1 - idx;
+  int S[FOCK_MAXM];
+  S[M - 1] = Nn;
+  for (int m = M - 2; m >= 0; --m) {
+    int v = S[m + 1];
+    while (v > 0 && host_binom(v + m, m + 1) > rem) --v;
+    S[m] = v;
+    rem -= host_binom(v + m, m + 1);
+  }
+  for (int m = 0; m < M; ++m) n[m] = S[m] - (m ? S[m - 1] : 0);
+}
+
+// The largest configuration index phase 1 gathers for (N-2)-space columns up
+// to n'_last: adding both particles to the most significant orbital M - 1
+// gives the largest index, and the map n' -> index(n' + a) is increasing.
+static uint64_t phase1_need(const fock_space *sp, uint64_t np_last) {
+  int n[FOCK_MAXM];
+  host_unrank(sp->N - 2, sp->M, np_last, n);
+  n[sp->M - 1] += 2;
+  return host_rank(sp->N, sp->M, n);
+}
 
 static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Cin, void *sigma, int nrhs,
                        int precision, const int32_t *map, const int *in_exp, bool maps, bool nrhs16, int maxm,
@@ -734,6 +820,8 @@ static void tuned_choice(const fock_space *sp, const fock_ham *ham, int nrhs, in
 static int apply_path(const fock_space *sp, const fock_ham *ham, const void *C, void *sigma, int nrhs,
                       int precision, int arm, void *ws, size_t ws_bytes, cudaStream_t stream, int force,
                       HostOverlap *ov = nullptr);
+static int select_path(const fock_space *sp, const fock_ham *ham, int nrhs, int precision, int arm,
+                       size_t ws_bytes, int force, int *path);
 
 int fock_apply_internal(const fock_space *sp, const fock_ham *ham, const void *C, void *sigma,
                         int nrhs, int precision, int arm, void *ws, size_t ws_bytes,
@@ -768,8 +856,12 @@ static int apply_path(const fock_space *sp, const fock_ham *ham, const void *C, 
     const size_t need = fock_apply_ws_bytes(sp, ham, nrhs, precision);
     if (!ws || ws_bytes < need) return FOCK_ERR_ARG;
     int *words = (int *)ws;  // [0] exponent bits, [1] output exponent
-    const int st0 = fock_prepare_df(C, sp->nc * (int64_t)nrhs, ws, sp->device, stream);
-    if (st0) return st0;
+    if (ov && ov->in_dev) {
+      FOCK_CUDA_TRY(cudaMemsetAsync(words, 0, 12, stream));   // split chunk by chunk in launch_main
+    } else {
+      const int st0 = fock_prepare_df(C, sp->nc * (int64_t)nrhs, ws, sp->device, stream);
+      if (st0) return st0;
+    }
     in_exp = words + 1;
     Cin = (const char *)ws + kWsHeader;
   }
@@ -787,6 +879,7 @@ static int apply_path(const fock_space *sp, const fock_ham *ham, const void *C, 
 // The pair-weight two-phase path: its phase-1 shared memory within the
 // device's per-block limit.
 static bool block_eligible(const fock_space *sp, const ApplyArgs<uint32_t> &a, int precision) {
+  if ((uint64_t)count_nm(sp->N - 2, sp->M) * (uint64_t)a.nrhs >= 0xffffffffull) return false;
   int optin = 0;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, sp->device) != cudaSuccess) return false;
   return fock_block_smem(sp->M, a.xdim, a.nsq, precision == FOCK_PREC_F32_MIXED) <= (size_t)optin;
@@ -854,6 +947,8 @@ static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Ci
         t.phases = 3;
         t.g_begin = 0;
         t.g_end = a.nc;
+        t.c_begin = 0;
+        t.c_end = (uint64_t)t.nc2 * (uint64_t)nrhs;
         *stop_recorded = ham->ev_stop != nullptr;
         const bool mixed = precision == FOCK_PREC_F32_MIXED;
         if (path == FOCK_PATH_TWOPHASE_TC) {
@@ -869,7 +964,37 @@ static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Ci
         if (!ov) return launch();
         // phase 1, then phase 2 in chunks, each chunk of sigma copied out behind it
         t.phases = 1;
-        int st = launch();
+        int st = FOCK_OK;
+        if (ov->in_dev) {
+          // phase 1 in column ranges (multiples of the 128-column tile), each
+          // launched once the input chunks it gathers from are on the device
+          // and (FOCK_PREC_F64) split
+          const uint64_t total = (uint64_t)t.nc2 * (uint64_t)nrhs;
+          const uint64_t step = ((total + kHostChunks - 1) / kHostChunks + 127) / 128 * 128;
+          const uint64_t in_chunk = ((uint64_t)a.nc + kHostChunks - 1) / kHostChunks;
+          int ready = 0;
+          for (uint64_t cb = 0; cb < total && !st; cb += step) {
+            const uint64_t ce = cb + step < total ? cb + step : total;
+            const uint64_t need = phase1_need(sp, (ce - 1) / (uint64_t)nrhs);
+            const int upto = (int)(need / in_chunk);
+            for (; ready <= upto && ready < kHostChunks && !st; ++ready) {
+              FOCK_CUDA_TRY(cudaStreamWaitEvent(stream, ov->ev_in[ready], 0));
+              if (precision == FOCK_PREC_F64) {
+                const int64_t b = (int64_t)((uint64_t)ready * in_chunk), e = b + (int64_t)in_chunk < (int64_t)a.nc
+                                                                                 ? b + (int64_t)in_chunk : (int64_t)a.nc;
+                st = prepare_df_chunk(ov->in_dev, b * nrhs, e * nrhs, ws, sp->device, stream);
+              }
+            }
+            t.c_begin = cb;
+            t.c_end = ce;
+            if (!st) st = launch();
+          }
+          for (; ready < kHostChunks && !st; ++ready) FOCK_CUDA_TRY(cudaStreamWaitEvent(stream, ov->ev_in[ready], 0));
+          t.c_begin = 0;
+          t.c_end = total;
+        } else {
+          st = launch();
+        }
         const uint32_t chunk = (a.nc + kHostChunks - 1) / kHostChunks;
         for (int i = 0; i < kHostChunks && !st; ++i) {
           t.phases = 2;
@@ -1036,22 +1161,66 @@ extern "C" int fock_apply_H_host(const fock_space *sp, const fock_ham *ham, cons
   }
   if (!H->hb_copy) {
     FOCK_CUDA_TRY(cudaStreamCreateWithFlags(&H->hb_copy, cudaStreamNonBlocking));
+    FOCK_CUDA_TRY(cudaStreamCreateWithFlags(&H->hb_copy_in, cudaStreamNonBlocking));
     for (int i = 0; i < kHostChunks; ++i)
       FOCK_CUDA_TRY(cudaEventCreateWithFlags(&H->hb_ev[i], cudaEventDisableTiming));
+    for (int i = 0; i <= kHostChunks; ++i)
+      FOCK_CUDA_TRY(cudaEventCreateWithFlags(&H->hb_in_ev[i], cudaEventDisableTiming));
   }
   cudaStream_t s = (cudaStream_t)stream;
-  FOCK_CUDA_TRY(cudaMemcpyAsync(H->hb_in, C_host, bytes, cudaMemcpyHostToDevice, s));
-  HostOverlap ov{sigma_host, H->hb_copy, H->hb_ev, (size_t)nrhs * elem, false};
   int path = FOCK_PATH_AUTO;
   tuned_choice(sp, ham, nrhs, precision, arm, path);
+  int runs = FOCK_PATH_LIST;
+  st = select_path(sp, ham, nrhs, precision, arm, H->ws_bytes, path, &runs);
+  if (st) return st;
+  const size_t row = (size_t)nrhs * elem;
+  HostOverlap ov{sigma_host, H->hb_copy, H->hb_ev, row, false, nullptr, H->hb_in_ev};
+  const bool chunked = (runs == FOCK_PATH_TWOPHASE_TC || runs == FOCK_PATH_TWOPHASE || runs == FOCK_PATH_TWOPHASE_BLOCK) &&
+                       (precision == FOCK_PREC_F64 || precision == FOCK_PREC_F32_MIXED);
+  if (chunked) {
+    // C in kHostChunks configuration ranges on the input stream; phase 1 starts
+    // as soon as the ranges it gathers from have arrived
+    FOCK_CUDA_TRY(cudaEventRecord(H->hb_in_ev[kHostChunks], s));          // after earlier work on `stream`
+    FOCK_CUDA_TRY(cudaStreamWaitEvent(H->hb_copy_in, H->hb_in_ev[kHostChunks], 0));
+    const size_t in_chunk = ((size_t)sp->nc + kHostChunks - 1) / kHostChunks;
+    for (int i = 0; i < kHostChunks; ++i) {
+      const size_t b = (size_t)i * in_chunk, e = b + in_chunk < (size_t)sp->nc ? b + in_chunk : (size_t)sp->nc;
+      if (e > b)
+        FOCK_CUDA_TRY(cudaMemcpyAsync((char *)H->hb_in + b * row, (const char *)C_host + b * row, (e - b) * row,
+                                      cudaMemcpyHostToDevice, H->hb_copy_in));
+      FOCK_CUDA_TRY(cudaEventRecord(H->hb_in_ev[i], H->hb_copy_in));
+    }
+    ov.in_dev = H->hb_in;
+  } else {
+    FOCK_CUDA_TRY(cudaMemcpyAsync(H->hb_in, C_host, bytes, cudaMemcpyHostToDevice, s));
+  }
   st = apply_path(sp, ham, H->hb_in, H->hb_out, nrhs, precision, arm, H->ws, H->ws_bytes, s, path, &ov);
   if (st) {
+    cudaStreamSynchronize(H->hb_copy_in);
     cudaStreamSynchronize(H->hb_copy);
     return st;
   }
   if (!ov.done) FOCK_CUDA_TRY(cudaMemcpyAsync(sigma_host, H->hb_out, bytes, cudaMemcpyDeviceToHost, s));
   FOCK_CUDA_TRY(cudaStreamSynchronize(s));
   FOCK_CUDA_TRY(cudaStreamSynchronize(H->hb_copy));
+  if (chunked && precision == FOCK_PREC_F64) {
+    // the chunks were split without a scale: valid when the largest magnitude
+    // lies in the band of fock_input_shift; otherwise apply again from the
+    // device copy with the scaled split (same result as fock_apply_H)
+    int eb = 0;
+    FOCK_CUDA_TRY(cudaMemcpy(&eb, H->ws, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!input_in_band(eb)) {
+      HostOverlap ov2{sigma_host, H->hb_copy, H->hb_ev, row, false, nullptr, H->hb_in_ev};
+      st = apply_path(sp, ham, H->hb_in, H->hb_out, nrhs, precision, arm, H->ws, H->ws_bytes, s, path, &ov2);
+      if (st) {
+        cudaStreamSynchronize(H->hb_copy);
+        return st;
+      }
+      if (!ov2.done) FOCK_CUDA_TRY(cudaMemcpyAsync(sigma_host, H->hb_out, bytes, cudaMemcpyDeviceToHost, s));
+      FOCK_CUDA_TRY(cudaStreamSynchronize(s));
+      FOCK_CUDA_TRY(cudaStreamSynchronize(H->hb_copy));
+    }
+  }
   if (H->ws && precision != FOCK_PREC_F64_NATIVE) {     // the other two clear the word at their start
     int status = 0;
     FOCK_CUDA_TRY(cudaMemcpy(&status, (const int *)H->ws + 2, sizeof(int), cudaMemcpyDeviceToHost));

@@ -23,19 +23,25 @@
 //
 //     Y = 2^(e_rho + e_c - 16) sum_{l=2..7} 2^(-9(l-2)) S_l
 //
-// as an FP32 pair.  What the product leaves out, per entry (rho, c):
-//   * levels 8..11 (i + j >= 8): at most 2P * 256 * 1293 * 2^-70 2^(e_rho+e_c),
-//     below 2^-46.2 2^(e_rho + e_c);
+// as an FP32 pair.  What the product leaves out, per entry (rho, c), with the
+// unit u = 2^(e_rho + e_c - 16) of the level sums:
+//   * levels 8..11 (i + j >= 8): at most 2P * 256 * 1293 * 2^-54 u, below
+//     2^-46.2 2^(e_rho + e_c) at M = 6;
 //   * the remainder of R~ after six digits, |dR| <= 2^-54 2^e_rho: below
 //     2P 2^-54 2^(e_rho + e_c);
 //   * the remainder of X after five digits, |dX| <= (2^-45 + 2^-59) 2^e_c:
-//     below 2^-45 2^e_c ||R~_rho||_1.
+//     below 2^-45 2^e_c ||R~_rho||_1;
+//   * the combination into a pair: S2, S3 2^-9 and S4 2^-18 are added by TwoSum
+//     (errors kept); S5 2^-27 + S6 2^-36 + S7 2^-45 (below 2^-3 u) is formed in
+//     FP32, an error below 2^-27 u = 2^-43 2^(e_rho + e_c); the low word's own
+//     rounding is below 2^-47 sum_k |R~[rho][k] X[k][c]|.
 // With 2^e_c < 2 max_k |X[k][c]| and 2^e_rho < 2 max_k |R~[rho][k]| <= 2 ||R~_rho||_1,
-// and the pair rounding of the combination (below 2^-46 of the same scale),
 //
-//     |Y^[rho][c] - Y[rho][c]| <= 2^-42.5 ||R~_rho||_1 max_k |X[k][c]|,
+//     |Y^[rho][c] - Y[rho][c]| <= 2^-40.5 ||R~_rho||_1 max_k |X[k][c]|,
 //
-// i.e. 1.6e-13 of the largest value the row can produce on that column.
+// i.e. 6.3e-13 of the largest value the row can produce on that column (the
+// X remainder alone gives 2^-44; the others count only when one coefficient
+// dominates its row).
 //
 // The MMA computes the transposed product: its M = 128 rows are the tile's
 // (configuration, rhs) columns, so tensor-memory lane c holds everything of
@@ -91,7 +97,7 @@ struct TcShape {
   }
   // tensor-memory column of level l (2..7) of real row rho
   __host__ __device__ constexpr int col(int rho, int l) const {
-    return l >= 5 ? 3 * rho + (7 - l) : N2 + 3 * rho + (4 - l);
+    return l >= 5 ? 6 * (rho >> 1) + 2 * (7 - l) + (rho & 1) : N2 + 6 * (rho >> 1) + 2 * (4 - l) + (rho & 1);
   }
 };
 
@@ -106,7 +112,7 @@ struct TcSmem {
     off_r = o;    o += (size_t)r_bytes;
     off_b0 = o;   o += (size_t)kTcCols * kt * 2;
     off_b1 = o;   o += (size_t)kTcCols * kt * 2;
-    off_er = o;   o = fock_align16(o + 4 * (size_t)r2);
+    off_er = o;   o = fock_align16(o + 4 * (size_t)r2 + 8 * (size_t)r2 + 16);
     off_mod = o;  o = fock_align16(o + 4 * (size_t)rows * xdim);
     off_sat = o;  o = fock_align16(o + 4 * (size_t)rows * xdim);
     off_sq = o;   o = fock_align16(o + (size_t)sq_bytes * nsq);
@@ -354,27 +360,25 @@ __device__ __forceinline__ void tc_produce(const TwoPhaseArgs &t, uint32_t tile,
 
 // Combination of the six level sums of two real rows (packed lanes) into
 // FP32 pairs: V = s2 + s3 2^-9 + s4 2^-18 + s5 2^-27 + s6 2^-36 + s7 2^-45
-// with the s_l exact integers below 2^24.  The scalings are exact; the first
-// four terms are added by TwoSum (their errors collected in e), the last two
-// (below 2^-12 of the unit) join e directly.  The rounding of e is below
-// 2^-46 of the largest partial sum, i.e. of sum_k |R~ X| for the row.
+// with the s_l exact integers below 2^24.  The scalings are exact; s2, s3 2^-9
+// and s4 2^-18 are added by TwoSum (errors collected in e); the lower levels,
+// below 2^-3 of the unit, are formed in FP32 (error below 2^-27 of the unit)
+// and join e.
 __device__ __forceinline__ void tc_combine2(fp2_t s2, fp2_t s3, fp2_t s4, fp2_t s5, fp2_t s6, fp2_t s7, fp2_t &hi,
                                             fp2_t &lo) {
   const fp2_t a3 = fp2_mul(s3, fp2_make(0x1p-9f, 0x1p-9f));
   const fp2_t a4 = fp2_mul(s4, fp2_make(0x1p-18f, 0x1p-18f));
-  const fp2_t a5 = fp2_mul(s5, fp2_make(0x1p-27f, 0x1p-27f));
+  const fp2_t a57 = fp2_fma(s7, fp2_make(0x1p-45f, 0x1p-45f),
+                            fp2_fma(s6, fp2_make(0x1p-36f, 0x1p-36f), fp2_mul(s5, fp2_make(0x1p-27f, 0x1p-27f))));
   fp2_t s = fp2_add(s2, a3);
   fp2_t bb = fp2_sub(s, s2);
   fp2_t e = fp2_add(fp2_sub(s2, fp2_sub(s, bb)), fp2_sub(a3, bb));
-  fp2_t t = fp2_add(s, a4);
+  const fp2_t t = fp2_add(s, a4);
   bb = fp2_sub(t, s);
   e = fp2_add(e, fp2_add(fp2_sub(s, fp2_sub(t, bb)), fp2_sub(a4, bb)));
-  s = fp2_add(t, a5);
-  bb = fp2_sub(s, t);
-  e = fp2_add(e, fp2_add(fp2_sub(t, fp2_sub(s, bb)), fp2_sub(a5, bb)));
-  e = fp2_fma(s7, fp2_make(0x1p-45f, 0x1p-45f), fp2_fma(s6, fp2_make(0x1p-36f, 0x1p-36f), e));
-  hi = fp2_add(s, e);
-  lo = fp2_sub(e, fp2_sub(hi, s));
+  e = fp2_add(e, a57);
+  hi = fp2_add(t, e);
+  lo = fp2_sub(e, fp2_sub(hi, t));
 }
 
 // ---------------------------------------------------------------------------
@@ -496,6 +500,9 @@ struct TcPolDF {                                         // FP64-class: exact di
     float4 *__restrict__ Y = (float4 *)t.Y;
     const float ecf = tc_ld_x1(tq + (uint32_t)sh.exp_col());
     int ec = 0;
+    bool fast = false;
+    fp2_t FC = 0ull;
+    const float *s_fr = (const float *)(s_er + 2 * P + ((2 * P) & 1));
 #pragma unroll
     for (int pass = NPASS - 1; pass >= 0; --pass) {
       const int nrow = P - 4 * pass < 4 ? P - 4 * pass : 4;
@@ -508,23 +515,30 @@ struct TcPolDF {                                         // FP64-class: exact di
           tc_ld_x8(tq + (uint32_t)(sh.N2 + 24 * pass + 8 * c), *reinterpret_cast<float(*)[8]>(&B[8 * c]));
         }
       tc_wait_ld();
-      if (pass == NPASS - 1) ec = (int)ecf - 16;
+      if (pass == NPASS - 1) {
+        ec = (int)ecf - 16;
+        const int *rng = (const int *)(s_fr + 2 * P);
+        // both factors and their product stay normal floats: one product per row
+        fast = rng[0] >= -126 && rng[1] <= 127 && ec >= -126 && ec <= 127 && rng[0] + ec >= -126 && rng[1] + ec <= 127;
+        FC = fp2_make(tc_pow2(max(-126, min(127, ec))), tc_pow2(max(-126, min(127, ec))));
+      }
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         if (j < nrow) {
           const int r = 4 * pass + j;                    // complex row
           fp2_t hi, lo;
-          tc_combine2(fp2_make(B[6 * j + 2], B[6 * j + 5]), fp2_make(B[6 * j + 1], B[6 * j + 4]),
-                      fp2_make(B[6 * j], B[6 * j + 3]), fp2_make(A[6 * j + 2], A[6 * j + 5]),
-                      fp2_make(A[6 * j + 1], A[6 * j + 4]), fp2_make(A[6 * j], A[6 * j + 3]), hi, lo);
-          const int e0 = s_er[2 * r] + ec, e1 = s_er[2 * r + 1] + ec;
+          tc_combine2(fp2_make(B[6 * j + 4], B[6 * j + 5]), fp2_make(B[6 * j + 2], B[6 * j + 3]),
+                      fp2_make(B[6 * j], B[6 * j + 1]), fp2_make(A[6 * j + 4], A[6 * j + 5]),
+                      fp2_make(A[6 * j + 2], A[6 * j + 3]), fp2_make(A[6 * j], A[6 * j + 1]), hi, lo);
           float4 y;
-          if (e0 >= -126 && e1 >= -126) {
-            const fp2_t sc = fp2_make(tc_pow2(e0), tc_pow2(e1));
+          if (fast) {
+            const float2 fr = *(const float2 *)(s_fr + 2 * r);
+            const fp2_t sc = fp2_mul(fp2_make(fr.x, fr.y), FC);
             hi = fp2_mul(hi, sc);
             lo = fp2_mul(lo, sc);
             y = make_float4(fp2_x(hi), fp2_y(hi), fp2_x(lo), fp2_y(lo));
           } else {
+            const int e0 = s_er[2 * r] + ec, e1 = s_er[2 * r + 1] + ec;
             float h0 = fp2_x(hi), h1 = fp2_y(hi), l0 = fp2_x(lo), l1 = fp2_y(lo);
             tc_scale(h0, l0, e0);
             tc_scale(h1, l1, e1);
@@ -608,6 +622,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
     for (int i = tid; i < Pol::R_BYTES / 16; i += kTcThreads) dst[i] = __ldg(src + i);
     int *s_er = (int *)(smem + L.off_er);
     for (int i = tid; i < Pol::R2; i += kTcThreads) s_er[i] = __ldg(t.tc_er + i);
+    float *s_fr = (float *)(s_er + Pol::R2 + (Pol::R2 & 1));       // 2^e_rho as floats (clamped)
+    for (int i = tid; i < Pol::R2; i += kTcThreads) {
+      const int e = __ldg(t.tc_er + i);
+      s_fr[i] = tc_pow2(max(-126, min(127, e)));
+    }
+    if (tid == 0) {
+      int lo = 1 << 30, hi = -(1 << 30);
+      for (int i = 0; i < Pol::R2; ++i) { lo = min(lo, __ldg(t.tc_er + i)); hi = max(hi, __ldg(t.tc_er + i)); }
+      ((int *)(s_fr + Pol::R2))[0] = lo;
+      ((int *)(s_fr + Pol::R2))[1] = hi;
+    }
     uint32_t *s_mod = (uint32_t *)(smem + L.off_mod), *s_sat = (uint32_t *)(smem + L.off_sat);
     for (int i = tid; i < rows * a.xdim; i += kTcThreads) {
       s_mod[i] = a.mod[i];
@@ -636,8 +661,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
   tc_fence_after_sync();
   const uint32_t tbase = *tslot;
 
-  const uint32_t total = t.nc2 * (uint32_t)a.nrhs;
-  const uint32_t ntiles = (total + kTcCols - 1) / kTcCols;
+  // tiles [tb, te) of this launch: columns [c_begin, c_end), c_begin a multiple of the tile
+  const uint32_t total = (uint32_t)t.c_end;
+  const uint32_t tb = (uint32_t)(t.c_begin / kTcCols), te = (total + kTcCols - 1) / kTcCols;
+  const uint32_t ntiles = te - tb;
   const uint32_t mytiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   uint32_t issued = 0;                                   // MMA role: tiles committed
 
@@ -653,7 +680,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
         tc_abort(flag, t.status);
         break;
       }
-      Pol::produce(t, blockIdx.x + k * gridDim.x, total, cl, bbuf, s_mod, s_sat, s_sq);
+      Pol::produce(t, tb + blockIdx.x + k * gridDim.x, total, cl, bbuf, s_mod, s_sat, s_sq);
       tc_fence_proxy_async();
       tc_arrive(&full[g]);
     }
@@ -685,7 +712,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
         break;
       }
       tc_fence_after_sync();
-      const uint32_t colg = (blockIdx.x + k * gridDim.x) * (uint32_t)kTcCols + (uint32_t)(32 * q + lane);
+      const uint32_t colg = (tb + blockIdx.x + k * gridDim.x) * (uint32_t)kTcCols + (uint32_t)(32 * q + lane);
       Pol::drain(t, tbase + (uint32_t)s * 256u + ((uint32_t)(32 * q) << 16), colg, colg < total, s_er);
       tc_fence_before_sync();
       __syncwarp();

@@ -40,6 +40,7 @@ struct TwoPhaseArgs {
   cudaEvent_t phase1_done;        // recorded between the two phases when non-null (profiling hook)
   int phases;                     // 1: phase 1 only, 2: phase 2 only, 3: both
   uint32_t g_begin, g_end;        // configurations phase 2 computes
+  uint64_t c_begin, c_end;        // (configuration, rhs) columns of H(N-2, M) phase 1 computes
 };
 
 template <int M>
@@ -218,11 +219,17 @@ fock_twophase_x_df(const TwoPhaseArgs t) {
   const float4 *__restrict__ C = (const float4 *)a.C;
   float4 *__restrict__ Y = (float4 *)t.Y;
 
-  for (uint32_t tile = blockIdx.x * (uint32_t)nt; tile < nc2; tile += gridDim.x * (uint32_t)nt) {
-    const uint32_t g = tile + tid;
-    const bool live = g < nc2;
-    const uint32_t base = twophase_slots<M, float2>(live ? g : nc2 - 1u, a, nc2, s_mod, s_sat, s_sq, slot, nt);
-    for (int j = 0; j < nrhs; ++j) {
+  // one thread per (configuration, right-hand side): the nrhs values of one
+  // gathered configuration are adjacent, so a warp's gathers stay coalesced
+  const size_t total = t.c_end;                         // columns [c_begin, c_end) of this launch
+  for (size_t tile = t.c_begin + blockIdx.x * (size_t)nt; tile < t.c_end; tile += gridDim.x * (size_t)nt) {
+    const size_t col = tile + tid;
+    const bool live = col < total;
+    const size_t cc = live ? col : total - 1u;
+    const uint32_t g = (uint32_t)(cc / (size_t)nrhs);
+    const int j = (int)(cc - (size_t)g * nrhs);
+    const uint32_t base = twophase_slots<M, float2>(g, a, nc2, s_mod, s_sat, s_sq, slot, nt);
+    {
       for (int r0 = 0; r0 < P; r0 += RB) {
         fp2_t K12h[RB], K12l[RB], K3h[RB / 2], K3l[RB / 2];
 #pragma unroll
@@ -293,7 +300,7 @@ fock_twophase_x_df(const TwoPhaseArgs t) {
 // gathers) 2 blocks per SM (N = 20, M = 8, 16 right-hand sides: 24.5 ms
 // against 27.7 ms at 5 blocks).
 template <int M>
-__global__ void __launch_bounds__(FOCK_APPLY_THREADS, (M <= 6 ? 3 : 2))
+__global__ void __launch_bounds__(FOCK_APPLY_THREADS, (M <= 6 ? 3 : (M <= 8 ? 2 : 4)))
 fock_twophase_sigma_df(const TwoPhaseArgs t) {
   const ApplyArgs<uint32_t> &a = t.a;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -318,11 +325,16 @@ fock_twophase_sigma_df(const TwoPhaseArgs t) {
   const bool failed = t.status && *(volatile const int *)t.status;
 
   const uint32_t g_end = t.g_end;
-  for (uint32_t tile = t.g_begin + blockIdx.x * (uint32_t)nt; tile < g_end; tile += gridDim.x * (uint32_t)nt) {
-    const uint32_t g = tile + tid;
-    const bool live = g < g_end;
+  // one thread per (configuration, right-hand side) of [g_begin, g_end)
+  const size_t cbeg = (size_t)t.g_begin * nrhs, cend = (size_t)g_end * nrhs;
+  for (size_t tile = cbeg + blockIdx.x * (size_t)nt; tile < cend; tile += gridDim.x * (size_t)nt) {
+    const size_t col = tile + tid;
+    const bool live = col < cend;
+    const size_t cc = live ? col : cend - 1u;
+    const uint32_t g = (uint32_t)(cc / (size_t)nrhs);
+    const int j = (int)(cc - (size_t)g * nrhs);
     int S[M], n[M];
-    fock_decode_fast<M>(live ? g : g_end - 1u, a.N, nc, s_sat, a.xdim, S);
+    fock_decode_fast<M>(g, a.N, nc, s_sat, a.xdim, S);
 #pragma unroll
     for (int m = 0; m < M; ++m) n[m] = S[m] - (m > 0 ? S[m - 1] : 0);
     float2 sq0[M], sq1[M];                                  // sqrt(n_m), sqrt(n_m - 1) as pairs
@@ -333,7 +345,7 @@ fock_twophase_sigma_df(const TwoPhaseArgs t) {
     }
     uint32_t P1[M], P2[M];
     const uint32_t q0 = twophase_prefix2<M>(S, s_mod, a.xdim, nc2, P1, P2);
-    for (int j = 0; j < nrhs; ++j) {
+    {
       fp2_t Ah = 0ull, Al = 0ull;
       // every removal is evaluated: an impossible one has amplitude 0
       // (sqrt(0) or sqrt(n - 1) = 0 for n = 1) and reads the block start
@@ -388,11 +400,15 @@ fock_twophase_x_mixed(const TwoPhaseArgs t) {
   const float2 *__restrict__ C = (const float2 *)a.C;
   float2 *__restrict__ Y = (float2 *)t.Y;
 
-  for (uint32_t tile = blockIdx.x * (uint32_t)nt; tile < nc2; tile += gridDim.x * (uint32_t)nt) {
-    const uint32_t g = tile + tid;
-    const bool live = g < nc2;
-    const uint32_t base = twophase_slots<M, float>(live ? g : nc2 - 1u, a, nc2, s_mod, s_sat, s_sq, slot, nt);
-    for (int j = 0; j < nrhs; ++j) {
+  const size_t total = t.c_end;                         // columns [c_begin, c_end) of this launch        // one thread per (configuration, right-hand side)
+  for (size_t tile = t.c_begin + blockIdx.x * (size_t)nt; tile < t.c_end; tile += gridDim.x * (size_t)nt) {
+    const size_t col = tile + tid;
+    const bool live = col < total;
+    const size_t cc = live ? col : total - 1u;
+    const uint32_t g = (uint32_t)(cc / (size_t)nrhs);
+    const int j = (int)(cc - (size_t)g * nrhs);
+    const uint32_t base = twophase_slots<M, float>(g, a, nc2, s_mod, s_sat, s_sq, slot, nt);
+    {
       for (int r0 = 0; r0 < P; r0 += RB) {
         fp2_t A1[RB], A2[RB];
 #pragma unroll
@@ -432,7 +448,7 @@ fock_twophase_x_mixed(const TwoPhaseArgs t) {
 // skipped impossible removals at 8 blocks); 2 blocks for M = 7, 8 (N = 20,
 // M = 8, 16 right-hand sides: 9.0 ms against 12.4 ms at 5 blocks).
 template <int M>
-__global__ void __launch_bounds__(FOCK_APPLY_THREADS, (M <= 6 ? 4 : 2))
+__global__ void __launch_bounds__(FOCK_APPLY_THREADS, (M <= 6 ? 4 : (M <= 8 ? 2 : 4)))
 fock_twophase_sigma_mixed(const TwoPhaseArgs t) {
   const ApplyArgs<uint32_t> &a = t.a;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -455,11 +471,16 @@ fock_twophase_sigma_mixed(const TwoPhaseArgs t) {
                                                                         : (float)a.out_scale;
 
   const uint32_t g_end = t.g_end;
-  for (uint32_t tile = t.g_begin + blockIdx.x * (uint32_t)nt; tile < g_end; tile += gridDim.x * (uint32_t)nt) {
-    const uint32_t g = tile + tid;
-    const bool live = g < g_end;
+  // one thread per (configuration, right-hand side) of [g_begin, g_end)
+  const size_t cbeg = (size_t)t.g_begin * nrhs, cend = (size_t)g_end * nrhs;
+  for (size_t tile = cbeg + blockIdx.x * (size_t)nt; tile < cend; tile += gridDim.x * (size_t)nt) {
+    const size_t col = tile + tid;
+    const bool live = col < cend;
+    const size_t cc = live ? col : cend - 1u;
+    const uint32_t g = (uint32_t)(cc / (size_t)nrhs);
+    const int j = (int)(cc - (size_t)g * nrhs);
     int S[M], n[M];
-    fock_decode_fast<M>(live ? g : g_end - 1u, a.N, nc, s_sat, a.xdim, S);
+    fock_decode_fast<M>(g, a.N, nc, s_sat, a.xdim, S);
 #pragma unroll
     for (int m = 0; m < M; ++m) n[m] = S[m] - (m > 0 ? S[m - 1] : 0);
     float sq0[M], sq1[M];                                   // sqrt(n_m), sqrt(n_m - 1)
@@ -470,7 +491,7 @@ fock_twophase_sigma_mixed(const TwoPhaseArgs t) {
     }
     uint32_t P1[M], P2[M];
     const uint32_t q0 = twophase_prefix2<M>(S, s_mod, a.xdim, nc2, P1, P2);
-    for (int j = 0; j < nrhs; ++j) {
+    {
       fp2_t Sh = 0ull, Sl = 0ull;
       // every removal is evaluated: an impossible one has amplitude 0
       // (sqrt(0) or sqrt(n - 1) = 0 for n = 1) and reads the block start
@@ -500,7 +521,7 @@ __host__ __device__ inline size_t twophase_sigma_smem(int rows, int xdim, int ns
 }
 
 template <class K>
-int fock_launch_grid(K kern, const TwoPhaseArgs &t, uint32_t n, size_t smem, int device, cudaStream_t stream) {
+int fock_launch_grid(K kern, const TwoPhaseArgs &t, uint64_t n, size_t smem, int device, cudaStream_t stream) {
   const int threads = FOCK_APPLY_THREADS;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -148,6 +148,8 @@ struct fock_ham {
   size_t hb_bytes;
   cudaStream_t hb_copy;
   cudaEvent_t hb_ev[8];
+  cudaStream_t hb_copy_in;  // chunked copy of C into hb_in, with hb_in_ev[0..7] after the chunks
+  cudaEvent_t hb_in_ev[9];  // (and hb_in_ev[8] ordering that stream after the caller's)
 };
 
 // Launch helpers implemented in fock_apply.cu and used by fock_lanczos.cu.

@@ -7,12 +7,12 @@ static int launch_df(const TwoPhaseArgs &t, int dev, cudaStream_t s) {
   const ApplyArgs<uint32_t> &a = t.a;
   const TwoPhaseSmem<M> L(a.xdim, a.nsq, 2 * sizeof(float4), sizeof(TwoPhaseSlot) * M, FOCK_APPLY_THREADS);
   if (t.phases & 1) {
-    const int st = fock_launch_grid(fock_twophase_x_df<M>, t, t.nc2, L.total, dev, s);
+    const int st = fock_launch_grid(fock_twophase_x_df<M>, t, t.c_end - t.c_begin, L.total, dev, s);
     if (st) return st;
     if (t.phase1_done) FOCK_CUDA_TRY(cudaEventRecord(t.phase1_done, s));
   }
   if (!(t.phases & 2)) return FOCK_OK;
-  return fock_launch_grid(fock_twophase_sigma_df<M>, t, t.g_end - t.g_begin, twophase_sigma_smem(a.rows, a.xdim, a.nsq),
+  return fock_launch_grid(fock_twophase_sigma_df<M>, t, (uint64_t)(t.g_end - t.g_begin) * a.nrhs, twophase_sigma_smem(a.rows, a.xdim, a.nsq),
                           dev, s);
 }
 
@@ -21,12 +21,12 @@ static int launch_mixed(const TwoPhaseArgs &t, int dev, cudaStream_t s) {
   const ApplyArgs<uint32_t> &a = t.a;
   const TwoPhaseSmem<M> L(a.xdim, a.nsq, sizeof(float2), sizeof(TwoPhaseSlot) * M, FOCK_APPLY_THREADS);
   if (t.phases & 1) {
-    const int st = fock_launch_grid(fock_twophase_x_mixed<M>, t, t.nc2, L.total, dev, s);
+    const int st = fock_launch_grid(fock_twophase_x_mixed<M>, t, t.c_end - t.c_begin, L.total, dev, s);
     if (st) return st;
     if (t.phase1_done) FOCK_CUDA_TRY(cudaEventRecord(t.phase1_done, s));
   }
   if (!(t.phases & 2)) return FOCK_OK;
-  return fock_launch_grid(fock_twophase_sigma_mixed<M>, t, t.g_end - t.g_begin,
+  return fock_launch_grid(fock_twophase_sigma_mixed<M>, t, (uint64_t)(t.g_end - t.g_begin) * a.nrhs,
                           twophase_sigma_smem(a.rows, a.xdim, a.nsq), dev, s);
 }
 

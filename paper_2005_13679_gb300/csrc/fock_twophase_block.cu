@@ -74,11 +74,46 @@ static bool block_tables(const std::complex<double> *R, double scale, std::vecto
   return true;
 }
 
-// Shared memory of phase 1: block coefficients, binomial tables, square roots.
+// Phase 1 runs a loop over the blocks at run time, each block by code
+// specialised for its size (1 .. floor(M/2) + 1 pairs), instead of one fully
+// unrolled body of all 2M - 1 blocks (about 4,800 instructions per column at
+// M = 10, 40 % of the issue slots stalled on instruction fetch).  The
+// column's per-orbital values (target offsets U, V and square roots) live in
+// a shared-memory slot per thread so that the run-time orbital indices of a
+// block need no local memory.
+template <class SqT>
+struct BlockSlot {
+  uint32_t U, V;
+  SqT b, c;                 // sqrt(n'_m + 1), sqrt(n'_m + 2)
+};
+
+template <int M, class SqT>
+__device__ __forceinline__ uint32_t block_slots(uint32_t np, const ApplyArgs<uint32_t> &a, uint32_t nc2,
+                                                const uint32_t *s_mod, const uint32_t *s_sat, const SqT *s_sq,
+                                                BlockSlot<SqT> *slot, int nt) {
+  int S[M];
+  fock_decode_fast<M>(np, a.N - 2, nc2, s_sat, a.xdim, S);
+  uint32_t U[M], V[M];
+  const uint32_t base = twophase_targets<M>(S, s_mod, a.xdim, a.nc, U, V);
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int occ = S[m] - (m > 0 ? S[m - 1] : 0);
+    BlockSlot<SqT> z;
+    z.U = U[m];
+    z.V = V[m];
+    z.b = s_sq[occ + 1];
+    z.c = s_sq[occ + 2];
+    slot[m * nt] = z;
+  }
+  return base;
+}
+
+// Shared memory of phase 1: block coefficients, binomial tables, square roots,
+// the threads' slots.
 template <int M>
-struct BlockSmem {
-  size_t off_coef, off_mod, off_sat, off_sq, total;
-  __host__ __device__ BlockSmem(int xdim, int nsq, size_t coef_bytes) {
+struct BlockSmemRT {
+  size_t off_coef, off_mod, off_sat, off_sq, off_slot, total;
+  __host__ __device__ BlockSmemRT(int xdim, int nsq, size_t coef_bytes, size_t slot_bytes, int threads) {
     constexpr PairBlocks<M> pb;
     const int rows = M - 1;
     size_t o = 0;
@@ -86,12 +121,13 @@ struct BlockSmem {
     off_mod = o;  o = fock_align16(o + 4 * (size_t)rows * xdim);
     off_sat = o;  o = fock_align16(o + 4 * (size_t)rows * xdim);
     off_sq = o;   o = fock_align16(o + 8 * (size_t)nsq);
+    off_slot = o; o = fock_align16(o + slot_bytes * M * (size_t)threads);
     total = o;
   }
 };
 
 template <int M, class CoefT, class SqT>
-__device__ __forceinline__ void block_stage(const TwoPhaseArgs &t, const BlockSmem<M> &L, unsigned char *smem) {
+__device__ __forceinline__ void block_stage_rt(const TwoPhaseArgs &t, const BlockSmemRT<M> &L, unsigned char *smem) {
   constexpr PairBlocks<M> pb;
   const ApplyArgs<uint32_t> &a = t.a;
   CoefT *s_coef = (CoefT *)(smem + L.off_coef);
@@ -106,66 +142,37 @@ __device__ __forceinline__ void block_stage(const TwoPhaseArgs &t, const BlockSm
   __syncthreads();
 }
 
-// Block K of M orbitals: pairs (s, K - s) for s = lo .. K/2, their count and
-// the offset of the block's coefficients (sum of the earlier blocks' squares).
-__host__ __device__ constexpr int blk_lo(int M, int K) { return K - (M - 1) > 0 ? K - (M - 1) : 0; }
-__host__ __device__ constexpr int blk_cnt(int M, int K) { return K / 2 - blk_lo(M, K) + 1; }
-__host__ __device__ constexpr int blk_coff(int M, int K) {
-  int c = 0;
-  for (int k = 0; k < K; ++k) c += blk_cnt(M, k) * blk_cnt(M, k);
-  return c;
-}
-__host__ __device__ constexpr int blk_pidx(int M, int s, int l) { return s * M - (s * (s - 1)) / 2 + (l - s); }
-
-// Per-thread state of one (N-2)-configuration column shared by its blocks.
-template <int M, class SqT>
-struct BlockCol {
-  uint32_t base, U[M], V[M];
-  SqT sq1[M], sq2[M];      // sqrt(n'_m + 1), sqrt(n'_m + 2)
-};
-
-template <int M, class SqT>
-__device__ __forceinline__ void block_col(uint32_t np, const ApplyArgs<uint32_t> &a, uint32_t nc2,
-                                          const uint32_t *s_mod, const uint32_t *s_sat, const SqT *s_sq,
-                                          BlockCol<M, SqT> &c) {
-  int S[M];
-  fock_decode_fast<M>(np, a.N - 2, nc2, s_sat, a.xdim, S);
-  c.base = twophase_targets<M>(S, s_mod, a.xdim, a.nc, c.U, c.V);
-#pragma unroll
-  for (int m = 0; m < M; ++m) {
-    const int occ = S[m] - (m > 0 ? S[m - 1] : 0);
-    c.sq1[m] = s_sq[occ + 1];
-    c.sq2[m] = s_sq[occ + 2];
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Phase 1, FP32 pairs: X_a = B_a C[n' + a] by Dekker products (lanes Re, Im),
 // Y_r = sum_a R[r][a] X_a with the coefficient's real part times (Re X, Im X)
-// and, for complex coefficients, (-Im R, Im R) times (Im X, Re X).
+// and, for complex coefficients, (-Im R, Im R) times (Im X, Re X).  One block
+// of NB pairs (s, K - s), s = lo .. lo + NB - 1, coefficients from s_coef[co].
 // ---------------------------------------------------------------------------
-template <int M, int K>
-__device__ __forceinline__ void block_df(const BlockCol<M, float2> &c, const float4 *__restrict__ C,
-                                         float4 *__restrict__ Y, const float4 *s_coef, uint32_t nrhs, uint32_t jr,
-                                         uint32_t col, bool live, bool real) {
-  constexpr int nb = blk_cnt(M, K), lo = blk_lo(M, K), co = blk_coff(M, K), P = M * (M + 1) / 2;
-  float4 v[nb];
+template <int M, int NB>
+__device__ __forceinline__ void block_df(int K, int lo, int co, uint32_t base, const BlockSlot<float2> *slot, int nt,
+                                         const float4 *__restrict__ C, float4 *__restrict__ Y, const float4 *s_coef,
+                                         uint32_t nrhs, uint32_t jr, size_t col, bool live, bool real) {
+  constexpr int P = M * (M + 1) / 2;
+  float4 v[NB];
+  float2 amp[NB];
 #pragma unroll
-  for (int i = 0; i < nb; ++i) v[i] = __ldg(C + (size_t)(c.base - c.U[lo + i] - c.V[K - lo - i]) * nrhs + jr);
-  fp2_t Xh[nb], Xl[nb];
-#pragma unroll
-  for (int i = 0; i < nb; ++i) {
-    const int s = lo + i, l = K - lo - i;
-    const float2 amp = df_mul(c.sq1[s], s == l ? c.sq2[s] : c.sq1[l]);
-    fp2_dprod(fp2_make(v[i].x, v[i].y), fp2_make(v[i].z, v[i].w), fp2_make(amp.x, amp.x), fp2_make(amp.y, amp.y),
-              Xh[i], Xl[i]);
+  for (int i = 0; i < NB; ++i) {
+    const int s = lo + i, l = K - s;
+    const BlockSlot<float2> zs = slot[s * nt], zl = slot[l * nt];
+    v[i] = __ldg(C + (size_t)(base - zs.U - zl.V) * nrhs + jr);
+    amp[i] = df_mul(zs.b, s == l ? zs.c : zl.b);
   }
+  fp2_t Xh[NB], Xl[NB];
 #pragma unroll
-  for (int r = 0; r < nb; ++r) {
+  for (int i = 0; i < NB; ++i)
+    fp2_dprod(fp2_make(v[i].x, v[i].y), fp2_make(v[i].z, v[i].w), fp2_make(amp[i].x, amp[i].x),
+              fp2_make(amp[i].y, amp[i].y), Xh[i], Xl[i]);
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
     fp2_t h = 0ull, lw = 0ull;
 #pragma unroll
-    for (int i = 0; i < nb; ++i) {
-      const float4 w = s_coef[co + r * nb + i];            // (Re R hi, Im R hi, Re R lo, Im R lo)
+    for (int i = 0; i < NB; ++i) {
+      const float4 w = s_coef[co + r * NB + i];            // (Re R hi, Im R hi, Re R lo, Im R lo)
       fp2_t p, e;
       fp2_dprod(Xh[i], Xl[i], fp2_make(w.x, w.x), fp2_make(w.z, w.z), p, e);
       fp2_dacc(h, lw, p, e);
@@ -174,40 +181,50 @@ __device__ __forceinline__ void block_df(const BlockCol<M, float2> &c, const flo
         fp2_dacc(h, lw, p, e);
       }
     }
-    if (live) Y[twophase_yidx(blk_pidx(M, lo + r, K - lo - r), col, P)] = make_float4(fp2_x(h), fp2_y(h), fp2_x(lw), fp2_y(lw));
-  }
-}
-
-template <int M, int K = 0>
-__device__ __forceinline__ void blocks_df(const BlockCol<M, float2> &c, const float4 *__restrict__ C,
-                                          float4 *__restrict__ Y, const float4 *s_coef, uint32_t nrhs, uint32_t jr,
-                                          uint32_t col, bool live, bool real) {
-  if constexpr (K < 2 * M - 1) {
-    block_df<M, K>(c, C, Y, s_coef, nrhs, jr, col, live, real);
-    blocks_df<M, K + 1>(c, C, Y, s_coef, nrhs, jr, col, live, real);
+    const int s = lo + r, l = K - s;
+    if (live) Y[twophase_yidx(s * M - (s * (s - 1)) / 2 + (l - s), col, P)] =
+        make_float4(fp2_x(h), fp2_y(h), fp2_x(lw), fp2_y(lw));
   }
 }
 
 template <int M>
-__global__ void __launch_bounds__(FOCK_APPLY_THREADS, 3) fock_twophase_x_block_df(const TwoPhaseArgs t) {
+__global__ void __launch_bounds__(FOCK_APPLY_THREADS, 4) fock_twophase_x_block_df(const TwoPhaseArgs t) {
   const ApplyArgs<uint32_t> &a = t.a;
   extern __shared__ __align__(16) unsigned char smem[];
-  const BlockSmem<M> L(a.xdim, a.nsq, sizeof(float4));
-  block_stage<M, float4, float2>(t, L, smem);
+  const BlockSmemRT<M> L(a.xdim, a.nsq, sizeof(float4), sizeof(BlockSlot<float2>), blockDim.x);
+  block_stage_rt<M, float4, float2>(t, L, smem);
   const float4 *s_coef = (const float4 *)(smem + L.off_coef);
   const uint32_t *s_mod = (const uint32_t *)(smem + L.off_mod);
   const uint32_t *s_sat = (const uint32_t *)(smem + L.off_sat);
   const float2 *s_sq = (const float2 *)(smem + L.off_sq);
-  const uint32_t nrhs = (uint32_t)a.nrhs, total = t.nc2 * nrhs;
+  const int nt = blockDim.x;
+  BlockSlot<float2> *slot = (BlockSlot<float2> *)(smem + L.off_slot) + threadIdx.x;
+  const uint32_t nrhs = (uint32_t)a.nrhs;
+  const size_t total = t.c_end;                           // columns [c_begin, c_end) of this launch
   const bool real = a.real;
-  for (uint32_t tile = blockIdx.x * (uint32_t)blockDim.x; tile < total; tile += gridDim.x * (uint32_t)blockDim.x) {
-    const uint32_t col = tile + threadIdx.x;
+  const float4 *__restrict__ C = (const float4 *)a.C;
+  float4 *__restrict__ Y = (float4 *)t.Y;
+  for (size_t tile = t.c_begin + blockIdx.x * (size_t)nt; tile < total; tile += gridDim.x * (size_t)nt) {
+    const size_t col = tile + threadIdx.x;
     const bool live = col < total;
-    const uint32_t cc = live ? col : total - 1u;
-    const uint32_t np = nrhs == 1u ? cc : cc / nrhs;
-    BlockCol<M, float2> c;
-    block_col<M, float2>(np, a, t.nc2, s_mod, s_sat, s_sq, c);
-    blocks_df<M>(c, (const float4 *)a.C, (float4 *)t.Y, s_coef, nrhs, cc - np * nrhs, col, live, real);
+    const size_t cc = live ? col : total - 1u;
+    const uint32_t np = (uint32_t)(cc / nrhs);
+    const uint32_t jr = (uint32_t)(cc - (size_t)np * nrhs);
+    const uint32_t base = block_slots<M, float2>(np, a, t.nc2, s_mod, s_sat, s_sq, slot, nt);
+    int co = 0;
+#pragma unroll 1
+    for (int K = 0; K < 2 * M - 1; ++K) {
+      const int lo = K - (M - 1) > 0 ? K - (M - 1) : 0, nb = K / 2 - lo + 1;
+      switch (nb) {
+        case 1: block_df<M, 1>(K, lo, co, base, slot, nt, C, Y, s_coef, nrhs, jr, col, live, real); break;
+        case 2: block_df<M, 2>(K, lo, co, base, slot, nt, C, Y, s_coef, nrhs, jr, col, live, real); break;
+        case 3: block_df<M, 3>(K, lo, co, base, slot, nt, C, Y, s_coef, nrhs, jr, col, live, real); break;
+        case 4: block_df<M, 4>(K, lo, co, base, slot, nt, C, Y, s_coef, nrhs, jr, col, live, real); break;
+        case 5: block_df<M, 5>(K, lo, co, base, slot, nt, C, Y, s_coef, nrhs, jr, col, live, real); break;
+        default: block_df<M, 6>(K, lo, co, base, slot, nt, C, Y, s_coef, nrhs, jr, col, live, real); break;
+      }
+      co += nb * nb;
+    }
   }
 }
 
@@ -215,42 +232,34 @@ __global__ void __launch_bounds__(FOCK_APPLY_THREADS, 3) fock_twophase_x_block_d
 // Phase 1, FP32-mixed: X_a = B_a C[n' + a] in FP32 from complex64 C, FP32
 // products and sums per block row, Y as complex64.
 // ---------------------------------------------------------------------------
-template <int M, int K>
-__device__ __forceinline__ void block_mixed(const BlockCol<M, float> &c, const float2 *__restrict__ C,
-                                            float2 *__restrict__ Y, const float2 *s_coef, uint32_t nrhs, uint32_t jr,
-                                            uint32_t col, bool live) {
-  constexpr int nb = blk_cnt(M, K), lo = blk_lo(M, K), co = blk_coff(M, K), P = M * (M + 1) / 2;
-  fp2_t Xp[nb], Xs[nb];                                   // (Re X, Im X) and (Im X, Re X)
+template <int M, int NB>
+__device__ __forceinline__ void block_mixed(int K, int lo, int co, uint32_t base, const BlockSlot<float> *slot, int nt,
+                                            const float2 *__restrict__ C, float2 *__restrict__ Y, const float2 *s_coef,
+                                            uint32_t nrhs, uint32_t jr, size_t col, bool live) {
+  constexpr int P = M * (M + 1) / 2;
+  fp2_t Xp[NB], Xs[NB];                                   // (Re X, Im X) and (Im X, Re X)
 #pragma unroll
-  for (int i = 0; i < nb; ++i) {
-    const int s = lo + i, l = K - lo - i;
-    const float2 v = __ldg(C + (size_t)(c.base - c.U[s] - c.V[l]) * nrhs + jr);
-    const float amp = c.sq1[s] * (s == l ? c.sq2[s] : c.sq1[l]);
+  for (int i = 0; i < NB; ++i) {
+    const int s = lo + i, l = K - s;
+    const BlockSlot<float> zs = slot[s * nt], zl = slot[l * nt];
+    const float2 v = __ldg(C + (size_t)(base - zs.U - zl.V) * nrhs + jr);
+    const float amp = zs.b * (s == l ? zs.c : zl.b);
     Xp[i] = fp2_make(v.x * amp, v.y * amp);
     Xs[i] = fp2_make(v.y * amp, v.x * amp);
   }
 #pragma unroll
-  for (int r = 0; r < nb; ++r) {
+  for (int r = 0; r < NB; ++r) {
     fp2_t A1 = 0ull, A2 = 0ull;
 #pragma unroll
-    for (int i = 0; i < nb; ++i) {
-      const float2 w = s_coef[co + r * nb + i];
+    for (int i = 0; i < NB; ++i) {
+      const float2 w = s_coef[co + r * NB + i];
       const fp2_t Rp = fp2_make(w.x, w.y);
       A1 = fp2_fma(Rp, Xp[i], A1);                         // (Re R Re X, Im R Im X)
       A2 = fp2_fma(Rp, Xs[i], A2);                         // (Re R Im X, Im R Re X)
     }
-    if (live)
-      Y[twophase_yidx(blk_pidx(M, lo + r, K - lo - r), col, P)] = make_float2(fp2_x(A1) - fp2_y(A1), fp2_x(A2) + fp2_y(A2));
-  }
-}
-
-template <int M, int K = 0>
-__device__ __forceinline__ void blocks_mixed(const BlockCol<M, float> &c, const float2 *__restrict__ C,
-                                             float2 *__restrict__ Y, const float2 *s_coef, uint32_t nrhs, uint32_t jr,
-                                             uint32_t col, bool live) {
-  if constexpr (K < 2 * M - 1) {
-    block_mixed<M, K>(c, C, Y, s_coef, nrhs, jr, col, live);
-    blocks_mixed<M, K + 1>(c, C, Y, s_coef, nrhs, jr, col, live);
+    const int s = lo + r, l = K - s;
+    if (live) Y[twophase_yidx(s * M - (s * (s - 1)) / 2 + (l - s), col, P)] =
+        make_float2(fp2_x(A1) - fp2_y(A1), fp2_x(A2) + fp2_y(A2));
   }
 }
 
@@ -258,21 +267,39 @@ template <int M>
 __global__ void __launch_bounds__(FOCK_APPLY_THREADS, 4) fock_twophase_x_block_mixed(const TwoPhaseArgs t) {
   const ApplyArgs<uint32_t> &a = t.a;
   extern __shared__ __align__(16) unsigned char smem[];
-  const BlockSmem<M> L(a.xdim, a.nsq, sizeof(float2));
-  block_stage<M, float2, float>(t, L, smem);
+  const BlockSmemRT<M> L(a.xdim, a.nsq, sizeof(float2), sizeof(BlockSlot<float>), blockDim.x);
+  block_stage_rt<M, float2, float>(t, L, smem);
   const float2 *s_coef = (const float2 *)(smem + L.off_coef);
   const uint32_t *s_mod = (const uint32_t *)(smem + L.off_mod);
   const uint32_t *s_sat = (const uint32_t *)(smem + L.off_sat);
   const float *s_sq = (const float *)(smem + L.off_sq);
-  const uint32_t nrhs = (uint32_t)a.nrhs, total = t.nc2 * nrhs;
-  for (uint32_t tile = blockIdx.x * (uint32_t)blockDim.x; tile < total; tile += gridDim.x * (uint32_t)blockDim.x) {
-    const uint32_t col = tile + threadIdx.x;
+  const int nt = blockDim.x;
+  BlockSlot<float> *slot = (BlockSlot<float> *)(smem + L.off_slot) + threadIdx.x;
+  const uint32_t nrhs = (uint32_t)a.nrhs;
+  const size_t total = t.c_end;                           // columns [c_begin, c_end) of this launch
+  const float2 *__restrict__ C = (const float2 *)a.C;
+  float2 *__restrict__ Y = (float2 *)t.Y;
+  for (size_t tile = t.c_begin + blockIdx.x * (size_t)nt; tile < total; tile += gridDim.x * (size_t)nt) {
+    const size_t col = tile + threadIdx.x;
     const bool live = col < total;
-    const uint32_t cc = live ? col : total - 1u;
-    const uint32_t np = nrhs == 1u ? cc : cc / nrhs;
-    BlockCol<M, float> c;
-    block_col<M, float>(np, a, t.nc2, s_mod, s_sat, s_sq, c);
-    blocks_mixed<M>(c, (const float2 *)a.C, (float2 *)t.Y, s_coef, nrhs, cc - np * nrhs, col, live);
+    const size_t cc = live ? col : total - 1u;
+    const uint32_t np = (uint32_t)(cc / nrhs);
+    const uint32_t jr = (uint32_t)(cc - (size_t)np * nrhs);
+    const uint32_t base = block_slots<M, float>(np, a, t.nc2, s_mod, s_sat, s_sq, slot, nt);
+    int co = 0;
+#pragma unroll 1
+    for (int K = 0; K < 2 * M - 1; ++K) {
+      const int lo = K - (M - 1) > 0 ? K - (M - 1) : 0, nb = K / 2 - lo + 1;
+      switch (nb) {
+        case 1: block_mixed<M, 1>(K, lo, co, base, slot, nt, C, Y, s_coef, nrhs, jr, col, live); break;
+        case 2: block_mixed<M, 2>(K, lo, co, base, slot, nt, C, Y, s_coef, nrhs, jr, col, live); break;
+        case 3: block_mixed<M, 3>(K, lo, co, base, slot, nt, C, Y, s_coef, nrhs, jr, col, live); break;
+        case 4: block_mixed<M, 4>(K, lo, co, base, slot, nt, C, Y, s_coef, nrhs, jr, col, live); break;
+        case 5: block_mixed<M, 5>(K, lo, co, base, slot, nt, C, Y, s_coef, nrhs, jr, col, live); break;
+        default: block_mixed<M, 6>(K, lo, co, base, slot, nt, C, Y, s_coef, nrhs, jr, col, live); break;
+      }
+      co += nb * nb;
+    }
   }
 }
 
@@ -280,16 +307,19 @@ template <int M>
 static int launch_block(const TwoPhaseArgs &t, bool mixed, int dev, cudaStream_t s) {
   const ApplyArgs<uint32_t> &a = t.a;
   if (t.phases & 1) {
-    const uint32_t n = t.nc2 * (uint32_t)a.nrhs;
-    const int st = mixed ? fock_launch_grid(fock_twophase_x_block_mixed<M>, t, n,
-                                            BlockSmem<M>(a.xdim, a.nsq, sizeof(float2)).total, dev, s)
-                         : fock_launch_grid(fock_twophase_x_block_df<M>, t, n,
-                                            BlockSmem<M>(a.xdim, a.nsq, sizeof(float4)).total, dev, s);
+    const uint64_t n = t.c_end - t.c_begin;
+    const int st =
+        mixed ? fock_launch_grid(fock_twophase_x_block_mixed<M>, t, n,
+                                 BlockSmemRT<M>(a.xdim, a.nsq, sizeof(float2), sizeof(BlockSlot<float>), FOCK_APPLY_THREADS).total,
+                                 dev, s)
+              : fock_launch_grid(fock_twophase_x_block_df<M>, t, n,
+                                 BlockSmemRT<M>(a.xdim, a.nsq, sizeof(float4), sizeof(BlockSlot<float2>), FOCK_APPLY_THREADS).total,
+                                 dev, s);
     if (st) return st;
     if (t.phase1_done) FOCK_CUDA_TRY(cudaEventRecord(t.phase1_done, s));
   }
   if (!(t.phases & 2)) return FOCK_OK;
-  const uint32_t n = t.g_end - t.g_begin;
+  const uint64_t n = (uint64_t)(t.g_end - t.g_begin) * a.nrhs;
   const size_t sm = twophase_sigma_smem(a.rows, a.xdim, a.nsq);
   return mixed ? fock_launch_grid(fock_twophase_sigma_mixed<M>, t, n, sm, dev, s)
                : fock_launch_grid(fock_twophase_sigma_df<M>, t, n, sm, dev, s);
@@ -341,7 +371,8 @@ bool fock_block_tables(int M, const std::complex<double> *R, double scale, std::
 size_t fock_block_smem(int M, int xdim, int nsq, bool mixed) {
   switch (M) {
 #define FOCK_BLK_SM(MM) \
-    case MM: return BlockSmem<MM>(xdim, nsq, mixed ? sizeof(float2) : sizeof(float4)).total;
+    case MM: return mixed ? BlockSmemRT<MM>(xdim, nsq, sizeof(float2), sizeof(BlockSlot<float>), FOCK_APPLY_THREADS).total \
+                          : BlockSmemRT<MM>(xdim, nsq, sizeof(float4), sizeof(BlockSlot<float2>), FOCK_APPLY_THREADS).total;
     FOCK_BLK_SM(2)
     FOCK_BLK_SM(3)
     FOCK_BLK_SM(4)

@@ -171,8 +171,7 @@ static int launch_tc(const TwoPhaseArgs &targ, int dev, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(fock_twophase_x_tc<M, Pol>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return fock_cuda_status(e);
-    const uint64_t total = (uint64_t)t.nc2 * (uint64_t)a.nrhs;
-    const uint64_t tiles = (total + kTcCols - 1) / kTcCols;
+    const uint64_t tiles = (t.c_end + kTcCols - 1) / kTcCols - t.c_begin / kTcCols;
     uint64_t grid = (uint64_t)fock_get_sm_count(dev);
     if (grid > tiles) grid = tiles;
     if (grid < 1) grid = 1;
@@ -182,7 +181,7 @@ static int launch_tc(const TwoPhaseArgs &targ, int dev, cudaStream_t s) {
     if (t.phase1_done) FOCK_CUDA_TRY(cudaEventRecord(t.phase1_done, s));
   }
   if (!(t.phases & 2)) return FOCK_OK;
-  const uint32_t n = t.g_end - t.g_begin;
+  const uint64_t n = (uint64_t)(t.g_end - t.g_begin) * a.nrhs;
   if (std::is_same<Pol, TcPolMixed<M>>::value)
     return fock_launch_grid(fock_twophase_sigma_mixed<M>, t, n, twophase_sigma_smem(a.rows, a.xdim, a.nsq), dev, s);
   return fock_launch_grid(fock_twophase_sigma_df<M>, t, n, twophase_sigma_smem(a.rows, a.xdim, a.nsq), dev, s);

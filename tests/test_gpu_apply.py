@@ -127,9 +127,13 @@ def test_maps_arm_equals_hash_arm(torch, N, M, kind, prec):
     for out in (a, b):
         assert rel(out.cpu().numpy().astype(np.complex128), ref) <= TOL[prec]
     if kind == "ll":
-        # same kernel and same arithmetic order on both arms: bit-identical sums
-        # (the one-body M = 3 case takes the nearest-neighbour kernel on the
-        # hash arm: every pair of three sites neighbours on a ring)
+        # the sparse kernel on both arms: same arithmetic order, bit-identical
+        # sums (left to itself the hash arm takes the pair-weight two-phase
+        # path, and the one-body M = 3 case the nearest-neighbour kernel:
+        # every pair of three sites neighbours on a ring)
+        fock.fock_apply_set_path(H.handle, 1, prec, fock.FOCK_PATH_SPARSE, fock.FOCK_ARM_HASH)
+        a = H.apply(C, precision=prec, arm=fock.FOCK_ARM_HASH)
+        fock.fock_apply_set_path(H.handle, 1, prec, fock.FOCK_PATH_AUTO)
         assert torch.equal(a, b)
 
 
@@ -238,7 +242,8 @@ def test_terms_count_matches_oracle_columns(torch):
     (8, 6, "generic", 1, True),      # two-phase on the tensor cores, sigma copied out by chunks
     (9, 6, "generic", 3, False),     # several right-hand sides, pageable host memory
     (6, 8, "generic", 1, True),      # two-phase with FP32 phase 1
-    (10, 5, "ll", 2, True),          # sparse kernel: one copy after the apply
+    (10, 5, "ll", 2, True),          # pair-weight two-phase: input and sigma copied by chunks
+    (16, 10, "ll", 1, True),
     (9, 6, "bh", 1, True),           # nearest-neighbour kernel, sigma copied out by chunks
     (8, 7, "bh", 3, False),
 ])
@@ -259,6 +264,24 @@ def test_host_buffer_entry_point(torch, N, M, kind, nrhs, pinned, prec):
     for j in range(nrhs):
         ref = oracle.apply_push(N, M, h, W, C[:, j])
         assert rel(out.numpy().reshape(sp.nc, nrhs)[:, j].astype(np.complex128), ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("scale", [1e-30, 1e9])
+def test_host_buffer_outside_the_unscaled_band(torch, scale):
+    # the host-buffer apply splits C chunk by chunk without a scale, which is
+    # exact while the largest magnitude lies in [2^-20, 2^21); outside it the
+    # call applies again from its device copy with the scaled split, so it
+    # still equals the device apply bit for bit
+    N, M = 8, 6
+    h, W = hw("generic", M)
+    sp = fock.Space(N, M)
+    H = fock.Hamiltonian(sp, h, W)
+    C = inputs.random_state(sp.nc, 12) * scale
+    Ch = torch.from_numpy(C).pin_memory()
+    out = torch.empty_like(Ch).pin_memory()
+    fock.fock_apply_H_host(sp.handle, H.handle, Ch, out)
+    assert torch.equal(out, H.apply(Ch.cuda()).cpu())
+    assert rel(out.numpy(), oracle.apply_push(N, M, h, W, C)) <= 1e-12
 
 
 # ---------------------------------------------------------------------------
