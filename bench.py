@@ -587,21 +587,25 @@ def measure_one_by_one(torch, fock, probs, B, Cd, batch_ms):
         objs.append((sp, fock.Hamiltonian(sp, h, W)))
     sig = torch.empty_like(Cd)
     paths = {}
+    # one workspace, the largest any instance prefers, shared by the sequence
+    wsz = max(fock.fock_apply_workspace_size(sp.handle, H.handle, 1, fock.FOCK_PREC_F64) for sp, H in objs)
+    wsb = torch.empty(max(wsz, 16), dtype=torch.uint8, device="cuda")
 
     def run():
         for i, (sp, H) in enumerate(objs):
             b, e = int(B.offsets[i]), int(B.offsets[i + 1])
-            fock.fock_apply_H(sp.handle, H.handle, Cd[b:e], sig[b:e], 1, fock.FOCK_PREC_F64)
-    run()                                        # workspaces and first launches
+            fock.fock_apply_H(sp.handle, H.handle, Cd[b:e], sig[b:e], 1, fock.FOCK_PREC_F64, fock.FOCK_ARM_AUTO, wsb)
+    run()                                        # first launches
     for sp, H in objs:
-        p = fock.PATH_NAMES[fock.fock_apply_path(sp.handle, H.handle)]
+        p = fock.PATH_NAMES[fock.fock_apply_path(sp.handle, H.handle, 1, fock.FOCK_PREC_F64, fock.FOCK_ARM_AUTO,
+                                                 wsb.numel())]
         paths[p] = paths.get(p, 0) + 1
     t = time_steps(torch, run, 3, 1, lambda: None)
     ref = B.apply(Cd)
     err = float(torch.linalg.vector_norm(sig - ref) / torch.linalg.vector_norm(ref))
-    del objs, sig, ref
+    del objs, sig, ref, wsb
     torch.cuda.empty_cache()
-    return {"ms_per_step": t, "batched_ms": batch_ms, "batched_speedup": t / batch_ms, "paths": paths,
+    return {"ms_per_step": t, "batched_ms": batch_ms, "workspace_bytes": wsz, "batched_speedup": t / batch_ms, "paths": paths,
             "rel_diff_vs_batched": err}
 
 
@@ -1021,8 +1025,8 @@ def main():
                 "ms_per_call": t, "rho1_columns": math.comb(w.N - 1 + w.M - 1, w.M - 1),
                 "rho2_columns": math.comb(w.N - 2 + w.M - 1, w.M - 1) if w.N >= 2 else 0,
                 "rho2_gram_entries": P * (P + 1) // 2,
-                "note": "host-synchronous call incl. its workspace allocation and the input split; "
-                        "Gram matrices over the (N-1)- and (N-2)-particle spaces"}
+                "note": "host-synchronous call incl. the input split (the workspace is kept with the space "
+                        "after the first call); Gram matrices over the (N-1)- and (N-2)-particle spaces"}
             del X
         out["cpu_baseline"] = cpu_baseline(w, h, W, Cn if w.nrhs == 1 else Cn[:, 0].copy(), H.terms / w.nc,
                                            args.cpu_seconds, all_cores=bool(args.cpu_all_cores))

@@ -169,8 +169,12 @@ int fock_hamiltonian_is_real(const fock_ham *ham, int *is_real);
 /* sigma = H C  (Eq. Haction)                                                */
 /* ------------------------------------------------------------------------- */
 /* precision */
-#define FOCK_PREC_F64        0  /* complex128 in/out; result within 1e-13 of
-                                   exact (normwise); FP32-pair arithmetic     */
+#define FOCK_PREC_F64        0  /* complex128 in/out; FP32-pair arithmetic
+                                   (48-bit significands); on the tensor-core
+                                   path each entry is within 2^-39.9 B of the
+                                   exact sigma, B = sum_r |A_r| ||R_r||_1
+                                   max|X| (the bound in fock_apply_tc.cuh),
+                                   measured 9e-14 normwise on random states */
 #define FOCK_PREC_F64_NATIVE 1  /* complex128 in/out; native FP64 arithmetic */
 #define FOCK_PREC_F32_MIXED  2  /* complex64 in/out; FP32 products, FP32-pair
                                    accumulation per configuration             */
@@ -377,8 +381,11 @@ int fock_sil_step(const fock_space *sp, const fock_ham *ham, void *C_dev, double
  * vectors a_l C over the (N-1)-particle and a_q a_s C over the (N-2)-particle
  * configurations: FP32-pair products within tiles of 128 configurations, FP64
  * sums across tiles, block partials added in a fixed order (deterministic).
- * rho2 is zero for N < 2.  Allocates and frees its own device workspace
- * (16 B per configuration plus the partial sums).  Synchronous on `stream`.
+ * rho2 is zero for N < 2.  Allocates its device workspace (16 B per
+ * configuration plus the partial sums) on the first call and keeps it with the
+ * space, grown when a call needs more; fock_space_destroy releases it.  Calls
+ * on one space share that workspace and must not overlap.  Synchronous on
+ * `stream`.
  * FOCK_ERR_UNSUPPORTED for M > 12 or N_c >= 2^32 - 1; FOCK_ERR_DEVICE when
  * the current device is not the space's. */
 int fock_density_matrices(const fock_space *sp, const void *C_dev, double *rho1_host, double *rho2_host,
@@ -458,11 +465,15 @@ typedef struct fock_batch fock_batch;
  * W[i] as for fock_hamiltonian_create; W[i] may be NULL) on the current
  * device.  Their coefficient vectors are concatenated in instance order
  * (instance i at offsets[i]..offsets[i+1], see fock_batch_offsets), complex
- * interleaved.  One apply covers every instance in one persistent launch: a
- * block takes work items (a range of configurations of one instance, largest
- * instances first) from an atomic queue and stages that instance's tables in
- * shared memory when the instance changes.  Requires N_c < 2^32 - 1 per
- * instance.  Hermiticity is checked as in fock_hamiltonian_create with tol. */
+ * interleaved.  An instance with at least 2^18 configurations whose default
+ * single-vector FP64-class path is a two-phase one (FOCK_PATH_TWOPHASE_TC,
+ * FOCK_PATH_TWOPHASE, FOCK_PATH_TWOPHASE_BLOCK) gets an apply of its own, one
+ * after another on the stream with one shared workspace.  Every other
+ * instance is served by one persistent launch: a block takes work items (a
+ * range of configurations of one instance, largest instances first) from an
+ * atomic queue and stages that instance's tables in shared memory when the
+ * instance changes.  Requires N_c < 2^32 - 1 per instance.  Hermiticity is
+ * checked as in fock_hamiltonian_create with tol. */
 int fock_batch_create(int32_t count, const int32_t *N, const int32_t *M, const double *const *h_host,
                       const double *const *W_host, double tol, fock_batch **out);
 int fock_batch_destroy(fock_batch *b);
@@ -470,19 +481,26 @@ int fock_batch_destroy(fock_batch *b);
 /* offsets[0..count] of the instances in concatenated vectors (host array). */
 int fock_batch_offsets(const fock_batch *b, int64_t *offsets);
 
+/* own[0..count-1]: 1 where the instance has an apply of its own (see
+ * fock_batch_create), 0 where the persistent launch serves it (host array). */
+int fock_batch_own_apply(const fock_batch *b, int32_t *own);
+
 /* Sum of the instances' configuration terms (see fock_hamiltonian_terms). */
 int fock_batch_terms(const fock_batch *b, int64_t *config_terms);
 
 /* sigma = H_i C_i for every instance i, precision FOCK_PREC_F64 (complex128,
- * FP32-pair arithmetic; one scale for the whole batch, so the instances'
- * vectors should lie within 2^100 of each other in magnitude) or
- * FOCK_PREC_F32_MIXED (complex64).  Buffers as for fock_apply_H, concatenated.
- * Device scratch (queue counter, FP32-pair split copy) is owned by the batch.
- * Asynchronous on `stream`. */
+ * FP32-pair arithmetic; one scale for the instances of the persistent launch,
+ * so their vectors should lie within 2^100 of each other in magnitude; an
+ * instance with its own apply is scaled by itself) or FOCK_PREC_F32_MIXED
+ * (complex64).  Buffers as for fock_apply_H, concatenated.  Device scratch
+ * (queue counter, FP32-pair split copy of the instances of the persistent
+ * launch, the shared workspace of the others) is owned by the batch and
+ * allocated by the first call.  Asynchronous on `stream`. */
 int fock_batch_apply(fock_batch *b, const void *C_dev, void *sigma_dev, int precision, void *stream);
 
-/* Autotuner: times fock_batch_apply on the caller's buffers (contents are
- * overwritten in sigma only) for work items of 1..32 tiles of 128
+/* Autotuner: times the persistent launch of fock_batch_apply on the caller's
+ * buffers (contents are overwritten in sigma only; nothing is timed when every
+ * instance has its own apply) for work items of 1..32 tiles of 128
  * configurations and 1..4 resident blocks per SM, keeps the fastest for this
  * batch and precision, and reports it.  If cache_path is not NULL the choice
  * is read from / appended to that text file, keyed by the instance sizes, the

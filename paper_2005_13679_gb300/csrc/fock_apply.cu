@@ -42,6 +42,9 @@ int fock_launch_twophase_block(const TwoPhaseArgs &, bool, int, cudaStream_t);
 bool fock_block_tables(int M, const std::complex<double> *R, double scale, std::vector<float4> &df,
                        std::vector<float2> &mx);
 size_t fock_block_smem(int M, int xdim, int nsq, bool mixed);
+int fock_launch_twophase_pairs(const TwoPhaseArgs &, bool, int, cudaStream_t);
+bool fock_pairs_tables(int M, const std::complex<double> *R, double scale, double tol, std::vector<float2> &df,
+                       std::vector<float> &mx);
 
 // Segment form of one term (see fock_apply_sparse.cuh): the removal (k, q)
 // (q = -1 for one particle) and the addition (s, l) (s = -1 for one particle)
@@ -123,6 +126,8 @@ static void free_ham(fock_ham *h) {
   cudaFree(h->d_tc_mer);
   cudaFree(h->d_blk_df);
   cudaFree(h->d_blk_32);
+  cudaFree(h->d_ps1_df);
+  cudaFree(h->d_ps1_32);
   for (int i = 0; i < 3; ++i) {
     cudaFree(h->d_nn_bond[i]);
     cudaFree(h->d_nn_e[i]);
@@ -493,6 +498,14 @@ static int hamiltonian_create(const fock_space *sp, const double *h_host, const 
       st = upload(&H->d_blk_df, bdf.data(), bdf.size());
       if (!st) st = upload(&H->d_blk_32, b32.data(), b32.size());
       if (!st) H->pairsum = true;
+      // rank-one blocks (contact interactions): the pair-momentum form
+      std::vector<float2> pdf;
+      std::vector<float> p32;
+      if (!st && fock_pairs_tables(M, R.data(), H->coef_scale, 1e-14, pdf, p32)) {
+        st = upload(&H->d_ps1_df, pdf.data(), pdf.size());
+        if (!st) st = upload(&H->d_ps1_32, p32.data(), p32.size());
+        if (!st) H->ps1 = true;
+      }
     }
   }
   if (!st) st = build_nn(H, h_host, W_host);
@@ -608,6 +621,30 @@ int fock_prepare_df(const void *C, int64_t n, void *ws, int device, cudaStream_t
   return FOCK_OK;
 }
 
+// The same preparation over several ranges of C with one scale: range i,
+// src[i] .. src[i] + len[i], is split into ws + 256 at dst[i] (elements).
+int fock_prepare_df_ranges(const void *C, const int64_t *src, const int64_t *dst, const int64_t *len, int nr,
+                           void *ws, int device, cudaStream_t stream) {
+  int *words = (int *)ws;
+  float4 *split = (float4 *)((char *)ws + kWsHeader);
+  FOCK_CUDA_TRY(cudaMemsetAsync(words, 0, 12, stream));
+  const int sms = fock_get_sm_count(device);
+  for (int pass = 0; pass < 2; ++pass)
+    for (int i = 0; i < nr; ++i) {
+      const int64_t n = len[i];
+      if (n <= 0) continue;
+      int64_t blocks = ((pass ? n : 2 * n) + 255) / 256;
+      if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+      if (pass == 0)
+        fock_max_exponent_kernel<<<(unsigned)blocks, 256, 0, stream>>>((const double *)C + 2 * src[i], 2 * n, words);
+      else
+        fock_split_kernel<<<(unsigned)blocks, 256, 0, stream>>>((const double2 *)C + src[i], n, words, split + dst[i],
+                                                                words + 1);
+    }
+  FOCK_CUDA_TRY(cudaGetLastError());
+  return FOCK_OK;
+}
+
 // One chunk [b, e) of the FP32-pair preparation for the overlapped host-buffer
 // apply: the chunk's largest exponent joins ws word 0 and the chunk is split
 // without a scale (the band of fock_input_shift, checked after the apply).
@@ -651,11 +688,13 @@ static size_t twophase_y_offset(const fock_space *sp, const fock_ham *ham, int n
   return (base + 255) & ~(size_t)255;
 }
 
-static size_t twophase_y_bytes(const fock_space *sp, int nrhs, int precision) {
+static size_t twophase_y_bytes(const fock_space *sp, const fock_ham *ham, int nrhs, int precision) {
   const int64_t nc2 = count_nm(sp->N - 2, sp->M);
   const size_t elem = precision == FOCK_PREC_F32_MIXED ? sizeof(float2) : sizeof(float4);
   const size_t cols = ((size_t)nc2 * (size_t)nrhs + kYBlock - 1) / kYBlock * kYBlock;
-  return (size_t)fock_pair_count(sp->M) * cols * elem;
+  // rows: one per removal pair, or one per pair momentum for the rank-one form
+  const size_t rows = ham->ps1 ? (size_t)(2 * sp->M - 1) : (size_t)fock_pair_count(sp->M);
+  return rows * cols * elem;
 }
 
 // Phase 1 on the tensor cores: FP64-class or FP32-mixed precision, dense
@@ -676,7 +715,7 @@ static bool tc_eligible(const fock_space *sp, const fock_ham *ham, const ApplyAr
 // Workspace that selects the fastest path (the minimum is fock_apply_ws_bytes).
 size_t fock_apply_ws_pref(const fock_space *sp, const fock_ham *ham, int nrhs, int precision) {
   if (!twophase_eligible(sp, ham, precision)) return fock_apply_ws_bytes(sp, ham, nrhs, precision);
-  return twophase_y_offset(sp, ham, nrhs, precision) + twophase_y_bytes(sp, nrhs, precision);
+  return twophase_y_offset(sp, ham, nrhs, precision) + twophase_y_bytes(sp, ham, nrhs, precision);
 }
 
 extern "C" int fock_apply_set_events(fock_ham *ham, void *start_event, void *stop_event) {
@@ -958,7 +997,13 @@ static int launch_main(const fock_space *sp, const fock_ham *ham, const void *Ci
         }
         auto launch = [&]() {
           if (path == FOCK_PATH_TWOPHASE_TC) return fock_launch_twophase_tc(t, mixed, sp->device, stream);
-          if (path == FOCK_PATH_TWOPHASE_BLOCK) return fock_launch_twophase_block(t, mixed, sp->device, stream);
+          if (path == FOCK_PATH_TWOPHASE_BLOCK) {
+            if (ham->ps1) {
+              t.blk = mixed ? (const void *)ham->d_ps1_32 : (const void *)ham->d_ps1_df;
+              return fock_launch_twophase_pairs(t, mixed, sp->device, stream);
+            }
+            return fock_launch_twophase_block(t, mixed, sp->device, stream);
+          }
           return fock_launch_twophase(t, mixed, sp->device, stream);
         };
         if (!ov) return launch();

@@ -64,8 +64,11 @@
 
 constexpr int kTcCols = 128;        // (configuration, rhs) columns per tile = MMA M
 constexpr int kTcProducers = 128;   // producer group: 4 warps, one thread per column
-constexpr int kTcThreads = 416;     // two producer groups (warps 0-3 even tiles, 4-7 odd tiles),
-                                    // warps 8-11 epilogue (warp 8 + q: tile columns 32q .. 32q+31), warp 12 MMA
+constexpr int kTcThreads = 544;     // two producer groups (warps 0-3 even tiles, 4-7 odd tiles),
+                                    // warps 8-15 epilogue (warp 8 + q + 4h: tile columns 32q .. 32q+31,
+                                    // complex rows of half h), warp 16 MMA
+constexpr int kTcEpiWarps = 8;
+constexpr int kTcMmaWarp = 16;
 constexpr int kTcTmemCols = 512;    // two tiles x NT (<= 256) columns, at 0 and 256
 constexpr uint32_t kTcPolls = 1u << 20;
 constexpr int kTcExpCol = 15;       // tensor-memory column of the column exponent
@@ -493,18 +496,20 @@ struct TcPolDF {                                         // FP64-class: exact di
   }
   // Lane-local epilogue in passes of four complex rows: levels 7, 6, 5 of a
   // complex row r sit in columns 6r .. 6r+5 (Re row, then Im row) and levels
-  // 4, 3, 2 in N2 + 6r .. N2 + 6r + 5, read as 8-column loads.  The last pass
-  // runs first, so the column exponent is read with the first loads.
-  __device__ static void drain(const TwoPhaseArgs &t, uint32_t tq, uint32_t colg, bool live, const int *s_er) {
+  // 4, 3, 2 in N2 + 6r .. N2 + 6r + 5, read as 8-column loads.  The two warps
+  // of a lane quarter take alternate passes (half = pass & 1), last pass
+  // first; the column exponent is read with a warp's first loads.
+  __device__ static void drain(const TwoPhaseArgs &t, uint32_t tq, uint32_t colg, bool live, const int *s_er, int half) {
     constexpr int P = sh.P, NPASS = (P + 3) / 4;
     float4 *__restrict__ Y = (float4 *)t.Y;
     const float ecf = tc_ld_x1(tq + (uint32_t)sh.exp_col());
     int ec = 0;
-    bool fast = false;
+    bool fast = false, fast_set = false;
     fp2_t FC = 0ull;
     const float *s_fr = (const float *)(s_er + 2 * P + ((2 * P) & 1));
 #pragma unroll
     for (int pass = NPASS - 1; pass >= 0; --pass) {
+      if ((pass & 1) != half) continue;                  // the two warps of a lane quarter share the passes
       const int nrow = P - 4 * pass < 4 ? P - 4 * pass : 4;
       const int nch = (6 * nrow + 7) / 8;
       float A[24], B[24];
@@ -515,7 +520,8 @@ struct TcPolDF {                                         // FP64-class: exact di
           tc_ld_x8(tq + (uint32_t)(sh.N2 + 24 * pass + 8 * c), *reinterpret_cast<float(*)[8]>(&B[8 * c]));
         }
       tc_wait_ld();
-      if (pass == NPASS - 1) {
+      if (!fast_set) {
+        fast_set = true;
         ec = (int)ecf - 16;
         const int *rng = (const int *)(s_fr + 2 * P);
         // both factors and their product stay normal floats: one product per row
@@ -570,8 +576,9 @@ struct TcPolMixed {                                      // FP32-mixed: fp16 hi/
                  idesc, kk > 0);
   }
   // Y = D 2^(e_rho + e_c - 30): the row scale 2^(15 - e_rho) of the image and
-  // the column scale 2^(15 - e_c) of the digits taken out.
-  __device__ static void drain(const TwoPhaseArgs &t, uint32_t tq, uint32_t colg, bool live, const int *s_er) {
+  // the column scale 2^(15 - e_c) of the digits taken out.  Both warps of a
+  // lane quarter read every column; each writes alternate complex rows.
+  __device__ static void drain(const TwoPhaseArgs &t, uint32_t tq, uint32_t colg, bool live, const int *s_er, int half) {
     constexpr int P = M * (M + 1) / 2;
     float2 *__restrict__ Y = (float2 *)t.Y;
     float d[NT];
@@ -581,6 +588,7 @@ struct TcPolMixed {                                      // FP32-mixed: fp16 hi/
     const int ec = (int)d[R2] - 30;
 #pragma unroll
     for (int r = 0; r < P; ++r) {
+      if ((r & 1) != half) continue;                     // the two warps of a lane quarter take alternate rows
       float v[2];
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
@@ -604,8 +612,10 @@ __host__ __device__ inline TcSmem tc_smem_of(int xdim, int nsq) {
 // memory of a tile):
 //   producers (warps 0-3 for even k, warps 4-7 for odd k)
 //                           wait done[s] of tile k-2, write B[s], arrive full[s]
-//   MMA (warp 12, one lane) wait full[s] and empty[s] of tile k-2, issue, commit done[s]
-//   epilogue (warps 8-11)   wait done[s], drain tensor memory, write Y, arrive empty[s]
+//   MMA (warp 16, one lane) wait full[s] and empty[s] of tile k-2, issue, commit done[s]
+//   epilogue (warps 8-15)   wait done[s], drain tensor memory (warp w reads TMEM lanes
+//                           32 (w % 4) .. +31; warps w and w + 4 take alternate passes
+//                           of four complex rows), write Y, arrive empty[s] (8 arrivals)
 // ---------------------------------------------------------------------------
 template <int M, class Pol>
 __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPhaseArgs t) {
@@ -650,12 +660,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
     for (int i = 0; i < 2; ++i) {
       tc_mbar_init(&full[i], kTcProducers);
       tc_mbar_init(&done[i], 1);
-      tc_mbar_init(&empty[i], 4);
+      tc_mbar_init(&empty[i], kTcEpiWarps);
     }
     *flag = 0;
     tc_fence_mbar_init();
   }
-  if (warp == 12) tc_tmem_alloc(tslot, kTcTmemCols);
+  if (warp == kTcMmaWarp) tc_tmem_alloc(tslot, kTcTmemCols);
   tc_fence_before_sync();
   __syncthreads();
   tc_fence_after_sync();
@@ -684,7 +694,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
       tc_fence_proxy_async();
       tc_arrive(&full[g]);
     }
-  } else if (warp == 12) {
+  } else if (warp == kTcMmaWarp) {
     // ---------------- MMA issue ----------------
     if (lane == 0) {
       const uint32_t r_addr = tc_smem_addr(smem + L.off_r);
@@ -702,8 +712,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
       }
     }
   } else {
-    // ---------------- epilogue: tile columns 32q .. 32q+31, one per lane ----------------
-    const int q = warp - 8;
+    // ---------------- epilogue: tile columns 32q .. 32q+31, one per lane; rows of half h ----------------
+    const int q = (warp - 8) & 3, half = (warp - 8) >> 2;
     const int *s_er = (const int *)(smem + L.off_er);
     for (uint32_t k = 0; k < mytiles; ++k) {
       const int s = k & 1;
@@ -713,7 +723,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
       }
       tc_fence_after_sync();
       const uint32_t colg = (tb + blockIdx.x + k * gridDim.x) * (uint32_t)kTcCols + (uint32_t)(32 * q + lane);
-      Pol::drain(t, tbase + (uint32_t)s * 256u + ((uint32_t)(32 * q) << 16), colg, colg < total, s_er);
+      Pol::drain(t, tbase + (uint32_t)s * 256u + ((uint32_t)(32 * q) << 16), colg, colg < total, s_er, half);
       tc_fence_before_sync();
       __syncwarp();
       if (lane == 0) tc_arrive(&empty[s]);
@@ -721,7 +731,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
   }
 
   __syncthreads();
-  if (warp == 12) {
+  if (warp == kTcMmaWarp) {
     // after an abort, let the MMAs already committed finish before the
     // columns are released
     if (*flag && lane == 0 && issued > 0) {

@@ -13,6 +13,11 @@
 #include "fock_apply_sparse.cuh"
 
 int fock_make_terms(const fock_ham *ham, int maxm, FockTerm *out);
+int fock_apply_internal(const fock_space *sp, const fock_ham *ham, const void *C, void *sigma, int nrhs, int precision,
+                        int arm, void *ws, size_t ws_bytes, cudaStream_t stream);
+size_t fock_apply_ws_pref(const fock_space *sp, const fock_ham *ham, int nrhs, int precision);
+int fock_prepare_df_ranges(const void *C, const int64_t *src, const int64_t *dst, const int64_t *len, int nr,
+                           void *ws, int device, cudaStream_t stream);
 
 namespace {
 
@@ -23,6 +28,7 @@ struct BatchInst {
   int N, M, xdim, rows, nrem, nadd, nsq, real;
   uint32_t nc, pad;
   long long off;                  // offset of the instance in concatenated vectors
+  long long soff;                 // offset of its FP32-pair split copy in the batch workspace
   const uint32_t *mod, *sat;
   const FockRemoval *rem;
   const FockTerm *terms;
@@ -48,6 +54,7 @@ struct BatchArgs {
 };
 
 const int kBatchMaxM = 12;
+const uint32_t kOwnMinNc = 1u << 18;   // smaller instances stay in the shared persistent launch
 
 // One persistent launch over every instance.  A block claims items from the
 // queue; items are ordered largest instance first and are whole tiles of 128
@@ -89,7 +96,7 @@ __global__ void __launch_bounds__(FOCK_APPLY_THREADS, 4) fock_batch_apply_kernel
       v.terms = (const FockTerm *)(smem + b.L.off_terms);
       v.coef = smem + b.L.off_coef;
       v.rem = I.rem;
-      v.C = (const vec_t *)b.C + I.off;
+      v.C = (const vec_t *)b.C + (DF ? I.soff : I.off);
       v.sigma = (out_t *)b.sigma + I.off;
       v.map = nullptr;
       v.slots = nullptr;
@@ -319,9 +326,18 @@ struct fock_batch {
   BatchItem *d_items = nullptr;
   unsigned *d_queue = nullptr;
   int *d_active = nullptr;       // all ones unless a solver masks instances
-  // FP32-pair scratch: status words + split copy of the concatenated input
+  // FP32-pair scratch: status words + split copy of the instances the
+  // persistent launch serves (split_total configurations, ranges pr_*)
   void *ws = nullptr;
   size_t ws_bytes = 0;
+  int64_t split_total = 0;
+  std::vector<int64_t> pr_src, pr_dst, pr_len;
+  // instances large enough for their own two-phase apply (one after another
+  // on the stream, sharing one workspace)
+  std::vector<char> own;
+  int nown = 0;
+  void *own_ws = nullptr;
+  size_t own_ws_bytes = 0, own_ws_need = 0;
   int max_nadd = 0, max_rows = 1, max_xdim = 0, max_nsq = 0;
 };
 
@@ -332,6 +348,7 @@ static int build_items(fock_batch *b, int tiles) {
   std::vector<BatchItem> items;
   const uint32_t span = (uint32_t)tiles * FOCK_APPLY_THREADS;
   for (int i : order) {
+    if (b->own[i]) continue;
     const uint32_t nc = b->h_inst[i].nc;
     for (uint32_t g0 = 0; g0 < nc; g0 += span) {
       BatchItem it;
@@ -343,6 +360,9 @@ static int build_items(fock_batch *b, int tiles) {
   }
   cudaFree(b->d_items);
   b->d_items = nullptr;
+  b->nitems = 0;
+  b->tiles_per_item = tiles;
+  if (items.empty()) return FOCK_OK;
   FOCK_CUDA_TRY(cudaMalloc(&b->d_items, sizeof(BatchItem) * items.size()));
   FOCK_CUDA_TRY(cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
   b->nitems = (int)items.size();
@@ -360,6 +380,7 @@ extern "C" int fock_batch_destroy(fock_batch *b) {
   cudaFree(b->d_queue);
   cudaFree(b->d_active);
   cudaFree(b->ws);
+  cudaFree(b->own_ws);
   delete b;
   return FOCK_OK;
 }
@@ -395,20 +416,39 @@ extern "C" int fock_batch_create(int32_t count, const int32_t *N, const int32_t 
     }
     if (st) break;
     b->off[i + 1] = b->off[i] + s->nc;
+    // its own apply when the instance is large and its default path is a two-phase one
+    int32_t path = FOCK_PATH_LIST;
+    const size_t pref = fock_apply_ws_pref(s, h, 1, FOCK_PREC_F64);
+    const bool own = s->nc >= kOwnMinNc && fock_apply_path(s, h, 1, FOCK_PREC_F64, FOCK_ARM_HASH, pref, &path) == FOCK_OK &&
+                     (path == FOCK_PATH_TWOPHASE_TC || path == FOCK_PATH_TWOPHASE || path == FOCK_PATH_TWOPHASE_BLOCK);
+    b->own.push_back(own ? 1 : 0);
+    if (own) {
+      b->nown++;
+      b->own_ws_need = std::max(b->own_ws_need, std::max(pref, fock_apply_ws_pref(s, h, 1, FOCK_PREC_F32_MIXED)));
+    }
     b->terms += h->config_terms;
     b->real = b->real && h->real;
     BatchInst I;
     memset(&I, 0, sizeof(I));
     I.N = s->N; I.M = s->M; I.xdim = s->tab.xdim; I.rows = s->tab.rows; I.nrem = h->nrem; I.nadd = h->nadd;
     I.nsq = s->N + 4; I.real = h->real; I.nc = (uint32_t)s->nc; I.off = b->off[i];
+    I.soff = b->split_total;
+    if (!own) {
+      b->pr_src.push_back(b->off[i]);
+      b->pr_dst.push_back(b->split_total);
+      b->pr_len.push_back(s->nc);
+      b->split_total += s->nc;
+    }
     I.mod = s->tab.mod32; I.sat = s->tab.sat32; I.rem = h->d_rem; I.terms = dt;
     I.coef_df = h->d_coefdf; I.sq_df = h->d_sqrtdf; I.coef32 = h->d_coef32; I.sq32 = h->d_sqrt32;
     I.coef_scale = h->coef_scale;
     b->h_inst.push_back(I);
-    b->max_nadd = std::max(b->max_nadd, h->nadd);
-    b->max_rows = std::max(b->max_rows, s->tab.rows);
-    b->max_xdim = std::max(b->max_xdim, s->tab.xdim);
-    b->max_nsq = std::max(b->max_nsq, s->N + 4);
+    if (!own) {
+      b->max_nadd = std::max(b->max_nadd, h->nadd);
+      b->max_rows = std::max(b->max_rows, s->tab.rows);
+      b->max_xdim = std::max(b->max_xdim, s->tab.xdim);
+      b->max_nsq = std::max(b->max_nsq, s->N + 4);
+    }
   }
   if (!st) {
     b->total = b->off[count];
@@ -434,6 +474,12 @@ extern "C" int fock_batch_create(int32_t count, const int32_t *N, const int32_t 
 extern "C" int fock_batch_offsets(const fock_batch *b, int64_t *offsets) {
   if (!b || !offsets) return FOCK_ERR_ARG;
   for (int i = 0; i <= b->count; ++i) offsets[i] = b->off[i];
+  return FOCK_OK;
+}
+
+extern "C" int fock_batch_own_apply(const fock_batch *b, int32_t *own) {
+  if (!b || !own) return FOCK_ERR_ARG;
+  for (int i = 0; i < b->count; ++i) own[i] = b->own[i];
   return FOCK_OK;
 }
 
@@ -476,12 +522,15 @@ static int launch_batch(fock_batch *b, const void *C, void *sigma, const int *in
   return e == cudaSuccess ? FOCK_OK : fock_cuda_status(e);
 }
 
-static int batch_apply_internal(fock_batch *b, const void *C, void *sigma, int precision, const int *active,
-                                cudaStream_t s) {
+// The persistent launch over the instances without an apply of their own.
+static int batch_apply_shared(fock_batch *b, const void *C, void *sigma, int precision, const int *active,
+                              cudaStream_t s) {
+  if (b->nitems == 0) return FOCK_OK;
   if (precision == FOCK_PREC_F64) {
-    const size_t need = 256 + (size_t)b->total * sizeof(float4);
+    const size_t need = 256 + (size_t)b->split_total * sizeof(float4);
     if (b->ws_bytes < need) return FOCK_ERR_NOMEM;
-    int st = fock_prepare_df(C, b->total, b->ws, b->device, s);
+    int st = fock_prepare_df_ranges(C, b->pr_src.data(), b->pr_dst.data(), b->pr_len.data(), (int)b->pr_src.size(),
+                                    b->ws, b->device, s);
     if (st) return st;
     const void *Cin = (const char *)b->ws + 256;
     const int *in_exp = (const int *)b->ws + 1;
@@ -494,14 +543,39 @@ static int batch_apply_internal(fock_batch *b, const void *C, void *sigma, int p
   return FOCK_ERR_UNSUPPORTED;
 }
 
+// Every instance: the shared launch, then the instances with an apply of
+// their own (skipped where host_active is given and 0).
+static int batch_apply_internal(fock_batch *b, const void *C, void *sigma, int precision, const int *active,
+                                cudaStream_t s, const int *host_active = nullptr) {
+  int st = batch_apply_shared(b, C, sigma, precision, active, s);
+  if (st || b->nown == 0) return st;
+  if (b->own_ws_bytes < b->own_ws_need) return FOCK_ERR_NOMEM;
+  const size_t elem = precision == FOCK_PREC_F64 ? 16 : 8;
+  for (int i = 0; i < b->count && !st; ++i) {
+    if (!b->own[i] || (host_active && !host_active[i])) continue;
+    st = fock_apply_internal(b->sp[i], b->ham[i], (const char *)C + (size_t)b->off[i] * elem,
+                             (char *)sigma + (size_t)b->off[i] * elem, 1, precision, FOCK_ARM_HASH, b->own_ws,
+                             b->own_ws_bytes, s);
+  }
+  return st;
+}
+
 static int ensure_ws(fock_batch *b) {
-  const size_t need = 256 + (size_t)b->total * sizeof(float4);
-  if (b->ws_bytes >= need) return FOCK_OK;
-  cudaFree(b->ws);
-  b->ws = nullptr;
-  b->ws_bytes = 0;
-  FOCK_CUDA_TRY(cudaMalloc(&b->ws, need));
-  b->ws_bytes = need;
+  const size_t need = 256 + (size_t)b->split_total * sizeof(float4);
+  if (b->ws_bytes < need) {
+    cudaFree(b->ws);
+    b->ws = nullptr;
+    b->ws_bytes = 0;
+    FOCK_CUDA_TRY(cudaMalloc(&b->ws, need));
+    b->ws_bytes = need;
+  }
+  if (b->own_ws_bytes < b->own_ws_need) {
+    cudaFree(b->own_ws);
+    b->own_ws = nullptr;
+    b->own_ws_bytes = 0;
+    FOCK_CUDA_TRY(cudaMalloc(&b->own_ws, b->own_ws_need));
+    b->own_ws_bytes = b->own_ws_need;
+  }
   return FOCK_OK;
 }
 
@@ -520,10 +594,8 @@ extern "C" int fock_batch_apply(fock_batch *b, const void *C_dev, void *sigma_de
   const size_t bytes = (size_t)b->total * (precision == FOCK_PREC_F64 ? 16 : 8);
   const char *c0 = (const char *)C_dev, *s0 = (const char *)sigma_dev;
   if (c0 < s0 + bytes && s0 < c0 + bytes) return FOCK_ERR_ALIAS;
-  if (precision == FOCK_PREC_F64) {
-    st = ensure_ws(b);
-    if (st) return st;
-  }
+  st = ensure_ws(b);
+  if (st) return st;
   return batch_apply_internal(b, C_dev, sigma_dev, precision, nullptr, (cudaStream_t)stream);
 }
 
@@ -575,9 +647,12 @@ extern "C" int fock_batch_autotune(fock_batch *b, const void *C_dev, void *sigma
       }
     }
   }
-  if (precision == FOCK_PREC_F64) {
-    st = ensure_ws(b);
-    if (st) return st;
+  st = ensure_ws(b);
+  if (st) return st;
+  if (b->nown == b->count) {             // no instance in the shared launch: nothing to tune
+    if (tiles_per_item) *tiles_per_item = b->tiles_per_item;
+    if (blocks_per_sm) *blocks_per_sm = b->blocks_per_sm;
+    return FOCK_OK;
   }
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
@@ -592,10 +667,10 @@ extern "C" int fock_batch_autotune(fock_batch *b, const void *C_dev, void *sigma
     if (st) break;
     for (int bp : blocks_c) {
       b->blocks_per_sm = bp;
-      st = batch_apply_internal(b, C_dev, sigma_dev, precision, nullptr, s);  // warm-up
+      st = batch_apply_shared(b, C_dev, sigma_dev, precision, nullptr, s);  // warm-up
       if (st) break;
       FOCK_CUDA_TRY(cudaEventRecord(e0, s));
-      for (int r = 0; r < 3 && !st; ++r) st = batch_apply_internal(b, C_dev, sigma_dev, precision, nullptr, s);
+      for (int r = 0; r < 3 && !st; ++r) st = batch_apply_shared(b, C_dev, sigma_dev, precision, nullptr, s);
       FOCK_CUDA_TRY(cudaEventRecord(e1, s));
       FOCK_CUDA_TRY(cudaEventSynchronize(e1));
       if (st) break;
@@ -644,6 +719,7 @@ struct BLanczos {
   int *cbeg = nullptr;
   int ldh;
   int grid;
+  const int *hact = nullptr;     // host activity of the instances (their own applies are skipped at 0)
 
   int dots(const double2 *Vb, int k, const double2 *w, double2 *out) {
     for (int i0 = 0; i0 < k; i0 += kVec) {
@@ -667,7 +743,7 @@ struct BLanczos {
   // one Lanczos step j (apply, two Gram-Schmidt passes, alpha, beta, next vector)
   int step(int j) {
     double2 *vj = V + (size_t)j * n;
-    int st = batch_apply_internal(b, vj, W, FOCK_PREC_F64, b->d_active, s);
+    int st = batch_apply_internal(b, vj, W, FOCK_PREC_F64, b->d_active, s, hact);
     if (st) return st;
     if ((st = dots(V, j + 1, W, H1))) return st;
     if ((st = combine(V, j + 1, H1, true, W))) return st;
@@ -779,6 +855,8 @@ extern "C" int fock_batch_lanczos_ground(fock_batch *b, int32_t max_iter, int32_
 
   // host state per instance
   std::vector<int> active(count, 1), iters(count, 0), pcur(count, 0);
+  std::vector<int> cap_active(count, 1);   // activity the graphs were captured with
+  L.hact = active.data();
   std::vector<std::vector<double>> theta(count), coup(count);   // kept Ritz values and couplings
   std::vector<double> ha((size_t)m * count), hb((size_t)m * count);
   std::vector<double2> Yh((size_t)count * L.ldh);
@@ -787,6 +865,15 @@ extern "C" int fock_batch_lanczos_ground(fock_batch *b, int32_t max_iter, int32_
   while (true) {
     // one restart cycle: steps p..m-1 as one graph
     const int gi = p == 0 ? 0 : 1;
+    // an instance with its own apply that stopped: capture again without it
+    bool recapture = false;
+    for (int i = 0; i < count; ++i) recapture = recapture || (b->own[i] && active[i] != cap_active[i]);
+    if (recapture) {
+      for (auto &g : graphs)
+        if (g) cudaGraphExecDestroy(g);
+      graphs[0] = graphs[1] = nullptr;
+      cap_active = active;
+    }
     if (!graphs[gi]) {
       cudaGraph_t g;
       BCUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));

@@ -70,6 +70,9 @@ struct fock_space {
   int32_t *d_j1;         // single-jump map or NULL
   int32_t *d_j2;         // double-jump map or NULL
   size_t j1_bytes, j2_bytes;
+  // workspace of fock_density_matrices, kept between calls (grown on demand)
+  void *dm_ws, *dm_part;
+  size_t dm_ws_bytes, dm_part_bytes;
 };
 
 // One removal (one or two annihilated orbitals) and its slice of additions.
@@ -124,6 +127,11 @@ struct fock_ham {
   bool pairsum;
   float4 *d_blk_df;         // block tables, (re_hi, im_hi, re_lo, im_lo) of coef / coef_scale
   float2 *d_blk_32;         // block tables, complex float, unscaled
+  // ... whose blocks are rank one off the diagonal (contact interactions;
+  // fock_twophase_pairs.cu): c_K, 2 c_K and D_r as pairs (scaled) and floats
+  bool ps1;
+  float2 *d_ps1_df;
+  float *d_ps1_32;
   // nearest-neighbour operators (h on sites and bonds k, k + 1 mod M, W only
   // on-site): per-bond and per-site coefficients, indexed by the precision
   bool nn;

@@ -8,12 +8,15 @@
 // sqrt(n'_q + 1) sqrt(n'_s + 1 + delta_qs) C[n' + e_q + e_s] over the
 // (N-2)-particle configurations (a_q a_s = a_s a_q, so one vector per unordered
 // pair).  Both are Hermitian Gram matrices of small vectors over a large
-// space: one thread builds the vector of one configuration in a shared tile,
-// the block accumulates the upper triangle over the tile's 128 columns in
-// FP32 pairs, the per-tile sums are added in FP64, and the per-block partials
-// are summed in a fixed order (deterministic).  This replaces the paper's
-// element-by-element sums over beta with a reduction that reads each C
-// gather once per configuration of the smaller space.
+// space: one thread builds the vector of one configuration in a shared tile
+// of 128 columns; the upper triangle is cut into 3 x 3 blocks of entries, and
+// a thread takes one block over one of G interleaved column groups of the
+// tile (9 complex products per 6 shared-memory reads), accumulating in FP32
+// pairs.  Each thread adds its tile sums in FP64 to its own shared slots;
+// the groups, then the per-block partials, are summed in a fixed order
+// (deterministic).  This replaces the paper's element-by-element sums over
+// beta with a reduction that reads each C gather once per configuration of
+// the smaller space.
 #include <math.h>
 
 #include <vector>
@@ -28,6 +31,11 @@ template <int M, bool TWO>
 struct GramShape {
   static constexpr int K = TWO ? M * (M + 1) / 2 : M;     // vectors per configuration
   static constexpr int E = K * (K + 1) / 2;               // upper-triangle entries
+  static constexpr int NB = (K + 2) / 3;                  // 3 x 3 blocks of entries per row
+  static constexpr int KP = 3 * NB;                       // tile row length (zero padded)
+  static constexpr int W = NB * (NB + 1) / 2;             // upper-triangle blocks
+  static constexpr int G = kGramCols / W >= 8 ? 8 : (kGramCols / W >= 4 ? 4 : (kGramCols / W >= 2 ? 2 : 1));
+  static constexpr int NI = W * G;                        // work items (block, column group)
 };
 
 struct GramArgs {
@@ -60,37 +68,29 @@ __device__ __forceinline__ void gram_mac(fp2_t &h, fp2_t &l, float4 a, float4 b)
 
 template <int M, bool TWO>
 __global__ void __launch_bounds__(kGramCols) fock_gram_kernel(const GramArgs g) {
-  constexpr int K = GramShape<M, TWO>::K, E = GramShape<M, TWO>::E;
+  using Sh = GramShape<M, TWO>;
+  constexpr int K = Sh::K, E = Sh::E, KP = Sh::KP, NI = Sh::NI, G = Sh::G;
   extern __shared__ __align__(16) unsigned char smem[];
   const int rows = M > 1 ? M - 1 : 1;
-  float4 *Xt = (float4 *)smem;                                        // [kGramCols][K]
-  double2 *acc = (double2 *)(Xt + kGramCols * K);                     // [E]
-  uint32_t *s_mod = (uint32_t *)(acc + E);
+  float4 *Xt = (float4 *)smem;                                        // [kGramCols][KP]
+  double2 *acc = (double2 *)(Xt + kGramCols * KP);                    // [NI][9]
+  uint32_t *s_mod = (uint32_t *)(acc + 9 * NI);
   uint32_t *s_sat = s_mod + rows * g.xdim;
   float2 *s_sq = (float2 *)(s_sat + rows * g.xdim + 2);
-  uint8_t *emap = (uint8_t *)(s_sq + g.nsq);                          // [E][2]
   const int tid = threadIdx.x;
   for (int i = tid; i < rows * g.xdim; i += kGramCols) {
     s_mod[i] = g.mod[i];
     s_sat[i] = g.sat[i];
   }
   for (int i = tid; i < g.nsq; i += kGramCols) s_sq[i] = gram_sqrt_pair(i);
-  for (int e = tid; e < E; e += kGramCols) {
-    int a = 0, r = e;                                                 // row-major upper triangle
-    while (r >= K - a) {
-      r -= K - a;
-      ++a;
-    }
-    emap[2 * e] = (uint8_t)a;
-    emap[2 * e + 1] = (uint8_t)(a + r);
-    acc[e] = make_double2(0.0, 0.0);
-  }
+  for (int i = tid; i < 9 * NI; i += kGramCols) acc[i] = make_double2(0.0, 0.0);
   __syncthreads();
 
   for (uint32_t tile = blockIdx.x * (uint32_t)kGramCols; tile < g.ncol; tile += gridDim.x * (uint32_t)kGramCols) {
     // ---- this thread's column vector into the tile ----
     const uint32_t col = tile + tid;
-    float4 *xrow = Xt + tid * K;
+    float4 *xrow = Xt + tid * KP;
+    for (int a = K; a < KP; ++a) xrow[a] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (col < g.ncol) {
       int S[M];
       if (TWO) {
@@ -146,20 +146,56 @@ __global__ void __launch_bounds__(kGramCols) fock_gram_kernel(const GramArgs g) 
       for (int a = 0; a < K; ++a) xrow[a] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-    // ---- Gram entries of the tile ----
-    for (int e = tid; e < E; e += kGramCols) {
-      const int a = emap[2 * e], b = emap[2 * e + 1];
-      fp2_t h = 0ull, l = 0ull;
-#pragma unroll 4
-      for (int c = 0; c < kGramCols; ++c) gram_mac(h, l, Xt[c * K + a], Xt[c * K + b]);
-      double2 s = acc[e];
-      s.x += (double)fp2_x(h) + (double)fp2_x(l);
-      s.y += (double)fp2_y(h) + (double)fp2_y(l);
-      acc[e] = s;
+    // ---- Gram entries of the tile: item = (block w, column group q) ----
+    for (int it = tid; it < NI; it += kGramCols) {
+      const int w = it / G, q = it - (it / G) * G;
+      int bi = 0, r = w;                                              // row-major upper triangle of blocks
+      while (r >= Sh::NB - bi) {
+        r -= Sh::NB - bi;
+        ++bi;
+      }
+      const int a0 = 3 * bi, b0 = 3 * (bi + r);
+      fp2_t h[9], l[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) h[i] = l[i] = 0ull;
+#pragma unroll 2
+      for (int c = q; c < kGramCols; c += G) {                      // interleaved columns: groups on distinct banks
+        const float4 *x = Xt + c * KP;
+        const float4 A0 = x[a0], A1 = x[a0 + 1], A2 = x[a0 + 2];
+        const float4 B0 = x[b0], B1 = x[b0 + 1], B2 = x[b0 + 2];
+        gram_mac(h[0], l[0], A0, B0); gram_mac(h[1], l[1], A0, B1); gram_mac(h[2], l[2], A0, B2);
+        gram_mac(h[3], l[3], A1, B0); gram_mac(h[4], l[4], A1, B1); gram_mac(h[5], l[5], A1, B2);
+        gram_mac(h[6], l[6], A2, B0); gram_mac(h[7], l[7], A2, B1); gram_mac(h[8], l[8], A2, B2);
+      }
+      double2 *dst = acc + 9 * it;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        double2 s = dst[i];
+        s.x += (double)fp2_x(h[i]) + (double)fp2_x(l[i]);
+        s.y += (double)fp2_y(h[i]) + (double)fp2_y(l[i]);
+        dst[i] = s;
+      }
     }
     __syncthreads();
   }
-  for (int e = tid; e < E; e += kGramCols) g.partial[(size_t)blockIdx.x * E + e] = acc[e];
+  // upper-triangle entries: the sum over column groups, in group order
+  for (int e = tid; e < E; e += kGramCols) {
+    int a = 0, r = e;
+    while (r >= K - a) {
+      r -= K - a;
+      ++a;
+    }
+    const int b = a + r, bi = a / 3, bj = b / 3;
+    const int w = bi * Sh::NB - (bi * (bi - 1)) / 2 + (bj - bi);
+    const int slot = 3 * (a - 3 * bi) + (b - 3 * bj);
+    double2 s = make_double2(0.0, 0.0);
+    for (int q = 0; q < G; ++q) {
+      const double2 v = acc[9 * (w * G + q) + slot];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    g.partial[(size_t)blockIdx.x * E + e] = s;
+  }
 }
 
 // out[e] = sum over blocks of partial[b][e], in block order.
@@ -177,14 +213,25 @@ __global__ void fock_gram_reduce(const double2 *__restrict__ partial, int blocks
 
 template <int M, bool TWO>
 size_t gram_smem(int xdim, int nsq) {
-  constexpr int K = GramShape<M, TWO>::K, E = GramShape<M, TWO>::E;
+  using Sh = GramShape<M, TWO>;
   const int rows = M > 1 ? M - 1 : 1;
-  return (size_t)kGramCols * K * 16 + (size_t)E * 16 + 8 * (size_t)rows * xdim + 8 + 8 * (size_t)nsq + 2 * (size_t)E;
+  return (size_t)kGramCols * Sh::KP * 16 + (size_t)9 * Sh::NI * 16 + 8 * (size_t)rows * xdim + 8 + 8 * (size_t)nsq;
 }
 
 // Runs one Gram reduction; G receives the upper triangle (E entries).
+// Device buffer of at least `bytes`, kept in *buf between calls (grown when needed).
+static int grow(void **buf, size_t *cap, size_t bytes) {
+  if (*cap >= bytes) return FOCK_OK;
+  cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  FOCK_CUDA_TRY(cudaMalloc(buf, bytes));
+  *cap = bytes;
+  return FOCK_OK;
+}
+
 template <int M, bool TWO>
-int gram_run(const GramArgs &g0, int device, cudaStream_t s, std::vector<double> &G) {
+int gram_run(const GramArgs &g0, int device, cudaStream_t s, std::vector<double> &G, fock_space *sp) {
   constexpr int E = GramShape<M, TWO>::E;
   GramArgs g = g0;
   const size_t smem = gram_smem<M, TWO>(g.xdim, g.nsq);
@@ -197,8 +244,9 @@ int gram_run(const GramArgs &g0, int device, cudaStream_t s, std::vector<double>
   int64_t grid = (int64_t)per_sm * fock_get_sm_count(device);
   if (grid > tiles) grid = tiles;
   if (grid < 1) grid = 1;
-  double2 *buf = nullptr;
-  FOCK_CUDA_TRY(cudaMalloc(&buf, sizeof(double2) * (size_t)E * (grid + 1)));
+  const int gst = grow(&sp->dm_part, &sp->dm_part_bytes, sizeof(double2) * (size_t)E * (grid + 1));
+  if (gst) return gst;
+  double2 *buf = (double2 *)sp->dm_part;
   g.partial = buf;
   kern<<<(unsigned)grid, kGramCols, smem, s>>>(g);
   cudaError_t e = cudaGetLastError();
@@ -209,15 +257,14 @@ int gram_run(const GramArgs &g0, int device, cudaStream_t s, std::vector<double>
   G.assign(2 * (size_t)E, 0.0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(G.data(), buf + (size_t)E * grid, sizeof(double2) * E, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(buf);
   return e == cudaSuccess ? FOCK_OK : fock_cuda_status(e);
 }
 
 template <bool TWO>
-int gram_dispatch(int M, const GramArgs &g, int device, cudaStream_t s, std::vector<double> &G) {
+int gram_dispatch(int M, const GramArgs &g, int device, cudaStream_t s, std::vector<double> &G, fock_space *sp) {
   switch (M) {
 #define FOCK_GRAM_CASE(MM) \
-    case MM: return gram_run<MM, TWO>(g, device, s, G);
+    case MM: return gram_run<MM, TWO>(g, device, s, G, sp);
     FOCK_GRAM_CASE(1)
     FOCK_GRAM_CASE(2)
     FOCK_GRAM_CASE(3)
@@ -258,9 +305,11 @@ extern "C" int fock_density_matrices(const fock_space *sp, const void *C_dev, do
   const int N = sp->N, M = sp->M;
   cudaStream_t s = (cudaStream_t)stream;
   // FP32-pair split of C, scaled by a power of two (the apply's preparation)
-  void *ws = nullptr;
-  FOCK_CUDA_TRY(cudaMalloc(&ws, 256 + 16 * (size_t)sp->nc));
-  int st = fock_prepare_df(C_dev, sp->nc, ws, sp->device, s);
+  fock_space *spw = (fock_space *)sp;                    // the space keeps the workspace between calls
+  int st = grow(&spw->dm_ws, &spw->dm_ws_bytes, 256 + 16 * (size_t)sp->nc);
+  if (st) return st;
+  void *ws = spw->dm_ws;
+  st = fock_prepare_df(C_dev, sp->nc, ws, sp->device, s);
   int words[2] = {0, 0};
   if (!st) {
     cudaError_t e = cudaMemcpyAsync(words, ws, sizeof(words), cudaMemcpyDeviceToHost, s);
@@ -285,7 +334,7 @@ extern "C" int fock_density_matrices(const fock_space *sp, const void *C_dev, do
   if (!st && rho1_host) {
     g.ncol = (uint32_t)nc_of(N - 1, M);
     std::vector<double> G;
-    st = gram_dispatch<false>(M, g, sp->device, s, G);
+    st = gram_dispatch<false>(M, g, sp->device, s, G, (fock_space *)sp);
     if (!st) {
       int e = 0;
       for (int a = 0; a < M; ++a)
@@ -305,7 +354,7 @@ extern "C" int fock_density_matrices(const fock_space *sp, const void *C_dev, do
     } else {
       g.ncol = (uint32_t)nc_of(N - 2, M);
       std::vector<double> G;
-      st = gram_dispatch<true>(M, g, sp->device, s, G);
+      st = gram_dispatch<true>(M, g, sp->device, s, G, (fock_space *)sp);
       if (!st) {
         const int P = M * (M + 1) / 2;
         std::vector<double> full(2 * (size_t)P * P);
@@ -329,6 +378,5 @@ extern "C" int fock_density_matrices(const fock_space *sp, const void *C_dev, do
       }
     }
   }
-  cudaFree(ws);
   return st;
 }

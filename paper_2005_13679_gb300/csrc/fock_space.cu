@@ -162,6 +162,8 @@ extern "C" int fock_jump_maps_free(fock_space *sp) {
 extern "C" int fock_space_destroy(fock_space *sp) {
   if (!sp) return FOCK_OK;
   fock_jump_maps_free(sp);
+  cudaFree(sp->dm_ws);
+  cudaFree(sp->dm_part);
   free_tables(sp->tab);
   cudaFree(sp->d_flag);
   free(sp);

@@ -66,7 +66,7 @@ EXPORTS = (
     "fock_lanczos_ground", "fock_sil_step", "fock_density_matrices",
     "fock_sector_create", "fock_sector_destroy", "fock_sector_size", "fock_sector_rank", "fock_sector_unrank",
     "fock_sector_terms", "fock_sector_workspace_size", "fock_sector_apply_H", "fock_sector_lanczos_ground",
-    "fock_batch_create", "fock_batch_destroy", "fock_batch_offsets", "fock_batch_terms", "fock_batch_apply",
+    "fock_batch_create", "fock_batch_destroy", "fock_batch_offsets", "fock_batch_own_apply", "fock_batch_terms", "fock_batch_apply",
     "fock_batch_autotune", "fock_batch_lanczos_ground",
 )
 
@@ -148,6 +148,7 @@ def load(path: str | None = None):
         "fock_batch_destroy": [vp],
         "fock_batch_offsets": [vp, vp],
         "fock_batch_terms": [vp, P(i64)],
+        "fock_batch_own_apply": [vp, vp],
         "fock_batch_apply": [vp, vp, vp, ctypes.c_int, vp],
         "fock_batch_autotune": [vp, vp, vp, ctypes.c_int, ctypes.c_char_p, P(i32), P(i32), vp],
         "fock_batch_lanczos_ground": [vp, i32, i32, dbl, ctypes.c_uint64, vp, vp, vp, vp],
@@ -601,6 +602,9 @@ class Batch:
         t = ctypes.c_int64()
         _check(load().fock_batch_terms(self.handle, ctypes.byref(t)), "fock_batch_terms")
         self.terms = t.value
+        own = np.zeros(self.count, dtype=np.int32)
+        _check(load().fock_batch_own_apply(self.handle, own.ctypes.data_as(ctypes.c_void_p)), "fock_batch_own_apply")
+        self.own = own.astype(bool)     # instances with an apply of their own
 
     def apply(self, C, sigma=None, precision=FOCK_PREC_F64, stream=None):
         import torch

@@ -214,6 +214,10 @@ WORKLOADS = {
     # Profiling size of the Lieb-Liniger M = 10 workload: 20,160,075
     # configurations (complex128 C of 323 MB, larger than L2).
     "ll_n22_m10": Workload("ll_n22_m10", N=22, M=10, kind="ll", g=0.5, seed=3),
+    # Profiling size of the Lieb-Liniger M = 10 two-phase kernels: 10,015,005
+    # configurations (complex128 C of 160 MB, larger than L2) and an
+    # (N-2)-space intermediate of 55 x 4,686,825 FP32-pair rows (4.1 GB).
+    "ll_n20_m10": Workload("ll_n20_m10", N=20, M=10, kind="ll", g=0.5, seed=3),
     # Lieb-Liniger ring N = 30, M = 10, g = 0.5 restricted to total momentum 0
     # (orbital weights sum_i i n_i = 150): 2,462,733 of the 211,915,132 configurations.
     "ll_n30_m10_p0": Workload("ll_n30_m10_p0", N=30, M=10, kind="ll", g=0.5, seed=3, lanczos_seed=103,

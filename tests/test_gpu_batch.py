@@ -1,7 +1,7 @@
-"""Uneven batches (one persistent launch over many problems) through the C ABI:
-the batched apply against the oracle and against single-problem applies, the
-autotuner, and the batched Lanczos against dense diagonalisation and the
-single-problem solver."""
+"""Uneven batches (one persistent launch over the small problems, an apply of
+its own for each large one) through the C ABI: the batched apply against the
+oracle and against single-problem applies, the autotuner, and the batched
+Lanczos against dense diagonalisation and the single-problem solver."""
 import numpy as np
 import pytest
 
@@ -56,6 +56,40 @@ def test_batch_apply_matches_oracle_and_single(torch, prec):
     assert B.terms == sum(fock.Hamiltonian(fock.Space(N, M), h, W).terms for N, M, h, W in probs)
 
 
+@pytest.mark.parametrize("prec", [fock.FOCK_PREC_F64, fock.FOCK_PREC_F32_MIXED])
+def test_batch_own_and_shared_instances(torch, prec):
+    """Instances of 2^18 configurations or more whose default path is a
+    two-phase one are applied by that path (a generic M = 6 problem on the
+    tensor-core phase 1, a Lieb-Liniger ring on the pair-weight form), the
+    rest by the persistent launch; both against the oracle on sampled rows
+    (every row of the small instances) and against the single-problem apply."""
+    probs = small_problems()[:3]
+    h, W = inputs.random_hermitian_hw(6, 21)
+    probs.append((30, 6, h, W))                               # 324632 configurations
+    probs.append((30, 7) + inputs.lieb_liniger_hw(7, 1.3))   # 1947792 configurations
+    B = fock.Batch(probs)
+    assert list(B.own) == [False, False, False, True, True]
+    C = np.concatenate([inputs.random_state(oracle.nc(N, M), 200 + i) for i, (N, M, _, _) in enumerate(probs)])
+    C[B.offsets[3]:B.offsets[4]] *= 1e5                       # scaled on its own
+    dt = torch.complex128 if prec == fock.FOCK_PREC_F64 else torch.complex64
+    Cd = torch.from_numpy(C).to(dt).cuda()
+    out = B.apply(Cd, precision=prec).cpu().numpy().astype(np.complex128)
+    tol = 1e-12 if prec == fock.FOCK_PREC_F64 else 5e-6
+    rng = np.random.default_rng(3)
+    for i, (N, M, h, W) in enumerate(probs):
+        a, b = B.offsets[i], B.offsets[i + 1]
+        if b - a <= 20000:
+            rows = np.arange(b - a)
+        else:
+            rows = np.unique(np.concatenate([rng.integers(0, b - a, 800), np.arange(100), np.arange(b - a - 100, b - a)]))
+        ref = oracle.apply_rows(N, M, h, W, C[a:b], rows)
+        assert rel(out[a:b][rows], ref) <= tol, i
+        sp = fock.Space(N, M)
+        H = fock.Hamiltonian(sp, h, W)
+        one = H.apply(Cd[a:b].contiguous(), precision=prec).cpu().numpy().astype(np.complex128)
+        assert rel(out[a:b], one) <= tol, i
+
+
 def test_batch_autotune_keeps_results(torch, tmp_path):
     probs = small_problems()
     B = fock.Batch(probs)
@@ -83,12 +117,14 @@ def test_batch_lanczos_against_dense(torch):
 
 
 def test_batch_lanczos_uneven_ll(torch):
-    """Uneven Lieb-Liniger instances (cap 10^6 configurations): every energy
-    matches the single-problem solver to 1e-10 and lies between the Bethe-ansatz
-    energy and the zero-momentum condensate energy."""
+    """Uneven Lieb-Liniger instances (cap 10^6 configurations; all but one
+    with an apply of their own, stopping at different cycles): every energy
+    matches the single-problem solver to 1e-10 and lies between the
+    Bethe-ansatz energy and the zero-momentum condensate energy."""
     inst = inputs.uneven_ll_batch(count=12, seed=5, cap=10 ** 6)
     probs = [(x.N, x.M) + inputs.lieb_liniger_hw(x.M, x.g) for x in inst]
     B = fock.Batch(probs)
+    assert B.own.sum() == len(inst) - 1      # the 286-configuration instance stays in the shared launch
     E, R, it, st = B.lanczos_ground(max_iter=400, restart_len=12, tol=1e-10, seed=9)
     assert st == fock.FOCK_OK
     for i, x in enumerate(inst):

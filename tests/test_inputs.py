@@ -52,7 +52,7 @@ def test_nearest_neighbour_structure():
 def test_named_workload_sizes():
     sizes = {"ll_n5_m5": 126, "generic_n100_m6": 96560646, "ll_n30_m10": 211915132,
              "generic_n60_m6": 8259888, "bh_n20_m12": 84672315, "bh_n16_m12": 13037895,
-             "generic_n20_m8_rhs16": 888030}
+             "generic_n20_m8_rhs16": 888030, "ll_n20_m10": 10015005}
     for name, n in sizes.items():
         w = inputs.WORKLOADS[name]
         assert w.nc == n == math.comb(w.N + w.M - 1, w.M - 1), name
