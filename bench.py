@@ -308,6 +308,11 @@ def run_reference(args, w):
 FLOPS_PER_TERM = {("f64", "direct"): 70, ("f64", "twophase"): 42, ("f32_mixed", "direct"): 10,
                   ("f32_mixed", "twophase"): 8, ("f64_native", "direct"): 10}
 FLOPS_PER_TERM_REAL = {("f64", "direct"): 35, ("f32_mixed", "direct"): 6, ("f64_native", "direct"): 6}
+# phase 1 of the pair-momentum form per (addition, (N-2)-configuration): the
+# amplitude sqrt(n_s + 1) sqrt(n_l + 1 + d_sl) as an FP32-pair product (6), the
+# factor o (2), the product with C (8) and the TwoSum accumulation (16); mixed:
+# the amplitude (2) and one packed FMA (4)
+PAIRS_FLOPS = {"f64": 32, "f32_mixed": 6}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
 
 
@@ -579,8 +584,8 @@ def inputs_random_state(n, seed):
 
 def measure_one_by_one(torch, fock, probs, B, Cd, batch_ms):
     """The same FP64-class applies one instance at a time (each its own space,
-    operator and the library's path for it, workspaces allocated beforehand),
-    beside the one persistent launch over all instances."""
+    operator and the library's path for it, one workspace allocated
+    beforehand), beside the batched apply."""
     objs = []
     for (N, M, h, W) in probs:
         sp = fock.Space(N, M)
@@ -609,12 +614,24 @@ def measure_one_by_one(torch, fock, probs, B, Cd, batch_ms):
             "rel_diff_vs_batched": err}
 
 
+def batch_launches(B, prec):
+    """Kernels of one batched apply: per instance with its own apply, the
+    FP32-pair preparation (2, FP64-class) and the two phases; for the shared
+    launch, the preparation of each of its instances (2 each, FP64-class) and
+    the persistent kernel."""
+    own = int(B.own.sum())
+    shared = B.count - own
+    prep = 2 if prec == 0 else 0
+    return own * (prep + 2) + ((prep * shared + 1) if shared else 0)
+
+
 def run_batch(args):
     """64 uneven Lieb-Liniger instances (N in [10, 200], M in 4..12, log g uniform,
     capped at 10^7 configurations each): one step is one batched FP64-class
-    apply of every instance in one persistent launch with autotuned work items.
-    Also reports the FP32-mixed batched apply and the time to solve every ground
-    state with the graph-captured batched Lanczos."""
+    apply of every instance (its own two-phase apply for each instance of at
+    least 2^18 configurations, one persistent launch with autotuned work items
+    for the rest).  Also reports the FP32-mixed batched apply and the time to
+    solve every ground state with the graph-captured batched Lanczos."""
     import tempfile
 
     import numpy as np
@@ -652,8 +669,9 @@ def run_batch(args):
         "config": {"workload": "ll_batch64", "instances": B.count * ws, "instances_per_rank": B.count,
                    "total_nc_rank0": B.total,
                    "tiles_per_item": tiles, "blocks_per_sm": blocks, "l2": "inputs larger than L2 (no flush)"},
-        "gpu_launches": 3 * args.steps, "clocks": clocks,
+        "gpu_launches": batch_launches(B, fock.FOCK_PREC_F64) * args.steps, "clocks": clocks,
     }
+    out["config"]["own_apply_instances"] = int(B.own.sum())
     if args.extras:
         out["one_by_one"] = measure_one_by_one(torch, fock, probs, B, Cd, ms_all)
         C32 = Cd.to(torch.complex64)
@@ -953,6 +971,19 @@ def main():
                          "algorithmic_bytes": 2 * nbytes, "path": path,
                          "peak_note": f"HBM: measured copy bandwidth ({peak_src}); FP32 pipe: 152 SMs x 128 "
                                       "lanes x 2 flop x 2070 MHz"})
+    elif path == "twophase_block" and (H.forms & fock.FOCK_FORM_PAIR_MOMENTUM) and args.precision in PAIRS_FLOPS:
+        # phase 1 of the pair-momentum form: one amplitude-times-C product per
+        # (addition pair, (N-2)-configuration), no coefficient products
+        P = w.M * (w.M + 1) // 2
+        executed = math.comb(w.N - 2 + w.M - 1, w.M - 1) * P * w.nrhs
+        flops_term = PAIRS_FLOPS[args.precision]
+        achieved = executed * flops_term / (kernel_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                    "kernel": "phase 1 (pair-momentum amplitudes Z_K)", "kernel_ms": kernel_ms,
+                    "executed_terms": executed, "flops_per_term": flops_term, "path": path,
+                    "form": "pair_momentum",
+                    "pipe": "FP32 (fma.rn.f32x2 and scalar); peak = 152 SMs x 128 lanes x 2 flop x 2070 MHz"}
     else:
         key = (args.precision, "twophase" if path.startswith("twophase") else "direct")
         flops_term = FLOPS_PER_TERM_REAL[key] if (H.real and key in FLOPS_PER_TERM_REAL) else FLOPS_PER_TERM[key]
@@ -1020,13 +1051,21 @@ def main():
             for _ in range(reps):
                 fock.fock_density_matrices(sp.handle, X, w.M)
             t = (time.perf_counter() - t0) / reps * 1e3
+            fock.fock_density_matrices(sp.handle, X, w.M, want_rho2=False)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                fock.fock_density_matrices(sp.handle, X, w.M, want_rho2=False)
+            t1 = (time.perf_counter() - t0) / reps * 1e3
             P = w.M * (w.M + 1) // 2
             out["density_matrices"] = {
-                "ms_per_call": t, "rho1_columns": math.comb(w.N - 1 + w.M - 1, w.M - 1),
+                "ms_per_call": t, "rho1_only_ms_per_call": t1,
+                "rho1_columns": math.comb(w.N - 1 + w.M - 1, w.M - 1),
                 "rho2_columns": math.comb(w.N - 2 + w.M - 1, w.M - 1) if w.N >= 2 else 0,
                 "rho2_gram_entries": P * (P + 1) // 2,
-                "note": "host-synchronous call incl. the input split (the workspace is kept with the space "
-                        "after the first call); Gram matrices over the (N-1)- and (N-2)-particle spaces"}
+                "note": "host-synchronous calls incl. the input split (the workspace is kept with the space "
+                        "after the first call); rho2 is a Gram matrix over the (N-2)-particle space and rho1 "
+                        "its partial trace; alone, rho1 is a Gram matrix over the (N-1)-particle space"}
             del X
         out["cpu_baseline"] = cpu_baseline(w, h, W, Cn if w.nrhs == 1 else Cn[:, 0].copy(), H.terms / w.nc,
                                            args.cpu_seconds, all_cores=bool(args.cpu_all_cores))

@@ -165,6 +165,19 @@ int fock_hamiltonian_terms(const fock_ham *ham, int64_t *config_terms);
 /* Nonzero 1 if every coefficient is real (imaginary parts all zero). */
 int fock_hamiltonian_is_real(const fock_ham *ham, int *is_real);
 
+/* Structure found in the operator when it was created, as FOCK_FORM_* bits:
+ * DENSE every reduced two-body coefficient present; PAIR_WEIGHT reduced
+ * coefficients only between pairs of equal orbital sum (k + q = s + l);
+ * PAIR_MOMENTUM additionally rank one off the diagonal inside every pair-sum
+ * block with real entries (contact interactions, Sec. 6): the two-phase
+ * pair-weight path then runs through the 2M - 1 pair-momentum amplitudes;
+ * NEAREST_NEIGHBOUR the Bose-Hubbard class served by FOCK_PATH_NN. */
+#define FOCK_FORM_DENSE 1
+#define FOCK_FORM_PAIR_WEIGHT 2
+#define FOCK_FORM_PAIR_MOMENTUM 4
+#define FOCK_FORM_NEAREST_NEIGHBOUR 8
+int fock_hamiltonian_forms(const fock_ham *ham, int32_t *forms);
+
 /* ------------------------------------------------------------------------- */
 /* sigma = H C  (Eq. Haction)                                                */
 /* ------------------------------------------------------------------------- */
@@ -377,10 +390,13 @@ int fock_sil_step(const fock_space *sp, const fock_ham *ham, void *C_dev, double
  *     rho2_host[2 (((k M + l) M + q) M + s) + {0,1}] = <C| a^dag_k a^dag_l a_q a_s |C>,
  * complex128 interleaved, host memory of M^2 and M^4 complex values; either
  * may be NULL (not both).  C_dev holds N_c complex128 values on the space's
- * device (not required to be normalised).  Computed as Gram matrices of the
- * vectors a_l C over the (N-1)-particle and a_q a_s C over the (N-2)-particle
- * configurations: FP32-pair products within tiles of 128 configurations, FP64
- * sums across tiles, block partials added in a fixed order (deterministic).
+ * device (not required to be normalised).  rho2 is the Gram matrix of the
+ * vectors a_q a_s C over the (N-2)-particle configurations; when both are
+ * asked for (N >= 2), rho1 is its partial trace (sum_x rho2[k][x][x][l] =
+ * (N - 1) rho1[k][l]); asked for alone, rho1 is the Gram matrix of the
+ * vectors a_l C over the (N-1)-particle configurations.  Each warp reduces
+ * tiles of 32 configurations: FP32-pair products within a tile, FP64 sums
+ * across tiles, the warps' sums added in a fixed order (deterministic).
  * rho2 is zero for N < 2.  Allocates its device workspace (16 B per
  * configuration plus the partial sums) on the first call and keeps it with the
  * space, grown when a call needs more; fock_space_destroy releases it.  Calls

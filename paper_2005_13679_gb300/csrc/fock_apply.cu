@@ -552,6 +552,13 @@ extern "C" int fock_hamiltonian_is_real(const fock_ham *ham, int *is_real) {
   return FOCK_OK;
 }
 
+extern "C" int fock_hamiltonian_forms(const fock_ham *ham, int32_t *forms) {
+  if (!ham || !forms) return FOCK_ERR_ARG;
+  *forms = (ham->dense ? FOCK_FORM_DENSE : 0) | (ham->pairsum ? FOCK_FORM_PAIR_WEIGHT : 0) |
+           (ham->ps1 ? FOCK_FORM_PAIR_MOMENTUM : 0) | (ham->nn ? FOCK_FORM_NEAREST_NEIGHBOUR : 0);
+  return FOCK_OK;
+}
+
 // ---------------------------------------------------------------------------
 // FP32-pair input preparation: exponent of max |C| (one atomicMax of the FP64
 // exponent field), then every entry scaled by 2^-(e) and split into hi + lo.

@@ -64,11 +64,11 @@
 
 constexpr int kTcCols = 128;        // (configuration, rhs) columns per tile = MMA M
 constexpr int kTcProducers = 128;   // producer group: 4 warps, one thread per column
-constexpr int kTcThreads = 544;     // two producer groups (warps 0-3 even tiles, 4-7 odd tiles),
+constexpr int kTcThreads = 512;     // two producer groups (warps 0-3 even tiles, 4-7 odd tiles),
                                     // warps 8-15 epilogue (warp 8 + q + 4h: tile columns 32q .. 32q+31,
-                                    // complex rows of half h), warp 16 MMA
+                                    // alternate passes of rows by h); lane 0 of warp 8 also issues the MMAs
 constexpr int kTcEpiWarps = 8;
-constexpr int kTcMmaWarp = 16;
+constexpr int kTcMmaWarp = 8;
 constexpr int kTcTmemCols = 512;    // two tiles x NT (<= 256) columns, at 0 and 256
 constexpr uint32_t kTcPolls = 1u << 20;
 constexpr int kTcExpCol = 15;       // tensor-memory column of the column exponent
@@ -152,6 +152,15 @@ __device__ __forceinline__ void tc_scale(float &h, float &l, int e) {
     h = __fmul_rn(__fmul_rn(h, f1), f2);
     l = __fmul_rn(__fmul_rn(l, f1), f2);
   }
+}
+
+// The row (hi, lo) packed pair scaled by 2^e0 (Re) and 2^e1 (Im), any
+// exponents: the rare path of the epilogue, kept out of line.
+__device__ __noinline__ float4 tc_scale_row(fp2_t hi, fp2_t lo, int e0, int e1) {
+  float h0 = fp2_x(hi), h1 = fp2_y(hi), l0 = fp2_x(lo), l1 = fp2_y(lo);
+  tc_scale(h0, l0, e0);
+  tc_scale(h1, l1, e1);
+  return make_float4(h0, h1, l0, l1);
 }
 
 constexpr float kTcMagic = 12582912.f;   // 1.5 * 2^23
@@ -504,24 +513,24 @@ struct TcPolDF {                                         // FP64-class: exact di
     float4 *__restrict__ Y = (float4 *)t.Y;
     const float ecf = tc_ld_x1(tq + (uint32_t)sh.exp_col());
     int ec = 0;
-    bool fast = false, fast_set = false;
+    bool fast = false, first = true;
     fp2_t FC = 0ull;
     const float *s_fr = (const float *)(s_er + 2 * P + ((2 * P) & 1));
-#pragma unroll
-    for (int pass = NPASS - 1; pass >= 0; --pass) {
-      if ((pass & 1) != half) continue;                  // the two warps of a lane quarter share the passes
+    // this warp's passes: p0, p0 - 2, ... (p0 the last pass of its parity)
+    const int p0 = (NPASS - 1) - (((NPASS - 1) & 1) ^ half);
+#pragma unroll 1
+    for (int pass = p0; pass >= 0; pass -= 2) {
       const int nrow = P - 4 * pass < 4 ? P - 4 * pass : 4;
-      const int nch = (6 * nrow + 7) / 8;
       float A[24], B[24];
 #pragma unroll
       for (int c = 0; c < 3; ++c)
-        if (c < nch) {
+        if (6 * nrow > 8 * c) {
           tc_ld_x8(tq + (uint32_t)(24 * pass + 8 * c), *reinterpret_cast<float(*)[8]>(&A[8 * c]));
           tc_ld_x8(tq + (uint32_t)(sh.N2 + 24 * pass + 8 * c), *reinterpret_cast<float(*)[8]>(&B[8 * c]));
         }
       tc_wait_ld();
-      if (!fast_set) {
-        fast_set = true;
+      if (first) {
+        first = false;
         ec = (int)ecf - 16;
         const int *rng = (const int *)(s_fr + 2 * P);
         // both factors and their product stay normal floats: one product per row
@@ -544,11 +553,7 @@ struct TcPolDF {                                         // FP64-class: exact di
             lo = fp2_mul(lo, sc);
             y = make_float4(fp2_x(hi), fp2_y(hi), fp2_x(lo), fp2_y(lo));
           } else {
-            const int e0 = s_er[2 * r] + ec, e1 = s_er[2 * r + 1] + ec;
-            float h0 = fp2_x(hi), h1 = fp2_y(hi), l0 = fp2_x(lo), l1 = fp2_y(lo);
-            tc_scale(h0, l0, e0);
-            tc_scale(h1, l1, e1);
-            y = make_float4(h0, h1, l0, l1);
+            y = tc_scale_row(hi, lo, s_er[2 * r] + ec, s_er[2 * r + 1] + ec);
           }
           if (live) Y[twophase_yidx(r, colg, P)] = y;
         }
@@ -612,7 +617,8 @@ __host__ __device__ inline TcSmem tc_smem_of(int xdim, int nsq) {
 // memory of a tile):
 //   producers (warps 0-3 for even k, warps 4-7 for odd k)
 //                           wait done[s] of tile k-2, write B[s], arrive full[s]
-//   MMA (warp 16, one lane) wait full[s] and empty[s] of tile k-2, issue, commit done[s]
+//   MMA (warp 8, lane 0)    after draining tile k: wait full[s] of tile k+2 and empty[s] of
+//                           tile k, issue, commit done[s] (tiles 0 and 1 before the loop)
 //   epilogue (warps 8-15)   wait done[s], drain tensor memory (warp w reads TMEM lanes
 //                           32 (w % 4) .. +31; warps w and w + 4 take alternate passes
 //                           of four complex rows), write Y, arrive empty[s] (8 arrivals)
@@ -694,27 +700,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
       tc_fence_proxy_async();
       tc_arrive(&full[g]);
     }
-  } else if (warp == kTcMmaWarp) {
-    // ---------------- MMA issue ----------------
-    if (lane == 0) {
-      const uint32_t r_addr = tc_smem_addr(smem + L.off_r);
-      for (uint32_t k = 0; k < mytiles; ++k) {
-        const int s = k & 1;
-        if (!tc_wait(&full[s], (k >> 1) & 1u, flag, t.polls) ||
-            (k >= 2 && !tc_wait(&empty[s], ((k - 2) >> 1) & 1u, flag, t.polls))) {
-          tc_abort(flag, t.status);
-          break;
-        }
-        tc_fence_after_sync();
-        Pol::issue(tbase + (uint32_t)s * 256u, tc_smem_addr(smem + (s ? L.off_b1 : L.off_b0)), r_addr);
-        tc_commit(&done[s]);
-        issued = k + 1;
-      }
-    }
   } else {
-    // ---------------- epilogue: tile columns 32q .. 32q+31, one per lane; rows of half h ----------------
+    // ---------------- epilogue (tile columns 32q .. 32q+31, one per lane; rows of half h) ----------------
+    // ---------------- and, on lane 0 of warp 8, the MMA issue ----------------
     const int q = (warp - 8) & 3, half = (warp - 8) >> 2;
+    const bool issuer = warp == kTcMmaWarp;
     const int *s_er = (const int *)(smem + L.off_er);
+    const uint32_t r_addr = tc_smem_addr(smem + L.off_r);
+    bool ok = true;
+    // tile k into tensor-memory slot k & 1: its digits written (full) and
+    // tile k - 2 drained from the slot by all epilogue warps (empty)
+    auto issue = [&](uint32_t k) -> bool {
+      const int s = k & 1;
+      if (!tc_wait(&full[s], (k >> 1) & 1u, flag, t.polls) ||
+          (k >= 2 && !tc_wait(&empty[s], ((k - 2) >> 1) & 1u, flag, t.polls))) {
+        tc_abort(flag, t.status);
+        return false;
+      }
+      tc_fence_after_sync();
+      Pol::issue(tbase + (uint32_t)s * 256u, tc_smem_addr(smem + (s ? L.off_b1 : L.off_b0)), r_addr);
+      tc_commit(&done[s]);
+      issued = k + 1;
+      return true;
+    };
+    if (issuer && lane == 0)
+      for (uint32_t k = 0; k < 2 && k < mytiles && ok; ++k) ok = issue(k);
+    __syncwarp();
     for (uint32_t k = 0; k < mytiles; ++k) {
       const int s = k & 1;
       if (!tc_wait(&done[s], (k >> 1) & 1u, flag, t.polls)) {
@@ -727,6 +738,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) fock_twophase_x_tc(const TwoPha
       tc_fence_before_sync();
       __syncwarp();
       if (lane == 0) tc_arrive(&empty[s]);
+      if (issuer) {
+        if (lane == 0 && ok && k + 2 < mytiles) ok = issue(k + 2);
+        __syncwarp();
+      }
     }
   }
 

@@ -25,17 +25,23 @@
 
 namespace {
 
-constexpr int kGramCols = 128;
+constexpr int kGramWarp = 32;   // columns of a warp's tile (one per lane)
 
+// Shapes of one Gram reduction: K vectors per column, E upper-triangle
+// entries, in BS x BS blocks of entries (W blocks in the upper triangle).
 template <int M, bool TWO>
 struct GramShape {
   static constexpr int K = TWO ? M * (M + 1) / 2 : M;     // vectors per configuration
   static constexpr int E = K * (K + 1) / 2;               // upper-triangle entries
-  static constexpr int NB = (K + 2) / 3;                  // 3 x 3 blocks of entries per row
-  static constexpr int KP = 3 * NB;                       // tile row length (zero padded)
+  static constexpr int W3 = ((K + 2) / 3) * ((K + 2) / 3 + 1) / 2, W2 = ((K + 1) / 2) * ((K + 1) / 2 + 1) / 2;
+  static constexpr int BS = W3 >= 28 ? 3 : (W2 >= 28 ? 2 : 1);  // entry block edge: most reuse with >= 28 lanes busy
+  static constexpr int NB = (K + BS - 1) / BS;
+  static constexpr int KP = BS * NB;                      // tile row length (zero padded)
   static constexpr int W = NB * (NB + 1) / 2;             // upper-triangle blocks
-  static constexpr int G = kGramCols / W >= 8 ? 8 : (kGramCols / W >= 4 ? 4 : (kGramCols / W >= 2 ? 2 : 1));
-  static constexpr int NI = W * G;                        // work items (block, column group)
+  static constexpr int TILE = kGramWarp * KP * 16;        // bytes of a warp's column tile
+  static constexpr int SLOTS = W * BS * BS;              // entry slots (blocks x BS^2)
+  static constexpr int ACC = SLOTS * 16;                  // bytes of a warp's FP32-pair sums
+  static constexpr int WARP_BYTES = TILE + ACC;
 };
 
 struct GramArgs {
@@ -43,8 +49,11 @@ struct GramArgs {
   uint32_t nc, ncol;                // N-space size; columns (configurations of the smaller space)
   const uint32_t *mod, *sat;        // binomial tables of the N-space (wrapping and saturated)
   const float4 *C;                  // FP32-pair split of C (re_hi, im_hi, re_lo, im_lo), scaled
-  double2 *partial;                 // [gridDim.x][E]
+  double2 *slots;                   // [warps][SLOTS] FP64 sums
+  double2 *partial;                 // [warps][E]
 };
+
+constexpr int kGramFlush = 16;      // tiles between the FP32-pair and FP64 sums
 
 // sqrt(i) as an FP32 pair: the correctly rounded root and the residual
 // (i - hi^2, exact by FMA) divided by 2 hi.
@@ -66,30 +75,67 @@ __device__ __forceinline__ void gram_mac(fp2_t &h, fp2_t &l, float4 a, float4 b)
   fp2_dacc(h, l, p, e);
 }
 
+// Block (bi, bj), bi <= bj, of the row-major upper triangle of an NB x NB grid.
+__device__ __forceinline__ void gram_block(int it, int nb, int &bi, int &bj) {
+  int r = it, i = 0;
+  while (r >= nb - i) {
+    r -= nb - i;
+    ++i;
+  }
+  bi = i;
+  bj = i + r;
+}
+
+// Every warp works alone (no block barrier in the loop): it builds the
+// vectors of 32 consecutive columns in its own shared tile, one lane per
+// column, then each lane takes blocks of BS x BS entries over the 32 columns
+// (FP32 pairs, BS^2 independent sums) and adds them by TwoSum to the warp's
+// shared FP32-pair sums, which go into the warp's FP64 sums in global memory
+// every kGramFlush tiles (the FP64 pipe runs at 1/64 of the FP32 rate).  The
+// warps' sums go to `partial` in entry order.
 template <int M, bool TWO>
-__global__ void __launch_bounds__(kGramCols) fock_gram_kernel(const GramArgs g) {
+__global__ void __launch_bounds__(256) fock_gram_kernel(const GramArgs g) {
   using Sh = GramShape<M, TWO>;
-  constexpr int K = Sh::K, E = Sh::E, KP = Sh::KP, NI = Sh::NI, G = Sh::G;
+  constexpr int K = Sh::K, E = Sh::E, KP = Sh::KP, W = Sh::W, BS = Sh::BS;
   extern __shared__ __align__(16) unsigned char smem[];
   const int rows = M > 1 ? M - 1 : 1;
-  float4 *Xt = (float4 *)smem;                                        // [kGramCols][KP]
-  double2 *acc = (double2 *)(Xt + kGramCols * KP);                    // [NI][9]
-  uint32_t *s_mod = (uint32_t *)(acc + 9 * NI);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwb = blockDim.x >> 5;
+  uint32_t *s_mod = (uint32_t *)smem;
   uint32_t *s_sat = s_mod + rows * g.xdim;
   float2 *s_sq = (float2 *)(s_sat + rows * g.xdim + 2);
-  const int tid = threadIdx.x;
-  for (int i = tid; i < rows * g.xdim; i += kGramCols) {
+  const size_t tab = ((size_t)(8 * rows * g.xdim + 8 + 8 * g.nsq) + 15) & ~(size_t)15;
+  unsigned char *mine = smem + tab + (size_t)warp * Sh::WARP_BYTES;
+  float4 *Xt = (float4 *)mine;                                        // [32][KP]
+  float4 *acc = (float4 *)(mine + Sh::TILE);                          // [SLOTS] (re_h, im_h, re_l, im_l)
+  for (int i = tid; i < rows * g.xdim; i += blockDim.x) {
     s_mod[i] = g.mod[i];
     s_sat[i] = g.sat[i];
   }
-  for (int i = tid; i < g.nsq; i += kGramCols) s_sq[i] = gram_sqrt_pair(i);
-  for (int i = tid; i < 9 * NI; i += kGramCols) acc[i] = make_double2(0.0, 0.0);
+  for (int i = tid; i < g.nsq; i += blockDim.x) s_sq[i] = gram_sqrt_pair(i);
+  const uint32_t gw = blockIdx.x * (uint32_t)nwb + warp, nw = gridDim.x * (uint32_t)nwb;
+  double2 *gacc = g.slots + (size_t)gw * Sh::SLOTS;
+  for (int i = lane; i < Sh::SLOTS; i += 32) {
+    acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    gacc[i] = make_double2(0.0, 0.0);
+  }
   __syncthreads();
+  // FP32-pair sums into the FP64 sums
+  auto flush = [&]() {
+    for (int i = lane; i < Sh::SLOTS; i += 32) {
+      const float4 v = acc[i];
+      double2 d = gacc[i];
+      d.x += (double)v.x + (double)v.z;
+      d.y += (double)v.y + (double)v.w;
+      gacc[i] = d;
+      acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
 
-  for (uint32_t tile = blockIdx.x * (uint32_t)kGramCols; tile < g.ncol; tile += gridDim.x * (uint32_t)kGramCols) {
-    // ---- this thread's column vector into the tile ----
-    const uint32_t col = tile + tid;
-    float4 *xrow = Xt + tid * KP;
+  int ntile = 0;
+  for (uint32_t tile = gw; tile * kGramWarp < g.ncol; tile += nw) {
+    // ---- this lane's column vector into the warp's tile ----
+    const uint32_t col = tile * kGramWarp + lane;
+    float4 *xrow = Xt + lane * KP;
     for (int a = K; a < KP; ++a) xrow[a] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (col < g.ncol) {
       int S[M];
@@ -104,16 +150,21 @@ __global__ void __launch_bounds__(kGramCols) fock_gram_kernel(const GramArgs g) 
           sq1[m] = s_sq[occ + 1];
           sq2[m] = s_sq[occ + 2];
         }
+        float4 v[TWO ? K : 1];
         int a = 0;
 #pragma unroll
         for (int s = 0; s < M; ++s)
 #pragma unroll
+          for (int l = s; l < M; ++l, ++a) v[a] = __ldg(g.C + (base - U[s] - V[l]));
+        a = 0;
+#pragma unroll
+        for (int s = 0; s < M; ++s)
+#pragma unroll
           for (int l = s; l < M; ++l, ++a) {
-            const float4 v = __ldg(g.C + (base - U[s] - V[l]));
             const float2 amp = df_mul(sq1[s], s == l ? sq2[s] : sq1[l]);
             fp2_t Xh, Xl;
-            fp2_dprod(fp2_make(v.x, v.y), fp2_make(v.z, v.w), fp2_make(amp.x, amp.x), fp2_make(amp.y, amp.y),
-                      Xh, Xl);
+            fp2_dprod(fp2_make(v[a].x, v[a].y), fp2_make(v[a].z, v[a].w), fp2_make(amp.x, amp.x),
+                      fp2_make(amp.y, amp.y), Xh, Xl);
             xrow[a] = make_float4(fp2_x(Xh), fp2_y(Xh), fp2_x(Xl), fp2_y(Xl));
           }
       } else {
@@ -145,60 +196,61 @@ __global__ void __launch_bounds__(kGramCols) fock_gram_kernel(const GramArgs g) 
     } else {
       for (int a = 0; a < K; ++a) xrow[a] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    __syncthreads();
-    // ---- Gram entries of the tile: item = (block w, column group q) ----
-    for (int it = tid; it < NI; it += kGramCols) {
-      const int w = it / G, q = it - (it / G) * G;
-      int bi = 0, r = w;                                              // row-major upper triangle of blocks
-      while (r >= Sh::NB - bi) {
-        r -= Sh::NB - bi;
-        ++bi;
-      }
-      const int a0 = 3 * bi, b0 = 3 * (bi + r);
-      fp2_t h[9], l[9];
+    __syncwarp();
+    // ---- BS x BS entry blocks over the tile's 32 columns ----
+    for (int it = lane; it < W; it += 32) {
+      int bi, bj;
+      gram_block(it, Sh::NB, bi, bj);
+      const int a0 = BS * bi, b0 = BS * bj;
+      fp2_t h[BS * BS], l[BS * BS];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) h[i] = l[i] = 0ull;
+      for (int i = 0; i < BS * BS; ++i) h[i] = l[i] = 0ull;
 #pragma unroll 2
-      for (int c = q; c < kGramCols; c += G) {                      // interleaved columns: groups on distinct banks
+      for (int c = 0; c < kGramWarp; ++c) {
         const float4 *x = Xt + c * KP;
-        const float4 A0 = x[a0], A1 = x[a0 + 1], A2 = x[a0 + 2];
-        const float4 B0 = x[b0], B1 = x[b0 + 1], B2 = x[b0 + 2];
-        gram_mac(h[0], l[0], A0, B0); gram_mac(h[1], l[1], A0, B1); gram_mac(h[2], l[2], A0, B2);
-        gram_mac(h[3], l[3], A1, B0); gram_mac(h[4], l[4], A1, B1); gram_mac(h[5], l[5], A1, B2);
-        gram_mac(h[6], l[6], A2, B0); gram_mac(h[7], l[7], A2, B1); gram_mac(h[8], l[8], A2, B2);
-      }
-      double2 *dst = acc + 9 * it;
+        float4 A[BS], B[BS];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        double2 s = dst[i];
-        s.x += (double)fp2_x(h[i]) + (double)fp2_x(l[i]);
-        s.y += (double)fp2_y(h[i]) + (double)fp2_y(l[i]);
-        dst[i] = s;
+        for (int i = 0; i < BS; ++i) {
+          A[i] = x[a0 + i];
+          B[i] = x[b0 + i];
+        }
+#pragma unroll
+        for (int i = 0; i < BS; ++i)
+#pragma unroll
+          for (int j = 0; j < BS; ++j) gram_mac(h[BS * i + j], l[BS * i + j], A[i], B[j]);
+      }
+      float4 *dst = acc + BS * BS * it;
+#pragma unroll
+      for (int i = 0; i < BS * BS; ++i) {
+        const float4 v = dst[i];
+        fp2_t H = fp2_make(v.x, v.y), L = fp2_make(v.z, v.w);
+        fp2_dacc(H, L, h[i], l[i]);
+        dst[i] = make_float4(fp2_x(H), fp2_y(H), fp2_x(L), fp2_y(L));
       }
     }
-    __syncthreads();
+    __syncwarp();
+    if (++ntile == kGramFlush) {
+      flush();
+      ntile = 0;
+      __syncwarp();
+    }
   }
-  // upper-triangle entries: the sum over column groups, in group order
-  for (int e = tid; e < E; e += kGramCols) {
+  flush();
+  __syncwarp();
+  // this warp's upper-triangle entries
+  for (int e = lane; e < E; e += 32) {
     int a = 0, r = e;
     while (r >= K - a) {
       r -= K - a;
       ++a;
     }
-    const int b = a + r, bi = a / 3, bj = b / 3;
-    const int w = bi * Sh::NB - (bi * (bi - 1)) / 2 + (bj - bi);
-    const int slot = 3 * (a - 3 * bi) + (b - 3 * bj);
-    double2 s = make_double2(0.0, 0.0);
-    for (int q = 0; q < G; ++q) {
-      const double2 v = acc[9 * (w * G + q) + slot];
-      s.x += v.x;
-      s.y += v.y;
-    }
-    g.partial[(size_t)blockIdx.x * E + e] = s;
+    const int b = a + r, bi = a / BS, bj = b / BS;
+    const int it = bi * Sh::NB - (bi * (bi - 1)) / 2 + (bj - bi);
+    g.partial[(size_t)gw * E + e] = gacc[BS * BS * it + BS * (a - BS * bi) + (b - BS * bj)];
   }
 }
 
-// out[e] = sum over blocks of partial[b][e], in block order.
+// out[e] = sum over warps of partial[w][e], in warp order.
 __global__ void fock_gram_reduce(const double2 *__restrict__ partial, int blocks, int E, double2 *__restrict__ out) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
@@ -211,11 +263,14 @@ __global__ void fock_gram_reduce(const double2 *__restrict__ partial, int blocks
   out[e] = s;
 }
 
+// Shared memory of a block of `warps` warps: the tables, then one tile and
+// FP64 sums per warp.
 template <int M, bool TWO>
-size_t gram_smem(int xdim, int nsq) {
+size_t gram_smem(int xdim, int nsq, int warps) {
   using Sh = GramShape<M, TWO>;
   const int rows = M > 1 ? M - 1 : 1;
-  return (size_t)kGramCols * Sh::KP * 16 + (size_t)9 * Sh::NI * 16 + 8 * (size_t)rows * xdim + 8 + 8 * (size_t)nsq;
+  const size_t tab = ((size_t)(8 * rows * xdim + 8 + 8 * nsq) + 15) & ~(size_t)15;
+  return tab + (size_t)warps * Sh::WARP_BYTES;
 }
 
 // Runs one Gram reduction; G receives the upper triangle (E entries).
@@ -234,28 +289,45 @@ template <int M, bool TWO>
 int gram_run(const GramArgs &g0, int device, cudaStream_t s, std::vector<double> &G, fock_space *sp) {
   constexpr int E = GramShape<M, TWO>::E;
   GramArgs g = g0;
-  const size_t smem = gram_smem<M, TWO>(g.xdim, g.nsq);
   auto kern = fock_gram_kernel<M, TWO>;
-  if (smem > 48 * 1024) FOCK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  FOCK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGramCols, smem));
-  if (per_sm < 1) return FOCK_ERR_UNSUPPORTED;
-  int64_t tiles = ((int64_t)g.ncol + kGramCols - 1) / kGramCols;
+  int optin = 0;
+  FOCK_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  // warps per block: the most resident warps per SM (shared memory and
+  // registers), fewest blocks on a tie
+  int warps = 0, per_sm = 0;
+  for (int w = 8; w >= 1; w /= 2) {
+    const size_t sm_w = gram_smem<M, TWO>(g.xdim, g.nsq, w);
+    if (sm_w > (size_t)optin) continue;
+    FOCK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_w));
+    int b = 0;
+    FOCK_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 32 * w, sm_w));
+    if (b * w > per_sm * warps) {
+      warps = w;
+      per_sm = b;
+    }
+  }
+  if (warps < 1 || per_sm < 1) return FOCK_ERR_UNSUPPORTED;
+  const size_t smem = gram_smem<M, TWO>(g.xdim, g.nsq, warps);
+  FOCK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t tiles = ((int64_t)g.ncol + kGramWarp - 1) / kGramWarp;
   int64_t grid = (int64_t)per_sm * fock_get_sm_count(device);
-  if (grid > tiles) grid = tiles;
+  if (grid * warps > tiles) grid = (tiles + warps - 1) / warps;
   if (grid < 1) grid = 1;
-  const int gst = grow(&sp->dm_part, &sp->dm_part_bytes, sizeof(double2) * (size_t)E * (grid + 1));
+  const int64_t nwarps = grid * warps;
+  const size_t nslots = (size_t)GramShape<M, TWO>::SLOTS * nwarps;
+  const int gst = grow(&sp->dm_part, &sp->dm_part_bytes, sizeof(double2) * ((size_t)E * (nwarps + 1) + nslots));
   if (gst) return gst;
   double2 *buf = (double2 *)sp->dm_part;
   g.partial = buf;
-  kern<<<(unsigned)grid, kGramCols, smem, s>>>(g);
+  g.slots = buf + (size_t)E * (nwarps + 1);
+  kern<<<(unsigned)grid, 32 * warps, smem, s>>>(g);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) {
-    fock_gram_reduce<<<(E + 127) / 128, 128, 0, s>>>(buf, (int)grid, E, buf + (size_t)E * grid);
+    fock_gram_reduce<<<(E + 127) / 128, 128, 0, s>>>(buf, (int)nwarps, E, buf + (size_t)E * nwarps);
     e = cudaGetLastError();
   }
   G.assign(2 * (size_t)E, 0.0);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(G.data(), buf + (size_t)E * grid, sizeof(double2) * E, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(G.data(), buf + (size_t)E * nwarps, sizeof(double2) * E, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e == cudaSuccess ? FOCK_OK : fock_cuda_status(e);
 }
@@ -326,27 +398,12 @@ extern "C" int fock_density_matrices(const fock_space *sp, const void *C_dev, do
   g.sat = sp->tab.sat32;
   g.C = (const float4 *)((const char *)ws + 256);
   g.partial = nullptr;
+  g.slots = nullptr;
   const double scale2 = ldexp(1.0, 2 * words[1]);       // |C|^2 units of the split
   auto pair_index = [M](int k, int l) {                  // unordered pair {k, l} in the kernel's order
     const int s = k < l ? k : l, t = k < l ? l : k;
     return s * M - s * (s - 1) / 2 + (t - s);
   };
-  if (!st && rho1_host) {
-    g.ncol = (uint32_t)nc_of(N - 1, M);
-    std::vector<double> G;
-    st = gram_dispatch<false>(M, g, sp->device, s, G, (fock_space *)sp);
-    if (!st) {
-      int e = 0;
-      for (int a = 0; a < M; ++a)
-        for (int b = a; b < M; ++b, ++e) {
-          const double re = G[2 * e] * scale2, im = G[2 * e + 1] * scale2;
-          rho1_host[2 * (a * M + b)] = re;
-          rho1_host[2 * (a * M + b) + 1] = im;
-          rho1_host[2 * (b * M + a)] = re;
-          rho1_host[2 * (b * M + a) + 1] = -im;
-        }
-    }
-  }
   if (!st && rho2_host) {
     const size_t m4 = (size_t)M * M * M * M;
     if (N < 2) {
@@ -376,6 +433,37 @@ extern "C" int fock_density_matrices(const fock_space *sp, const void *C_dev, do
                 rho2_host[2 * o + 1] = full[2 * src + 1];
               }
       }
+    }
+  }
+  if (!st && rho1_host && rho2_host && N >= 2) {
+    // rho1 as the partial trace of rho2: sum_x a^dag_k a^dag_x a_x a_l =
+    // a^dag_k N^ a_l, and N^ a_l = (N - 1) a_l on N particles, so
+    // rho1[k][l] = sum_x rho2[k][x][x][l] / (N - 1)
+    for (int k = 0; k < M; ++k)
+      for (int l = 0; l < M; ++l) {
+        double re = 0.0, im = 0.0;
+        for (int x = 0; x < M; ++x) {
+          const size_t o = ((((size_t)k * M + x) * M + x) * M + l);
+          re += rho2_host[2 * o];
+          im += rho2_host[2 * o + 1];
+        }
+        rho1_host[2 * (k * M + l)] = re / (N - 1);
+        rho1_host[2 * (k * M + l) + 1] = im / (N - 1);
+      }
+  } else if (!st && rho1_host) {
+    g.ncol = (uint32_t)nc_of(N - 1, M);
+    std::vector<double> G;
+    st = gram_dispatch<false>(M, g, sp->device, s, G, (fock_space *)sp);
+    if (!st) {
+      int e = 0;
+      for (int a = 0; a < M; ++a)
+        for (int b = a; b < M; ++b, ++e) {
+          const double re = G[2 * e] * scale2, im = G[2 * e + 1] * scale2;
+          rho1_host[2 * (a * M + b)] = re;
+          rho1_host[2 * (a * M + b) + 1] = im;
+          rho1_host[2 * (b * M + a)] = re;
+          rho1_host[2 * (b * M + a) + 1] = -im;
+        }
     }
   }
   return st;

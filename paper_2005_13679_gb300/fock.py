@@ -51,6 +51,10 @@ FOCK_PATH_DENSE = 4
 FOCK_PATH_SPARSE = 5
 FOCK_PATH_LIST = 6
 FOCK_PATH_TWOPHASE_BLOCK = 7
+FOCK_FORM_DENSE = 1
+FOCK_FORM_PAIR_WEIGHT = 2
+FOCK_FORM_PAIR_MOMENTUM = 4
+FOCK_FORM_NEAREST_NEIGHBOUR = 8
 PATH_NAMES = {1: "twophase_tc", 2: "twophase", 3: "nn", 4: "dense", 5: "sparse", 6: "list", 7: "twophase_block"}
 
 # Every extern "C" symbol declared in include/fock.h.
@@ -59,7 +63,7 @@ EXPORTS = (
     "fock_space_create", "fock_space_destroy", "fock_space_size", "fock_rank", "fock_unrank",
     "fock_build_jump_maps", "fock_jump_map_get", "fock_jump_maps_free",
     "fock_hamiltonian_create", "fock_hamiltonian_destroy", "fock_hamiltonian_terms",
-    "fock_hamiltonian_is_real",
+    "fock_hamiltonian_is_real", "fock_hamiltonian_forms",
     "fock_apply_path", "fock_apply_set_path", "fock_autotune",
     "fock_apply_set_events", "fock_apply_workspace_size", "fock_apply_H", "fock_apply_check", "fock_debug_set_wait_polls",
     "fock_apply_H_host", "fock_apply_H_noalloc",
@@ -116,6 +120,7 @@ def load(path: str | None = None):
         "fock_hamiltonian_destroy": [vp],
         "fock_hamiltonian_terms": [vp, P(i64)],
         "fock_hamiltonian_is_real": [vp, P(ctypes.c_int)],
+        "fock_hamiltonian_forms": [vp, P(ctypes.c_int32)],
         "fock_apply_path": [vp, vp, i32, ctypes.c_int, ctypes.c_int, sz, P(i32)],
         "fock_apply_set_path": [vp, i32, ctypes.c_int, ctypes.c_int, ctypes.c_int],
         "fock_autotune": [vp, vp, i32, ctypes.c_int, ctypes.c_char_p, P(FockTuning), vp],
@@ -295,6 +300,13 @@ def fock_hamiltonian_is_real(ham) -> bool:
     return bool(r.value)
 
 
+def fock_hamiltonian_forms(ham) -> int:
+    """FOCK_FORM_* bits of the operator's structure."""
+    r = ctypes.c_int32()
+    _check(load().fock_hamiltonian_forms(ham, ctypes.byref(r)), "fock_hamiltonian_forms")
+    return r.value
+
+
 def fock_apply_path(sp, ham, nrhs: int = 1, precision: int = FOCK_PREC_F64, arm: int = FOCK_ARM_AUTO,
                     workspace_bytes: int | None = None) -> int:
     """FOCK_PATH_* an apply with these options takes (default: the preferred workspace)."""
@@ -454,6 +466,7 @@ class Hamiltonian:
         self.handle = fock_hamiltonian_create(space.handle, h, W, tol)
         self.terms = fock_hamiltonian_terms(self.handle)
         self.real = fock_hamiltonian_is_real(self.handle)
+        self.forms = fock_hamiltonian_forms(self.handle)
 
     def apply(self, C, sigma=None, nrhs=1, precision=FOCK_PREC_F64, arm=FOCK_ARM_AUTO, workspace=None):
         return fock_apply_H(self.space.handle, self.handle, C, sigma, nrhs, precision, arm, workspace)

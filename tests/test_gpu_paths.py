@@ -157,3 +157,26 @@ def test_autotune_block_rhs_and_nearest_neighbour(torch):
         rows = np.arange(j, sp.nc, 211)
         ref = oracle.apply_rows(N, M, h, W, Cb[:, j], rows)
         assert rel(out[rows, j], ref) <= 1e-12
+
+
+def test_operator_forms(torch):
+    """The structure the library finds in an operator: generic dense W, the
+    Lieb-Liniger contact interaction (pair weight conserved, rank one inside
+    every pair-momentum block), a pair-weight operator that is not of contact
+    form, and the Bose-Hubbard ring."""
+    F = fock
+    sp = fock.Space(6, 5)
+    h, W = inputs.random_hermitian_hw(5, 3)
+    assert fock.Hamiltonian(sp, h, W).forms & F.FOCK_FORM_DENSE
+    h, W = inputs.lieb_liniger_hw(5, 0.7)
+    f = fock.Hamiltonian(sp, h, W).forms
+    assert f & F.FOCK_FORM_PAIR_WEIGHT and f & F.FOCK_FORM_PAIR_MOMENTUM and not f & F.FOCK_FORM_DENSE
+    W2 = W.copy()
+    # one coupling of the block K = 4 ({0,4}, {1,3}, {2,2}) changed: k + q = s + l
+    # still holds, the block is no longer rank one off its diagonal
+    for k, q, s, l in ((0, 4, 1, 3), (1, 3, 0, 4)):
+        W2[k, q, s, l] = W2[q, k, l, s] = W2[k, q, l, s] = W2[q, k, s, l] = 0.3
+    f2 = fock.Hamiltonian(sp, h, W2).forms
+    assert f2 & F.FOCK_FORM_PAIR_WEIGHT and not f2 & F.FOCK_FORM_PAIR_MOMENTUM
+    h, W = inputs.bose_hubbard_hw(5, 1.0, 4.0)
+    assert fock.Hamiltonian(sp, h, W).forms & F.FOCK_FORM_NEAREST_NEIGHBOUR
