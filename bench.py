@@ -983,6 +983,9 @@ def main():
                     "kernel": "phase 1 (pair-momentum amplitudes Z_K)", "kernel_ms": kernel_ms,
                     "executed_terms": executed, "flops_per_term": flops_term, "path": path,
                     "form": "pair_momentum",
+                    "z_bytes_written": math.comb(w.N - 2 + w.M - 1, w.M - 1) * w.nrhs * (2 * w.M - 1)
+                                       * (8 if prec == 2 else 16),
+                    "traffic_phase2": load_traffic(w.name, args.precision, "_phase2"),
                     "pipe": "FP32 (fma.rn.f32x2 and scalar); peak = 152 SMs x 128 lanes x 2 flop x 2070 MHz"}
     else:
         key = (args.precision, "twophase" if path.startswith("twophase") else "direct")
