@@ -581,11 +581,14 @@ struct TcPolMixed {                                      // FP32-mixed: fp16 hi/
                  idesc, kk > 0);
   }
   // Y = D 2^(e_rho + e_c - 30): the row scale 2^(15 - e_rho) of the image and
-  // the column scale 2^(15 - e_c) of the digits taken out.  Both warps of a
-  // lane quarter read every column; each writes alternate complex rows.
+  // the column scale 2^(15 - e_c) of the digits taken out.  The epilogue is
+  // light (one scaling per value), so only the second warp of a lane quarter
+  // drains (the first warp of the first quarter issues the MMAs); the others
+  // only keep the barrier count.
   __device__ static void drain(const TwoPhaseArgs &t, uint32_t tq, uint32_t colg, bool live, const int *s_er, int half) {
     constexpr int P = M * (M + 1) / 2;
     float2 *__restrict__ Y = (float2 *)t.Y;
+    if (!half) return;
     float d[NT];
 #pragma unroll
     for (int i = 0; i < NT / 16; ++i) tc_ld_x16(tq + (uint32_t)(16 * i), *reinterpret_cast<float(*)[16]>(&d[16 * i]));
@@ -593,7 +596,6 @@ struct TcPolMixed {                                      // FP32-mixed: fp16 hi/
     const int ec = (int)d[R2] - 30;
 #pragma unroll
     for (int r = 0; r < P; ++r) {
-      if ((r & 1) != half) continue;                     // the two warps of a lane quarter take alternate rows
       float v[2];
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
