@@ -505,7 +505,8 @@ struct TcPolDF {                                         // FP64-class: exact di
   }
   // Lane-local epilogue in passes of four complex rows: levels 7, 6, 5 of a
   // complex row r sit in columns 6r .. 6r+5 (Re row, then Im row) and levels
-  // 4, 3, 2 in N2 + 6r .. N2 + 6r + 5, read as 8-column loads.  The two warps
+  // 4, 3, 2 in N2 + 6r .. N2 + 6r + 5, read as 16- and 8-column loads (a
+  // full pass; 8-column loads for the last, partial one).  The two warps
   // of a lane quarter take alternate passes (half = pass & 1), last pass
   // first; the column exponent is read with a warp's first loads.
   __device__ static void drain(const TwoPhaseArgs &t, uint32_t tq, uint32_t colg, bool live, const int *s_er, int half) {
@@ -522,12 +523,19 @@ struct TcPolDF {                                         // FP64-class: exact di
     for (int pass = p0; pass >= 0; pass -= 2) {
       const int nrow = P - 4 * pass < 4 ? P - 4 * pass : 4;
       float A[24], B[24];
+      if (nrow == 4) {
+        tc_ld_x16(tq + (uint32_t)(24 * pass), *reinterpret_cast<float(*)[16]>(&A[0]));
+        tc_ld_x8(tq + (uint32_t)(24 * pass + 16), *reinterpret_cast<float(*)[8]>(&A[16]));
+        tc_ld_x16(tq + (uint32_t)(sh.N2 + 24 * pass), *reinterpret_cast<float(*)[16]>(&B[0]));
+        tc_ld_x8(tq + (uint32_t)(sh.N2 + 24 * pass + 16), *reinterpret_cast<float(*)[8]>(&B[16]));
+      } else {
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
-        if (6 * nrow > 8 * c) {
-          tc_ld_x8(tq + (uint32_t)(24 * pass + 8 * c), *reinterpret_cast<float(*)[8]>(&A[8 * c]));
-          tc_ld_x8(tq + (uint32_t)(sh.N2 + 24 * pass + 8 * c), *reinterpret_cast<float(*)[8]>(&B[8 * c]));
-        }
+        for (int c = 0; c < 3; ++c)
+          if (6 * nrow > 8 * c) {
+            tc_ld_x8(tq + (uint32_t)(24 * pass + 8 * c), *reinterpret_cast<float(*)[8]>(&A[8 * c]));
+            tc_ld_x8(tq + (uint32_t)(sh.N2 + 24 * pass + 8 * c), *reinterpret_cast<float(*)[8]>(&B[8 * c]));
+          }
+      }
       tc_wait_ld();
       if (first) {
         first = false;
