@@ -563,7 +563,7 @@ struct TcPolDF {                                         // FP64-class: exact di
           } else {
             y = tc_scale_row(hi, lo, s_er[2 * r] + ec, s_er[2 * r + 1] + ec);
           }
-          if (live) Y[twophase_yidx(r, colg, P)] = y;
+          if (live) __stcs(&Y[twophase_yidx(r, colg, P)], y);
         }
       }
     }
@@ -611,7 +611,7 @@ struct TcPolMixed {                                      // FP32-mixed: fp16 hi/
         v[c] = e >= -126 ? __fmul_rn(d[2 * r + c], tc_pow2(e))
                          : __fmul_rn(__fmul_rn(d[2 * r + c], tc_pow2(-126)), tc_pow2(max(e + 126, -126)));
       }
-      if (live) Y[twophase_yidx(r, colg, P)] = make_float2(v[0], v[1]);
+      if (live) __stcs(&Y[twophase_yidx(r, colg, P)], make_float2(v[0], v[1]));
     }
   }
 };

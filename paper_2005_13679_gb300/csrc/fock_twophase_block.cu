@@ -182,8 +182,9 @@ __device__ __forceinline__ void block_df(int K, int lo, int co, uint32_t base, c
       }
     }
     const int s = lo + r, l = K - s;
-    if (live) Y[twophase_yidx(s * M - (s * (s - 1)) / 2 + (l - s), col, P)] =
-        make_float4(fp2_x(h), fp2_y(h), fp2_x(lw), fp2_y(lw));
+    if (live)
+      __stcs(&Y[twophase_yidx(s * M - (s * (s - 1)) / 2 + (l - s), col, P)],
+             make_float4(fp2_x(h), fp2_y(h), fp2_x(lw), fp2_y(lw)));
   }
 }
 
@@ -258,8 +259,9 @@ __device__ __forceinline__ void block_mixed(int K, int lo, int co, uint32_t base
       A2 = fp2_fma(Rp, Xs[i], A2);                         // (Re R Im X, Im R Re X)
     }
     const int s = lo + r, l = K - s;
-    if (live) Y[twophase_yidx(s * M - (s * (s - 1)) / 2 + (l - s), col, P)] =
-        make_float2(fp2_x(A1) - fp2_y(A1), fp2_x(A2) + fp2_y(A2));
+    if (live)
+      __stcs(&Y[twophase_yidx(s * M - (s * (s - 1)) / 2 + (l - s), col, P)],
+             make_float2(fp2_x(A1) - fp2_y(A1), fp2_x(A2) + fp2_y(A2)));
   }
 }
 

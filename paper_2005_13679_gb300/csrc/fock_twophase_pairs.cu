@@ -116,7 +116,7 @@ __device__ __forceinline__ void pairs_df(int K, int lo, uint32_t base, const Pai
   fp2_dprod(h, lw, fp2_make(cK.x, cK.x), fp2_make(cK.y, cK.y), p, e);
   h = fp2_add(p, e);
   lw = fp2_sub(e, fp2_sub(h, p));
-  if (live) Z[twophase_yidx(K, col, 2 * M - 1)] = make_float4(fp2_x(h), fp2_y(h), fp2_x(lw), fp2_y(lw));
+  if (live) __stcs(&Z[twophase_yidx(K, col, 2 * M - 1)], make_float4(fp2_x(h), fp2_y(h), fp2_x(lw), fp2_y(lw)));
 }
 
 template <int M>
@@ -173,7 +173,7 @@ __device__ __forceinline__ void pairs_mixed(int K, int lo, uint32_t base, const 
     acc = fp2_fma(fp2_make(amp, amp), fp2_make(v.x, v.y), acc);
   }
   acc = fp2_mul(acc, fp2_make(cK, cK));
-  if (live) Z[twophase_yidx(K, col, 2 * M - 1)] = make_float2(fp2_x(acc), fp2_y(acc));
+  if (live) __stcs(&Z[twophase_yidx(K, col, 2 * M - 1)], make_float2(fp2_x(acc), fp2_y(acc)));
 }
 
 template <int M>
